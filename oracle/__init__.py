@@ -1,0 +1,19 @@
+"""CPU oracle for the hierarchical Hough transform (test infrastructure only).
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg may import
+this package.  It loads `hht_oracle.c` (plain C, compiled with gcc on first
+use) through ctypes and shares no code with the CUDA library.
+"""
+from .oracle import (  # noqa: F401
+    build,
+    detect,
+    getcode,
+    scaled_F,
+    fht_votes,
+    frame_side,
+    OracleResult,
+    STAT_TESTED,
+    STAT_PASSED,
+    STAT_VOTES,
+    STAT_TESTS,
+)

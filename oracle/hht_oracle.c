@@ -1,0 +1,267 @@
+/*
+ * CPU oracle for the hierarchical Hough transform of Singh & Bhatia,
+ * "A Fast Decision Technique for Hierarchical Hough Transform for Line
+ * Detection" (arXiv:1007.0547).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct
+ * reference that the CUDA library is checked against.  Only the test suite,
+ * the smoke check and the benchmark's CPU-baseline leg may load it; the
+ * product library never calls it and shares no code with it.
+ *
+ * What it computes (Section 3):
+ *   - Every edge point (x, y) is the parameter-space line b = y - m*x.  Points
+ *     are processed in two halves: ALPHA as given and BETA with x and y
+ *     swapped (Section 3, first paragraph).  Here every point enters both
+ *     halves; the Sobel-gradient split is not part of this path.
+ *   - The parameter space m in [-1, 1], b in [-2L, 2L] (L = smallest power of
+ *     two >= max(W, H)) is the level-0 region.  A region is split into four
+ *     quadrants NE, NW, SW, SE (quad1..quad4, Section 3).
+ *   - A line gets a 4-bit code per region: one bit per corner in the order
+ *     NE, NW, SW, SE (NE is the leftmost bit); a bit is 1 when the corner is
+ *     below the line, i.e. F = y0 - m*x0 - b < 0 for the corner (x0, y0) and
+ *     the line's slope m and intercept b (Section 2, getcode() in Section 3).
+ *   - A line votes for a region when its code is neither 0000 nor 1111
+ *     (Section 3, steps 5 and 12.v).
+ *   - A region whose votes reach the threshold T is split further, down to
+ *     level `depth`, where it is reported as a peak cell (Section 3, step 13).
+ *
+ * Readings where the paper is silent or ambiguous:
+ *   - The grid is dyadic: at depth D there are K = 2^D cells per side, with
+ *     m_i = -1 + 2i/K and b_j = -2L + 4Lj/K.  All arithmetic is done on
+ *     K * F, which is an exact integer (int64 here; int128 for the squared
+ *     circle test).
+ *   - Threshold: a region passes when votes >= T (the pseudocode's
+ *     "vote > THRESHOLD" is the same rule with T = THRESHOLD + 1).
+ *   - The level-0 region is always split (step 6 of the pseudocode has no
+ *     threshold test).
+ *   - The solution() removal of plotted voters is not applied, so the result
+ *     is independent of traversal order.
+ *   - The parent-code child-exclusion shortcut (step 12.i) is not applied:
+ *     every child code is computed, which cannot change any result.
+ *
+ * The traversal follows the pseudocode's depth-first order (NE, NW, SW, SE)
+ * with one voter list per level instead of one code array per level: a point
+ * is only tested for a child when it voted for the parent, which is what the
+ * code test "(level-1).linecode != 0000 and != 1111" of step 12.b decides.
+ *
+ * The FHT mode replaces the code test by the circumscribed-circle test of the
+ * prior-art Fast Hough Transform that the paper compares with (Sections 1-2):
+ * a line votes when its distance from the region centre is at most the radius
+ * of the circle through the region's corners.  Distances are measured in cell
+ * units, where regions are squares, and decided exactly with int128.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_OK 0
+#define ORACLE_E_ARG (-1)
+#define ORACLE_E_RANGE (-2)
+#define ORACLE_E_INVARIANT (-3)
+#define ORACLE_E_CAPACITY (-4)
+#define ORACLE_E_NOMEM (-5)
+
+#define ORACLE_MODE_EXACT 0
+#define ORACLE_MODE_FHT 1
+
+typedef struct {
+    uint32_t half, i, j, votes;
+} oracle_leaf;
+
+typedef struct {
+    uint32_t half, level, i0, j0, size, votes;
+} oracle_region;
+
+/* Side L of the square image frame: smallest power of two >= max(W, H). */
+int64_t oracle_frame_side(int32_t W, int32_t H)
+{
+    int64_t m = W > H ? W : H, L = 1;
+    while (L < m) L <<= 1;
+    return L;
+}
+
+/*
+ * K * F for edge point (x, y) at grid corner (i, j) of a depth-D grid.
+ * The parameter-space line of the point has slope -x and intercept y; the
+ * corner is the parameter point (m_i, b_j).  F = b_j - (-x) * m_i - y
+ * (Section 2), multiplied by K so that it is an integer.
+ */
+int64_t oracle_scaled_F(int32_t x, int32_t y, int64_t i, int64_t j, int64_t L, int32_t D)
+{
+    const int64_t K = (int64_t)1 << D;
+    const int64_t K_b = -2 * L * K + 4 * L * j; /* K * b_j */
+    const int64_t K_m = -K + 2 * i;             /* K * m_i */
+    const int64_t slope = -(int64_t)x, intercept = y;
+    return K_b - slope * K_m - K * intercept;
+}
+
+/* getcode() of Section 3 for region (i0, j0) of side S cells. */
+uint32_t oracle_getcode(int32_t x, int32_t y, int64_t i0, int64_t j0, int64_t S, int64_t L, int32_t D)
+{
+    uint32_t code = 0;
+    if (oracle_scaled_F(x, y, i0 + S, j0 + S, L, D) < 0) code |= 8u; /* bit 1: NorthEast */
+    if (oracle_scaled_F(x, y, i0, j0 + S, L, D) < 0) code |= 4u;     /* bit 2: NorthWest */
+    if (oracle_scaled_F(x, y, i0, j0, L, D) < 0) code |= 2u;         /* bit 3: SouthWest */
+    if (oracle_scaled_F(x, y, i0 + S, j0, L, D) < 0) code |= 1u;     /* bit 4: SouthEast */
+    return code;
+}
+
+/*
+ * Circumscribed-circle test of the FHT for region (i0, j0, S).
+ * In cell units the line is G(i, j) = K*F = 4L*j + 2x*i - 2LK - Kx - Ky = 0;
+ * its distance from the centre c = (i0 + S/2, j0 + S/2) is |G(c)| / |(2x, 4L)|
+ * and the circle radius is S / sqrt(2).  G(c) is an integer, so the test
+ * G(c)^2 <= 2 S^2 (x^2 + 4 L^2) is exact in int128.
+ */
+int oracle_fht_votes(int32_t x, int32_t y, int64_t i0, int64_t j0, int64_t S, int64_t L, int32_t D)
+{
+    const int64_t K = (int64_t)1 << D;
+    const __int128 Gc = (__int128)(2 * L) * (2 * j0 + S - K) + (__int128)x * (2 * i0 + S - K) - (__int128)K * y;
+    const __int128 lhs = Gc * Gc;
+    const __int128 rhs = (__int128)2 * S * S * ((__int128)x * x + (__int128)4 * L * L);
+    return lhs <= rhs;
+}
+
+typedef struct {
+    const int32_t *px, *py; /* current half's coordinates */
+    int64_t L;
+    int32_t D, T, mode, half;
+    uint32_t **lists;       /* lists[l]: voter ids of the region being visited at level l */
+    uint64_t *stats;        /* [2][D+1][4]: tested, passed, votes, tests */
+    oracle_leaf *leaves;
+    int64_t leaf_cap, n_leaves;
+    oracle_region *regions;
+    int64_t region_cap, n_regions;
+} walk_t;
+
+static uint64_t *stat_at(walk_t *w, int level, int k)
+{
+    return &w->stats[((int64_t)w->half * (w->D + 1) + level) * 4 + k];
+}
+
+static int line_votes(const walk_t *w, uint32_t v, int64_t i0, int64_t j0, int64_t S)
+{
+    if (w->mode == ORACLE_MODE_FHT) return oracle_fht_votes(w->px[v], w->py[v], i0, j0, S, w->L, w->D);
+    const uint32_t code = oracle_getcode(w->px[v], w->py[v], i0, j0, S, w->L, w->D);
+    return code != 0u && code != 15u;
+}
+
+static void record_region(walk_t *w, int level, int64_t i0, int64_t j0, int64_t S, int64_t votes)
+{
+    if (w->regions && w->n_regions < w->region_cap) {
+        oracle_region *r = &w->regions[w->n_regions];
+        r->half = (uint32_t)w->half; r->level = (uint32_t)level;
+        r->i0 = (uint32_t)i0; r->j0 = (uint32_t)j0; r->size = (uint32_t)S; r->votes = (uint32_t)votes;
+    }
+    w->n_regions++;
+}
+
+/* Split a region of level `level` that reached the threshold (or is the root). */
+static void subdivide(walk_t *w, int level, int64_t i0, int64_t j0, int64_t S, const uint32_t *V, int64_t nV)
+{
+    const int64_t h = S / 2;
+    /* quad1..quad4 = NE, NW, SW, SE: lower-left corners of the children. */
+    const int64_t ci[4] = {i0 + h, i0, i0, i0 + h};
+    const int64_t cj[4] = {j0 + h, j0 + h, j0, j0};
+    const int child = level + 1;
+    uint32_t *buf = w->lists[child];
+
+    *stat_at(w, child, 3) += 4 * (uint64_t)nV; /* four child codes per voter */
+    for (int q = 0; q < 4; ++q) {
+        int64_t cnt = 0;
+        for (int64_t k = 0; k < nV; ++k)
+            if (line_votes(w, V[k], ci[q], cj[q], h)) buf[cnt++] = V[k];
+        *stat_at(w, child, 0) += 1;
+        *stat_at(w, child, 2) += (uint64_t)cnt;
+        record_region(w, child, ci[q], cj[q], h, cnt);
+        if (cnt >= w->T) {
+            *stat_at(w, child, 1) += 1;
+            if (child == w->D) {
+                if (w->n_leaves < w->leaf_cap) {
+                    oracle_leaf *lf = &w->leaves[w->n_leaves];
+                    lf->half = (uint32_t)w->half; lf->i = (uint32_t)ci[q]; lf->j = (uint32_t)cj[q];
+                    lf->votes = (uint32_t)cnt;
+                }
+                w->n_leaves++;
+            } else {
+                subdivide(w, child, ci[q], cj[q], h, buf, cnt);
+            }
+        }
+    }
+}
+
+static int leaf_cmp(const void *a, const void *b)
+{
+    const oracle_leaf *x = (const oracle_leaf *)a, *y = (const oracle_leaf *)b;
+    if (x->half != y->half) return x->half < y->half ? -1 : 1;
+    if (x->i != y->i) return x->i < y->i ? -1 : 1;
+    if (x->j != y->j) return x->j < y->j ? -1 : 1;
+    return 0;
+}
+
+/*
+ * Run the hierarchy on n points (xy[2k] = x, xy[2k+1] = y) of a W x H image.
+ *   stats: caller array of 2 * (depth + 1) * 4 uint64, per half and level:
+ *          {regions tested, regions passed, votes, code evaluations}.
+ *   leaves: caller array of leaf_cap entries; *n_leaves receives the count
+ *          (also when it exceeds leaf_cap, which returns ORACLE_E_CAPACITY).
+ *   regions: optional (may be NULL) dump of every tested region.
+ * Leaves are sorted by (half, i, j).
+ */
+int oracle_detect(const int16_t *xy, int64_t n, int32_t W, int32_t H, int32_t depth, int32_t T, int32_t mode,
+                  oracle_leaf *leaves, int64_t leaf_cap, int64_t *n_leaves, uint64_t *stats,
+                  oracle_region *regions, int64_t region_cap, int64_t *n_regions)
+{
+    if (n < 0 || W < 1 || H < 1 || W > 32767 || H > 32767 || depth < 1 || depth > 24 || T < 1 || !n_leaves ||
+        !stats || (n > 0 && !xy) || (leaf_cap > 0 && !leaves) || (mode != ORACLE_MODE_EXACT && mode != ORACLE_MODE_FHT))
+        return ORACLE_E_ARG;
+    for (int64_t k = 0; k < n; ++k)
+        if (xy[2 * k] < 0 || xy[2 * k] >= W || xy[2 * k + 1] < 0 || xy[2 * k + 1] >= H) return ORACLE_E_RANGE;
+
+    walk_t w;
+    memset(&w, 0, sizeof w);
+    w.L = oracle_frame_side(W, H);
+    w.D = depth; w.T = T; w.mode = mode;
+    w.stats = stats; w.leaves = leaves; w.leaf_cap = leaf_cap;
+    w.regions = regions; w.region_cap = regions ? region_cap : 0;
+    memset(stats, 0, sizeof(uint64_t) * 2 * (size_t)(depth + 1) * 4);
+
+    int rc = ORACLE_OK;
+    const size_t cap = (size_t)(n > 0 ? n : 1);
+    int32_t *px = (int32_t *)malloc(cap * sizeof(int32_t));
+    int32_t *py = (int32_t *)malloc(cap * sizeof(int32_t));
+    uint32_t *pool = (uint32_t *)malloc(cap * sizeof(uint32_t) * (size_t)(depth + 1));
+    uint32_t **lists = (uint32_t **)malloc(sizeof(uint32_t *) * (size_t)(depth + 1));
+    if (!px || !py || !pool || !lists) { rc = ORACLE_E_NOMEM; goto done; }
+    for (int l = 0; l <= depth; ++l) lists[l] = pool + cap * (size_t)l;
+    w.lists = lists; w.px = px; w.py = py;
+
+    const int64_t K = (int64_t)1 << depth;
+    for (int half = 0; half < 2; ++half) {
+        w.half = half;
+        for (int64_t k = 0; k < n; ++k) {
+            /* ALPHA takes (x, y); BETA takes (y, x) (Section 3). */
+            px[k] = half == 0 ? xy[2 * k] : xy[2 * k + 1];
+            py[k] = half == 0 ? xy[2 * k + 1] : xy[2 * k];
+        }
+        /* Level 0: every line is tested against the whole parameter space. */
+        int64_t nv = 0;
+        for (int64_t k = 0; k < n; ++k)
+            if (line_votes(&w, (uint32_t)k, 0, 0, K)) lists[0][nv++] = (uint32_t)k;
+        if (nv != n) { rc = ORACLE_E_INVARIANT; goto done; } /* every line crosses the root */
+        *stat_at(&w, 0, 0) = 1;
+        *stat_at(&w, 0, 1) = 1; /* the root is always split */
+        *stat_at(&w, 0, 2) = (uint64_t)nv;
+        *stat_at(&w, 0, 3) = (uint64_t)n;
+        record_region(&w, 0, 0, 0, K, nv);
+        subdivide(&w, 0, 0, 0, K, lists[0], nv);
+    }
+    *n_leaves = w.n_leaves;
+    if (n_regions) *n_regions = w.n_regions;
+    if (w.n_leaves > leaf_cap) { rc = ORACLE_E_CAPACITY; goto done; }
+    if (w.n_leaves > 0) qsort(leaves, (size_t)w.n_leaves, sizeof(oracle_leaf), leaf_cmp);
+
+done:
+    free(px); free(py); free(pool); free(lists);
+    return rc;
+}
