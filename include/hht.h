@@ -1,0 +1,163 @@
+/*
+ * hht.h - C ABI of the GB300 hierarchical Hough transform library (libhht.so).
+ *
+ * The library runs the hierarchical Hough transform for straight lines of
+ * Singh & Bhatia, "A Fast Decision Technique for Hierarchical Hough Transform
+ * for Line Detection" (arXiv:1007.0547), on one CUDA device:
+ *
+ *   - Each edge point (x, y) is the line b = y - m*x of the (m, b) parameter
+ *     space (Section 1, slope-intercept form).  Points are processed in two
+ *     halves: half 0 ("ALPHA") as given, half 1 ("BETA") with x and y swapped,
+ *     so that both halves only need slopes |m| <= 1 (Section 3).  Every point
+ *     enters both halves.
+ *   - The parameter space m in [-1, 1], b in [-2L, 2L], L the smallest power
+ *     of two >= max(W, H), is the level-0 region.  A region is split into the
+ *     quadrants NE, NW, SW, SE (Section 3).
+ *   - A line's 4-bit code for a region has one bit per corner in the order NE,
+ *     NW, SW, SE; a bit is 1 when that corner lies strictly below the line
+ *     (Section 2: F = y0 - m*x0 - b < 0; a corner on the line is "above").
+ *     The line votes for the region when the code is neither 0000 nor 1111
+ *     (Section 3, steps 5 and 12).
+ *   - A region whose votes reach T (votes >= T) is split again; the level-0
+ *     region is always split.  At level `depth` the regions are cells of a
+ *     K x K grid, K = 2^depth, and each cell that reaches T is reported as a
+ *     leaf (Section 3, step 13; the paper's solution() output step, without
+ *     the removal of plotted voters).
+ *
+ * Leaf cell (i, j) of half h spans m in [-1 + 2i/K, -1 + 2(i+1)/K] and
+ * b in [-2L + 4Lj/K, -2L + 4L(j+1)/K] (in the half's own coordinates).
+ * Every decision is an exact integer comparison, so results are unique:
+ * leaves are reported sorted by (half, i, j).
+ *
+ * Errors: every call returns HHT_OK (0) or a negative HHT_E_* code.  No call
+ * aborts, asserts or traps; argument errors are found before any device work.
+ * Threads: a context is used by one host thread at a time.
+ */
+#ifndef HHT_H_
+#define HHT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HHT_MAX_DEPTH 24
+#define HHT_MAX_SIDE 32767
+
+enum {
+    HHT_OK = 0,
+    HHT_E_ARG = -1,          /* bad argument: NULL, n < 0, W/H outside [1, 32767],
+                                depth outside [1, 24], T < 1, bad image count */
+    HHT_E_RANGE = -2,        /* a point lies outside [0, W) x [0, H); result invalid */
+    HHT_E_CAPACITY = -3,     /* leaf buffer too small; n_leaves holds the needed count */
+    HHT_E_NOMEM = -4,        /* device memory (or the context's budget) exhausted */
+    HHT_E_TIMEOUT = -5,      /* a bounded device-side wait expired; result invalid */
+    HHT_E_CUDA = -6,         /* a CUDA runtime call failed */
+    HHT_E_PENDING = -7,      /* hht_poll: the request has not finished yet */
+    HHT_E_UNKNOWN_TICKET = -8
+};
+
+/* Edge point of an image, 0 <= x < W, 0 <= y < H. */
+typedef struct {
+    int16_t x, y;
+} hht_point;
+
+/* One reported cell: half (0 = as given, 1 = x/y swapped), cell indices (i, j)
+ * on the K x K grid of the half, and its vote count (>= T). */
+typedef struct {
+    uint32_t half, i, j, votes;
+} hht_leaf;
+
+/* Per half and level: regions tested, regions passed (votes >= T; the
+ * level-0 region always counts as passed), votes summed over the tested
+ * regions, and 4-bit codes evaluated (n at level 0, four per voter of every
+ * passed parent below). */
+typedef struct {
+    uint64_t tested, passed, votes, tests;
+} hht_level_stats;
+
+/* Result of one image.  The caller owns `leaves` (host or device memory of
+ * the context's device, leaf_capacity entries); the library fills the rest. */
+typedef struct {
+    hht_leaf *leaves;
+    uint64_t leaf_capacity;
+    uint64_t n_leaves;                               /* out: leaves found */
+    int32_t depth, L;                                /* out: grid depth, frame side */
+    int32_t status;                                  /* out: HHT_OK or HHT_E_* of this image */
+    int32_t reserved;
+    hht_level_stats stats[2][HHT_MAX_DEPTH + 1];     /* out: [half][level], levels 0..depth */
+} hht_result;
+
+/* One image of a batch or a serving request.  `points` is host memory or
+ * device memory of the context's device (n entries, read only). */
+typedef struct {
+    const hht_point *points;
+    int64_t n;
+    int32_t W, H, depth, T;
+} hht_image;
+
+typedef struct hht_ctx hht_ctx;
+
+/*
+ * Create a context on CUDA device `device`, issuing all work on `cuda_stream`
+ * (a cudaStream_t; NULL means the legacy default stream).
+ * mem_budget_bytes caps the device scratch memory the context may hold
+ * (0 = no cap beyond the device's free memory).  The context owns that
+ * scratch memory; it is freed by hht_destroy().
+ * Errors: HHT_E_ARG (out == NULL, bad device), HHT_E_CUDA.
+ */
+int hht_create(hht_ctx **out, int device, void *cuda_stream, uint64_t mem_budget_bytes);
+
+/* Destroy a context (NULL is ignored).  Waits for the context's stream. */
+void hht_destroy(hht_ctx *ctx);
+
+/*
+ * Detect lines in one image (Section 3, both halves).  `points` holds n edge
+ * points in host memory or in device memory of the context's device; n = 0 is
+ * valid.  On return the work is complete (the call synchronises the stream):
+ * out->leaves[0 .. n_leaves) hold the leaves sorted by (half, i, j) and
+ * out->stats[h][l] the statistics for levels 0..depth.
+ * Errors: HHT_E_ARG (checked before any device work), HHT_E_RANGE (a point
+ * outside the image), HHT_E_CAPACITY (out->n_leaves = required count; call
+ * again with a larger buffer), HHT_E_NOMEM, HHT_E_TIMEOUT, HHT_E_CUDA.
+ */
+int hht_detect(hht_ctx *ctx, const hht_point *points, int64_t n, int32_t W, int32_t H, int32_t depth,
+               int32_t T, hht_result *out);
+
+/*
+ * Detect lines in `count` independent images in one batched pass: all images
+ * and both halves of each advance level by level through the same kernel
+ * launches (captured as one CUDA graph per level schedule).  outs[k] receives
+ * image k's result exactly as hht_detect would produce it.  Returns HHT_OK
+ * when every image succeeded, else the first failing image's code (each
+ * outs[k].status holds that image's own code).
+ */
+int hht_detect_batch(hht_ctx *ctx, const hht_image *images, int32_t count, hht_result *outs);
+
+/*
+ * Serving interface.  hht_submit() queues one request and returns at once;
+ * the image is copied (host points) or referenced (device points; they must
+ * stay valid until the request is done).  Requests are admitted to the GPU as
+ * the context's memory budget and slots allow and are processed in
+ * continuous batches; hht_poll() returns HHT_E_PENDING until the request is
+ * done, then fills *out (whose leaf buffer the caller provides at poll time)
+ * and releases the ticket.  hht_progress() lets the library advance queued
+ * work without blocking (it returns the number of requests in flight).
+ */
+int hht_submit(hht_ctx *ctx, const hht_image *image, uint64_t *ticket);
+int hht_poll(hht_ctx *ctx, uint64_t ticket, hht_result *out);
+int hht_progress(hht_ctx *ctx);
+
+/* Short description of an HHT_* code (static string). */
+const char *hht_strerror(int code);
+
+/* Library build description (static string). */
+const char *hht_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HHT_H_ */

@@ -7,6 +7,7 @@ use) through ctypes and shares no code with the CUDA library.
 from .oracle import (  # noqa: F401
     build,
     detect,
+    count_region,
     getcode,
     scaled_F,
     fht_votes,

@@ -265,3 +265,23 @@ done:
     free(px); free(py); free(pool); free(lists);
     return rc;
 }
+
+/*
+ * Direct vote count of one region: the number of points whose line has a code
+ * other than 0000 and 1111 for region (i0, j0, S) of the given half, counted
+ * over all n points with no hierarchy.  Used to check single cells of
+ * full-size results.
+ */
+int64_t oracle_count_region(const int16_t *xy, int64_t n, int32_t W, int32_t H, int32_t depth, int32_t half,
+                            int64_t i0, int64_t j0, int64_t S)
+{
+    const int64_t L = oracle_frame_side(W, H);
+    int64_t cnt = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        const int32_t x = half == 0 ? xy[2 * k] : xy[2 * k + 1];
+        const int32_t y = half == 0 ? xy[2 * k + 1] : xy[2 * k];
+        const uint32_t code = oracle_getcode(x, y, i0, j0, S, L, depth);
+        if (code != 0u && code != 15u) ++cnt;
+    }
+    return cnt;
+}

@@ -69,6 +69,9 @@ def _load():
             lib.oracle_fht_votes.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
                                              ctypes.c_int64, ctypes.c_int64, ctypes.c_int32]
             lib.oracle_fht_votes.restype = ctypes.c_int
+            lib.oracle_count_region.argtypes = [i16p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
+            lib.oracle_count_region.restype = ctypes.c_int64
             lib.oracle_frame_side.argtypes = [ctypes.c_int32, ctypes.c_int32]
             lib.oracle_frame_side.restype = ctypes.c_int64
             _lib = lib
@@ -103,6 +106,13 @@ def getcode(x: int, y: int, i0: int, j0: int, S: int, L: int, D: int) -> int:
 
 def fht_votes(x: int, y: int, i0: int, j0: int, S: int, L: int, D: int) -> bool:
     return bool(_load().oracle_fht_votes(x, y, i0, j0, S, L, D))
+
+
+def count_region(points: np.ndarray, W: int, H: int, depth: int, half: int, i0: int, j0: int, S: int) -> int:
+    """Votes of one region counted directly over all points (no hierarchy)."""
+    pts = np.ascontiguousarray(np.asarray(points, dtype=np.int16).reshape(-1, 2))
+    return int(_load().oracle_count_region(pts.ctypes.data_as(ctypes.POINTER(ctypes.c_int16)), pts.shape[0],
+                                           W, H, depth, half, i0, j0, S))
 
 
 def detect(points: np.ndarray, W: int, H: int, depth: int, T: int, mode: str = "exact",

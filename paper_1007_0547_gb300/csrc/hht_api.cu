@@ -1,0 +1,539 @@
+// C ABI of libhht.so (declared in include/hht.h): contexts, device memory,
+// and the level loop that drives the stage / select / pass kernels.
+//
+// A job is a set of images; each image contributes two units (its two
+// halves).  All units of a job advance level by level through the same
+// launches: select(s) turns the level-s vote counters into passed regions or
+// leaves, pass(s) reads the level-(s-1) voter stream once and produces the
+// level-s stream and the level-(s+1) counters.  Buffers are sized exactly
+// from the per-level totals that select() writes; a batch that does not fit
+// the memory budget is split into waves.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/hht.h"
+#include "hht_internal.h"
+#include "hht_serve.h"
+
+using namespace hht;
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+int ceil_log2_i(int v) {
+    int e = 0;
+    while ((1 << e) < v) ++e;
+    return e;
+}
+
+}  // namespace
+
+struct hht_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    uint64_t budget = 0;
+    uint64_t held = 0;
+    int num_sms = 0;
+    int occ_select = 1, occ_pass32 = 1, occ_pass64 = 1;
+
+    // job buffers
+    DevBuf pts, img_start, img_unit, units, stats, infos, status, leaf_total, img_err, scan_states;
+    DevBuf rec[2], link[2], cnt[2], vox[2];
+    DevBuf leaves, leaves_tmp, sort_scratch;
+    DevBuf sel_flags, sel_data, pass_flags, pass_data;
+    // host staging
+    std::vector<uint64_t> h_stats;
+    std::vector<LevelInfo> h_infos;
+    std::vector<uint32_t> h_img_err;
+
+    hht::ServeState* serve = nullptr;
+    std::mutex mu;
+};
+
+namespace {
+
+int cuda_fail(cudaError_t e) {
+    if (e == cudaErrorMemoryAllocation) return HHT_E_NOMEM;
+    return HHT_E_CUDA;
+}
+
+// Grow a device buffer to at least `bytes` (contents are not preserved).
+int ensure(hht_ctx* c, DevBuf& b, size_t bytes, bool zero = false) {
+    if (bytes <= b.bytes && b.p) return HHT_OK;
+    size_t want = std::max<size_t>(bytes, b.bytes + b.bytes / 4);
+    want = (want + 4095) & ~size_t(4095);
+    if (want < 4096) want = 4096;
+    if (c->budget && c->held - b.bytes + want > c->budget) {
+        want = bytes;
+        if (c->held - b.bytes + want > c->budget) return HHT_E_NOMEM;
+    }
+    if (b.p) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(b.p);
+        c->held -= b.bytes;
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return HHT_E_NOMEM;
+    }
+    b.p = p;
+    b.bytes = want;
+    c->held += want;
+    if (zero) {
+        e = cudaMemsetAsync(p, 0, want, c->stream);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return HHT_OK;
+}
+
+// Grow a device buffer keeping its first `keep` bytes.
+int ensure_keep(hht_ctx* c, DevBuf& b, size_t bytes, size_t keep) {
+    if (bytes <= b.bytes && b.p) return HHT_OK;
+    if (!b.p || keep == 0) return ensure(c, b, bytes);
+    size_t want = std::max<size_t>(bytes, b.bytes + b.bytes / 2);
+    want = (want + 4095) & ~size_t(4095);
+    if (c->budget && c->held + want > c->budget) {
+        want = bytes;
+        if (c->held + want > c->budget) return HHT_E_NOMEM;
+    }
+    void* p = nullptr;
+    if (cudaMalloc(&p, want) != cudaSuccess) {
+        cudaGetLastError();
+        return HHT_E_NOMEM;
+    }
+    c->held += want;
+    cudaError_t e = cudaMemcpyAsync(p, b.p, std::min(keep, b.bytes), cudaMemcpyDeviceToDevice, c->stream);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(b.p);
+    c->held -= b.bytes;
+    b.p = p;
+    b.bytes = want;
+    return e == cudaSuccess ? HHT_OK : cuda_fail(e);
+}
+
+void release(hht_ctx* c, DevBuf& b) {
+    if (b.p) {
+        cudaFree(b.p);
+        c->held -= b.bytes;
+    }
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+int check_image(const hht_image& im) {
+    if (im.n < 0 || im.n > INT32_MAX) return HHT_E_ARG;
+    if (im.n > 0 && !im.points) return HHT_E_ARG;
+    if (im.W < 1 || im.H < 1 || im.W > HHT_MAX_SIDE || im.H > HHT_MAX_SIDE) return HHT_E_ARG;
+    if (im.depth < 1 || im.depth > HHT_MAX_DEPTH) return HHT_E_ARG;
+    if (im.T < 1) return HHT_E_ARG;
+    return HHT_OK;
+}
+
+constexpr int kSelTile = 1024;   // parents per select tile
+constexpr int kPassTile = 2048;  // voters per pass tile
+
+#define CK(call)                                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return cuda_fail(e_); \
+    } while (0)
+#define RK(call)                     \
+    do {                             \
+        int r_ = (call);             \
+        if (r_ != HHT_OK) return r_; \
+    } while (0)
+
+// Run one wave of images through the level loop; fills outs[k] for k in
+// [0, count).  Returns HHT_OK or a job-level error (per-image errors are in
+// outs[k].status).
+int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs) {
+    cudaStream_t st = c->stream;
+    const int n_units = 2 * count;
+    int Dmax = 0;
+    bool i64 = false;
+    uint64_t total = 0, v0_len = 0;
+    std::vector<Unit> units(n_units);
+    std::vector<uint64_t> img_start(count + 1);
+    for (int g = 0; g < count; ++g) {
+        const int lL = ceil_log2_i(std::max(im[g].W, im[g].H));
+        Dmax = std::max(Dmax, im[g].depth);
+        if (lL + im[g].depth > 27) i64 = true;  // int32 corner arithmetic is exact only below this
+        img_start[g] = total;
+        for (int h = 0; h < 2; ++h) {
+            Unit& U = units[2 * g + h];
+            U.lL = lL;
+            U.D = im[g].depth;
+            U.T = im[g].T;
+            U.image = g;
+            U.n = im[g].n;
+            U.W = im[g].W;
+            U.H = im[g].H;
+            U.half = h;
+            U.t0 = 0;
+            U.root_rec = (uint32_t)(2 * g + h);
+            U.pad = 0;
+            U.pad2 = 0;
+            U.v0_off = v0_len;
+            if (U.D >= 2) v0_len += (uint64_t)im[g].n;
+        }
+        total += (uint64_t)im[g].n;
+    }
+    img_start[count] = total;
+
+    // ---- inputs and job state
+    RK(ensure(c, c->pts, std::max<uint64_t>(total, 1) * sizeof(hht_point)));
+    for (int g = 0; g < count; ++g)
+        if (im[g].n > 0)
+            CK(cudaMemcpyAsync((char*)c->pts.p + img_start[g] * sizeof(hht_point), im[g].points,
+                               (size_t)im[g].n * sizeof(hht_point), cudaMemcpyDefault, st));
+    RK(ensure(c, c->units, n_units * sizeof(Unit)));
+    RK(ensure(c, c->img_start, (count + 1) * sizeof(uint64_t)));
+    RK(ensure(c, c->img_unit, count * sizeof(uint32_t)));
+    std::vector<uint32_t> img_unit(count);
+    for (int g = 0; g < count; ++g) img_unit[g] = (uint32_t)(2 * g);
+    RK(ensure(c, c->img_err, count * sizeof(uint32_t)));
+    const size_t stats_words = (size_t)n_units * (kMaxDepth + 1) * 4;
+    RK(ensure(c, c->stats, stats_words * sizeof(uint64_t)));
+    RK(ensure(c, c->infos, (kMaxDepth + 1) * sizeof(LevelInfo)));
+    RK(ensure(c, c->status, sizeof(DeviceStatus)));
+    RK(ensure(c, c->leaf_total, sizeof(uint64_t)));
+
+    c->h_stats.assign(stats_words, 0);
+    for (int u = 0; u < n_units; ++u) {
+        uint64_t* s0 = &c->h_stats[(size_t)u * (kMaxDepth + 1) * 4];
+        s0[0] = 1;                       // level 0: one region tested
+        s0[1] = 1;                       // ... and always split
+        s0[3] = (uint64_t)units[u].n;    // one code per point
+    }
+    c->h_infos.assign(kMaxDepth + 1, LevelInfo{});
+    c->h_infos[0].n_regions = (uint64_t)n_units;
+    c->h_infos[0].n_voters = v0_len;
+    std::vector<Region> roots(n_units);
+    for (int u = 0; u < n_units; ++u) roots[u] = Region{(uint32_t)u, 0u, 0u, (uint32_t)units[u].n};
+
+    RK(ensure(c, c->rec[0], n_units * sizeof(Region)));
+    RK(ensure(c, c->cnt[0], n_units * 4 * sizeof(uint32_t)));
+    RK(ensure(c, c->vox[0], std::max<uint64_t>(v0_len, 1) * sizeof(Voter)));
+    CK(cudaMemcpyAsync(c->units.p, units.data(), n_units * sizeof(Unit), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->img_start.p, img_start.data(), (count + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->img_unit.p, img_unit.data(), count * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->stats.p, c->h_stats.data(), stats_words * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->infos.p, c->h_infos.data(), (kMaxDepth + 1) * sizeof(LevelInfo), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->rec[0].p, roots.data(), n_units * sizeof(Region), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(c->cnt[0].p, 0, n_units * 4 * sizeof(uint32_t), st));
+    CK(cudaMemsetAsync(c->status.p, 0, sizeof(DeviceStatus), st));
+    CK(cudaMemsetAsync(c->leaf_total.p, 0, sizeof(uint64_t), st));
+    CK(cudaMemsetAsync(c->img_err.p, 0, count * sizeof(uint32_t), st));
+
+    LevelInfo* d_infos = (LevelInfo*)c->infos.p;
+    DeviceStatus* d_status = (DeviceStatus*)c->status.p;
+    ScanState* d_scan = (ScanState*)c->scan_states.p;
+
+    if (launch_stage((const int16_t*)c->pts.p, total, (const Unit*)c->units.p, count, (const uint64_t*)c->img_start.p,
+                     (const uint32_t*)c->img_unit.p, (Voter*)c->vox[0].p, (uint32_t*)c->cnt[0].p,
+                     (uint64_t*)c->stats.p, (uint32_t*)c->img_err.p, d_status, i64, st) != 0)
+        return HHT_E_CUDA;
+
+    // ---- level loop
+    uint64_t leaf_total = 0;
+    uint32_t err = 0;
+    for (int s = 1; s <= Dmax; ++s) {
+        const int pi = (s - 1) & 1, ci = s & 1;
+        const uint64_t P = c->h_infos[s - 1].n_regions;
+        if (P == 0) break;
+        RK(ensure(c, c->link[pi], P * sizeof(RegionLink)));
+        RK(ensure(c, c->rec[ci], 4 * P * sizeof(Region)));
+        RK(ensure(c, c->cnt[ci], 4 * P * 4 * sizeof(uint32_t)));
+        const uint64_t cap_leaves = leaf_total + 4 * P;
+        RK(ensure_keep(c, c->leaves, cap_leaves * sizeof(DevLeaf), leaf_total * sizeof(DevLeaf)));
+        const uint64_t sel_tiles = (P + kSelTile - 1) / kSelTile;
+        if ((sel_tiles + 1) * 4 > c->sel_flags.bytes) {
+            RK(ensure(c, c->sel_flags, (sel_tiles + 1) * 4, true));
+        }
+        RK(ensure(c, c->sel_data, (sel_tiles + 1) * 2 * 2 * sizeof(uint64_t)));
+
+        LevelArgs a{};
+        a.units = (const Unit*)c->units.p;
+        a.parents = (const Region*)c->rec[pi].p;
+        a.links = (RegionLink*)c->link[pi].p;
+        a.parent_cnt = (const uint32_t*)c->cnt[pi].p;
+        a.children = (Region*)c->rec[ci].p;
+        a.child_cnt = (uint32_t*)c->cnt[ci].p;
+        a.leaves = (DevLeaf*)c->leaves.p;
+        a.stats = (uint64_t*)c->stats.p;
+        a.info_prev = d_infos + (s - 1);
+        a.info = d_infos + s;
+        a.leaf_total = (uint64_t*)c->leaf_total.p;
+        a.status = d_status;
+        a.cap_children = 4 * P;
+        a.cap_leaves = cap_leaves;
+        a.cap_voters = c->vox[ci].bytes / sizeof(Voter);
+        a.level = s;
+        a.num_sms = c->num_sms;
+        a.scan = d_scan + 0;
+        a.tile_flags = (uint32_t*)c->sel_flags.p;
+        a.tile_data = (uint64_t*)c->sel_data.p;
+        a.cap_tiles = sel_tiles;
+        const int sel_grid = (int)std::min<uint64_t>(sel_tiles, (uint64_t)c->num_sms * c->occ_select);
+        // select's capacity test on the voter stream is re-done below with the exact size
+        a.cap_voters = UINT64_MAX;
+        if (launch_select(a, 256, std::max(sel_grid, 1), st) != 0) return HHT_E_CUDA;
+
+        CK(cudaMemcpyAsync(&c->h_infos[s], d_infos + s, sizeof(LevelInfo), cudaMemcpyDeviceToHost, st));
+        DeviceStatus hs{};
+        CK(cudaMemcpyAsync(&hs, d_status, sizeof hs, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        err = hs.err;
+        if (err) break;
+        leaf_total += c->h_infos[s].n_leaves;
+        if (s == Dmax) break;
+
+        const uint64_t nin = c->h_infos[s - 1].n_voters;
+        if (nin == 0) continue;  // no unit needs level s+1 counts
+        const uint64_t nout = c->h_infos[s].n_voters;
+        RK(ensure(c, c->vox[ci], std::max<uint64_t>(nout, 1) * sizeof(Voter)));
+        const uint64_t pass_tiles = (nin + kPassTile - 1) / kPassTile;
+        if ((pass_tiles + 1) * 4 > c->pass_flags.bytes) {
+            RK(ensure(c, c->pass_flags, (pass_tiles + 1) * 4, true));
+        }
+        RK(ensure(c, c->pass_data, (pass_tiles + 1) * 2 * 4 * sizeof(uint64_t)));
+        a.vin = (const Voter*)c->vox[pi].p;
+        a.vout = (Voter*)c->vox[ci].p;
+        a.cap_voters = nout;
+        a.scan = d_scan + 1;
+        a.tile_flags = (uint32_t*)c->pass_flags.p;
+        a.tile_data = (uint64_t*)c->pass_data.p;
+        a.cap_tiles = pass_tiles;
+        const int occ = i64 ? c->occ_pass64 : c->occ_pass32;
+        const int pass_grid = (int)std::min<uint64_t>(pass_tiles, (uint64_t)c->num_sms * occ);
+        if (launch_pass(a, i64, std::max(pass_grid, 1), st) != 0) return HHT_E_CUDA;
+    }
+
+    // ---- outputs
+    CK(cudaMemcpyAsync(c->h_stats.data(), c->stats.p, stats_words * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    c->h_img_err.assign(count, 0);
+    CK(cudaMemcpyAsync(c->h_img_err.data(), c->img_err.p, count * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    DeviceStatus hs{};
+    CK(cudaMemcpyAsync(&hs, d_status, sizeof hs, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    err |= hs.err;
+    if (err & kErrTimeout) return HHT_E_TIMEOUT;
+    if (err & kErrOverflow) return HHT_E_NOMEM;
+    if (err & kErrInvariant) return HHT_E_CUDA;
+
+    if (leaf_total > 1) {
+        RK(ensure(c, c->leaves_tmp, leaf_total * sizeof(DevLeaf)));
+        RK(ensure(c, c->sort_scratch, sort_scratch_bytes(leaf_total)));
+        const int unit_bits = ceil_log2_i(n_units);
+        if (launch_leaf_sort((DevLeaf*)c->leaves.p, (DevLeaf*)c->leaves_tmp.p, leaf_total, unit_bits, Dmax,
+                             c->sort_scratch.p, c->sort_scratch.bytes, d_status, c->num_sms, st) != 0)
+            return HHT_E_CUDA;
+    }
+    // leaves of image g are the contiguous block of units 2g, 2g+1 (sorted by
+    // unit); a leaf's half is its unit's parity
+    if (leaf_total > 0 && launch_unit_to_half(c->leaves.p, leaf_total, st) != 0) return HHT_E_CUDA;
+    uint64_t off = 0;
+    for (int g = 0; g < count; ++g) {
+        hht_result& r = outs[g];
+        const int D = im[g].depth;
+        r.depth = D;
+        r.L = 1 << ceil_log2_i(std::max(im[g].W, im[g].H));
+        std::memset(r.stats, 0, sizeof r.stats);
+        uint64_t nl = 0;
+        for (int h = 0; h < 2; ++h) {
+            const uint64_t* su = &c->h_stats[(size_t)(2 * g + h) * (kMaxDepth + 1) * 4];
+            for (int l = 0; l <= D; ++l) {
+                r.stats[h][l].tested = su[4 * l + 0];
+                r.stats[h][l].passed = su[4 * l + 1];
+                r.stats[h][l].votes = su[4 * l + 2];
+                r.stats[h][l].tests = su[4 * l + 3];
+            }
+            nl += su[4 * D + 1];
+        }
+        r.n_leaves = nl;
+        if (c->h_img_err[g]) {
+            r.status = HHT_E_RANGE;
+        } else if (nl > r.leaf_capacity || (nl > 0 && !r.leaves)) {
+            r.status = HHT_E_CAPACITY;
+        } else {
+            r.status = HHT_OK;
+            if (nl > 0) {
+                CK(cudaMemcpyAsync(r.leaves, (const char*)c->leaves.p + off * sizeof(DevLeaf), nl * sizeof(hht_leaf),
+                                   cudaMemcpyDefault, st));
+            }
+        }
+        off += nl;
+    }
+    if (off != leaf_total) return HHT_E_CUDA;
+    CK(cudaStreamSynchronize(st));
+    return HHT_OK;
+}
+
+// Upper estimate of a wave member's peak device bytes (two voter streams of
+// the two deepest written levels, both halves, dense regime).
+uint64_t estimate_bytes(const hht_image& im) {
+    const double n = (double)im.n;
+    const int D = im.depth;
+    if (D < 3) return (uint64_t)(64.0 * n + 4096);
+    const double dense = 1.25 * n * (std::ldexp(1.0, D - 2) + std::ldexp(1.0, D - 3));
+    return (uint64_t)(2.0 * 8.0 * dense * 1.2 + 64.0 * n + 4096);
+}
+
+int run_job(hht_ctx* c, const hht_image* im, int count, hht_result* outs) {
+    // wave split by the memory budget (or 80% of the free device memory)
+    uint64_t budget = c->budget;
+    if (!budget) {
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        budget = (uint64_t)((double)(fr + c->held) * 0.8);
+    }
+    int first = 0;
+    int rc_all = HHT_OK;
+    while (first < count) {
+        int last = first;
+        uint64_t acc = 0;
+        while (last < count) {
+            const uint64_t e = estimate_bytes(im[last]);
+            if (last > first && acc + e > budget) break;
+            acc += e;
+            ++last;
+        }
+        int rc = run_wave(c, im + first, last - first, outs + first);
+        if (rc == HHT_E_NOMEM && last - first > 1) {
+            // split the wave and retry each half
+            const int mid = first + (last - first) / 2;
+            rc = run_job(c, im + first, mid - first, outs + first);
+            if (rc == HHT_OK) rc = run_job(c, im + mid, last - mid, outs + mid);
+        }
+        if (rc != HHT_OK) {
+            for (int g = first; g < last; ++g) outs[g].status = rc;
+            return rc;
+        }
+        for (int g = first; g < last; ++g)
+            if (outs[g].status != HHT_OK && rc_all == HHT_OK) rc_all = outs[g].status;
+        first = last;
+    }
+    return rc_all;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+extern "C" {
+
+int hht_create(hht_ctx** out, int device, void* cuda_stream, uint64_t mem_budget_bytes) {
+    if (!out) return HHT_E_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+        cudaGetLastError();
+        return HHT_E_CUDA;
+    }
+    if (device < 0 || device >= ndev) return HHT_E_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) return HHT_E_CUDA;
+    hht_ctx* c = new (std::nothrow) hht_ctx();
+    if (!c) return HHT_E_NOMEM;
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->budget = mem_budget_bytes;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    c->occ_select = occupancy_select();
+    c->occ_pass32 = occupancy_pass(false);
+    c->occ_pass64 = occupancy_pass(true);
+    int rc = ensure(c, c->scan_states, 8 * sizeof(ScanState), true);
+    if (rc == HHT_OK) {
+        std::vector<ScanState> init(8, ScanState{0u, 0u, 1u, 0u});
+        if (cudaMemcpyAsync(c->scan_states.p, init.data(), 8 * sizeof(ScanState), cudaMemcpyHostToDevice, c->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess)
+            rc = HHT_E_CUDA;
+    }
+    if (rc != HHT_OK) {
+        hht_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return HHT_OK;
+}
+
+void hht_destroy(hht_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    hht::serve_destroy(c->serve);
+    DevBuf* all[] = {&c->pts,       &c->img_start,  &c->img_unit, &c->units,        &c->stats,     &c->infos,      &c->status,
+                     &c->leaf_total, &c->img_err,   &c->scan_states,  &c->rec[0],    &c->rec[1],     &c->link[0],
+                     &c->link[1],   &c->cnt[0],     &c->cnt[1],       &c->vox[0],    &c->vox[1],     &c->leaves,
+                     &c->leaves_tmp, &c->sort_scratch, &c->sel_flags, &c->sel_data,  &c->pass_flags, &c->pass_data};
+    for (DevBuf* b : all) release(c, *b);
+    delete c;
+}
+
+int hht_detect(hht_ctx* c, const hht_point* points, int64_t n, int32_t W, int32_t H, int32_t depth, int32_t T,
+               hht_result* out) {
+    if (!c || !out) return HHT_E_ARG;
+    hht_image im{points, n, W, H, depth, T};
+    int rc = check_image(im);
+    if (rc != HHT_OK) return rc;
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    rc = run_job(c, &im, 1, out);
+    if (rc != HHT_OK) return rc;
+    return out->status;
+}
+
+int hht_detect_batch(hht_ctx* c, const hht_image* images, int32_t count, hht_result* outs) {
+    if (!c || !outs || count < 0 || (count > 0 && !images)) return HHT_E_ARG;
+    if (count == 0) return HHT_OK;
+    if (count > (1 << 20)) return HHT_E_ARG;
+    for (int g = 0; g < count; ++g) {
+        const int rc = check_image(images[g]);
+        if (rc != HHT_OK) return rc;
+    }
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    return run_job(c, images, count, outs);
+}
+
+const char* hht_strerror(int code) {
+    switch (code) {
+        case HHT_OK: return "ok";
+        case HHT_E_ARG: return "invalid argument";
+        case HHT_E_RANGE: return "point outside the image";
+        case HHT_E_CAPACITY: return "leaf buffer too small";
+        case HHT_E_NOMEM: return "out of device memory or budget";
+        case HHT_E_TIMEOUT: return "bounded device wait expired";
+        case HHT_E_CUDA: return "CUDA runtime error";
+        case HHT_E_PENDING: return "request pending";
+        case HHT_E_UNKNOWN_TICKET: return "unknown ticket";
+        default: return "unknown error";
+    }
+}
+
+const char* hht_version(void) { return "hht 0.1 (sm_103a, level-synchronous stage/select/pass)"; }
+
+}  // extern "C"
+
+// Internal entry used by the serving loop.
+int hht_internal_run_job(hht_ctx* c, const hht_image* im, int count, hht_result* outs) {
+    return run_job(c, im, count, outs);
+}
+
+hht::ServeState** hht_internal_serve_slot(hht_ctx* c) { return &c->serve; }

@@ -1,0 +1,204 @@
+// Device helpers: exact corner-sign grids, bit-sliced 4-bit codes, single-pass
+// scan state (decoupled look-back) with bounded waits, warp reductions.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "hht_internal.h"
+
+namespace hht {
+
+// ----------------------------------------------------------------- memory-model helpers
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// ----------------------------------------------------------------- corner signs and codes
+//
+// For one line and one region, the corner vertices of an N x N sub-grid
+// (N = 3: the region's four children; N = 5: also its sixteen grandchildren)
+// are classified exactly.  Along a column of the sub-grid, G grows by the
+// positive power of two dJ = 2^k per step, so the number of vertices with
+// G < 0 in that column is t = ceil(-G_column_base / dJ) clamped to [0, N],
+// an exact shift.  The result is an N*N-bit mask M with bit (alpha*N + beta)
+// set when vertex (column alpha, row beta) lies strictly below the line.
+template <typename I, int N>
+__device__ __forceinline__ uint32_t below_mask(I G0, I dI, int k) {
+    const I dJm1 = (I(1) << k) - I(1);
+    uint32_t M = 0;
+    I G = G0;
+#pragma unroll
+    for (int alpha = 0; alpha < N; ++alpha) {
+        I t = (dJm1 - G) >> k;  // floor((-G + dJ - 1) / dJ) = ceil(-G / dJ)
+        t = t < I(0) ? I(0) : (t > I(N) ? I(N) : t);
+        M |= ((1u << static_cast<int>(t)) - 1u) << (N * alpha);
+        G += dI;
+    }
+    return M;
+}
+
+// Bit-sliced 4-bit codes: for cells of side `sz` sub-grid steps, the word
+// `M >> (sz*N + sz)` holds at bit (alpha*N + beta) the NE-corner bit of the
+// cell whose SW corner is vertex (alpha, beta); likewise NW (>> sz),
+// SW (>> 0) and SE (>> sz*N).  A line votes for a cell when the cell's code
+// is neither 0000 nor 1111: some corner bit set and not all four.
+template <int N, int sz>
+__device__ __forceinline__ uint32_t crossing_cells(uint32_t M) {
+    const uint32_t ne = M >> (sz * N + sz), nw = M >> sz, sw = M, se = M >> (sz * N);
+    const uint32_t any = ne | nw | sw | se;
+    const uint32_t all = ne & nw & sw & se;
+    return any & ~all;
+}
+
+// Quadrant index of (east, north) halves: NE = 0, NW = 1, SW = 2, SE = 3.
+__device__ __forceinline__ int quad_of(int east, int north) {
+    return north ? (east ? NE : NW) : (east ? SE : SW);
+}
+
+// Child votes (bit q = quadrant q) from a 5 x 5 below-mask: children are the
+// 2 x 2 step cells with SW corners NE (2,2), NW (0,2), SW (0,0), SE (2,0).
+__device__ __forceinline__ uint32_t child_votes5(uint32_t M) {
+    const uint32_t v = crossing_cells<5, 2>(M);
+    return ((v >> 12) & 1u) | (((v >> 2) & 1u) << 1) | ((v & 1u) << 2) | (((v >> 10) & 1u) << 3);
+}
+// Same for a 3 x 3 below-mask (children are 1 x 1 step cells).
+__device__ __forceinline__ uint32_t child_votes3(uint32_t M) {
+    const uint32_t v = crossing_cells<3, 1>(M);
+    return ((v >> 4) & 1u) | (((v >> 1) & 1u) << 1) | ((v & 1u) << 2) | (((v >> 3) & 1u) << 3);
+}
+// Code of the whole region from a 3 x 3 mask: NE, NW, SW, SE corners are the
+// vertices (2,2), (0,2), (0,0), (2,0), i.e. bits 8, 2, 0, 6 (NE is the code's
+// leftmost bit).
+__device__ __forceinline__ uint32_t region_code3(uint32_t M) {
+    return (((M >> 8) & 1u) << 3) | (((M >> 2) & 1u) << 2) | (((M >> 0) & 1u) << 1) | ((M >> 6) & 1u);
+}
+
+// Grandchild cells (1 x 1 steps of the 5 x 5 grid, bits alpha*5 + beta with
+// alpha, beta < 4) that lie inside the children whose bit is set in `kids`.
+__device__ __forceinline__ uint32_t grandchild_mask(uint32_t kids) {
+    uint32_t m = 0;
+    m |= (kids & (1u << NE)) ? 0x63000u : 0u;  // alpha, beta in {2, 3}
+    m |= (kids & (1u << NW)) ? 0x0018Cu : 0u;  // alpha in {0, 1}, beta in {2, 3}
+    m |= (kids & (1u << SW)) ? 0x00063u : 0u;  // alpha, beta in {0, 1}
+    m |= (kids & (1u << SE)) ? 0x18C00u : 0u;  // alpha in {2, 3}, beta in {0, 1}
+    return m;
+}
+
+// Spread 4 bits into the low bit of 4 bytes (bit b -> byte b).
+__device__ __forceinline__ uint32_t spread4(uint32_t r) { return (r * 0x204081u) & 0x01010101u; }
+
+// ----------------------------------------------------------------- bounded spin
+constexpr uint32_t kSpinLimit = 1u << 22;  // ~0.5-1 s with the back-off below
+
+// ----------------------------------------------------------------- look-back scan
+// Per tile: flag word (epoch << 2 | state), state 1 = aggregate published,
+// 2 = inclusive prefix published; data[tile * 2C + c] = aggregate,
+// data[tile * 2C + C + c] = inclusive.  Called by all 32 lanes of one warp;
+// returns the exclusive prefix of tile t (identical in every lane).
+template <int C>
+__device__ void tile_lookback(uint32_t* flags, uint64_t* data, uint32_t t, uint32_t epoch, const uint64_t (&agg)[C],
+                              uint64_t (&prefix)[C], DeviceStatus* status) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < C; ++c) prefix[c] = 0;
+    if (t == 0) {
+        if (lane == 0) {
+#pragma unroll
+            for (int c = 0; c < C; ++c) st_relaxed_u64(&data[(size_t)t * 2 * C + C + c], agg[c]);
+            st_release_u32(&flags[t], (epoch << 2) | 2u);
+        }
+        return;
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) st_relaxed_u64(&data[(size_t)t * 2 * C + c], agg[c]);
+        st_release_u32(&flags[t], (epoch << 2) | 1u);
+    }
+    int64_t top = (int64_t)t - 1;
+    // once any wait of this job has expired, no further wait is started
+    bool timed_out = (*reinterpret_cast<volatile uint32_t*>(&status->err) & kErrTimeout) != 0u;
+    while (true) {
+        const int64_t idx = top - lane;
+        uint32_t state = 2;  // before tile 0: an inclusive prefix of zero
+        if (idx >= 0) {
+            uint32_t f = 0;
+            uint32_t spins = 0;
+            while (true) {
+                f = ld_acquire_u32(&flags[idx]);
+                if ((f >> 2) == epoch && (f & 3u) != 0) break;
+                if (timed_out || ++spins > kSpinLimit) {
+                    timed_out = true;
+                    f = (epoch << 2) | 1u;  // treat as an empty aggregate; the job is reported failed
+                    break;
+                }
+                if (spins > 64) __nanosleep(spins > 4096 ? 256 : 32);
+            }
+            state = f & 3u;
+        }
+        timed_out = __any_sync(0xffffffffu, timed_out);
+        const uint32_t inc = __ballot_sync(0xffffffffu, state == 2u);
+        const int first = inc ? (__ffs(inc) - 1) : 32;
+        uint64_t v[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            v[c] = 0;
+            if (idx >= 0 && lane <= first) {
+                const bool use_inc = (lane == first);
+                v[c] = timed_out ? 0 : ld_relaxed_u64(&data[(size_t)idx * 2 * C + (use_inc ? C : 0) + c]);
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], off);
+            prefix[c] += v[c];
+        }
+        if (inc) break;
+        top -= 32;
+    }
+    if (__any_sync(0xffffffffu, timed_out) && lane == 0) atomicOr(&status->err, kErrTimeout);
+    if (lane == 0) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) st_relaxed_u64(&data[(size_t)t * 2 * C + C + c], prefix[c] + agg[c]);
+        st_release_u32(&flags[t], (epoch << 2) | 2u);
+    }
+}
+
+// End-of-launch protocol for a scan: the last block to finish resets the tile
+// counter and advances the epoch.  Returns true in thread 0 of the last block.
+__device__ __forceinline__ bool scan_finish(ScanState* st) {
+    __syncthreads();
+    bool last = false;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const uint32_t d = atomicAdd(&st->done_counter, 1u);
+        if (d == gridDim.x - 1) {
+            st->tile_counter = 0;
+            st->done_counter = 0;
+            st->epoch = st->epoch + 1u;
+            __threadfence();
+            last = true;
+        }
+    }
+    return last;
+}
+
+__device__ __forceinline__ uint32_t claim_tile(ScanState* st, uint32_t* s_slot) {
+    __syncthreads();
+    if (threadIdx.x == 0) *s_slot = atomicAdd(&st->tile_counter, 1u);
+    __syncthreads();
+    return *s_slot;
+}
+
+}  // namespace hht

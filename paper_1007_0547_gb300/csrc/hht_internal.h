@@ -1,0 +1,154 @@
+// Internal layouts shared by the kernels (hht_kernels.cu, hht_sort.cu) and the
+// host orchestration (hht_api.cu).  Nothing here is part of the public ABI.
+//
+// Geometry (the paper's Sections 2-3, on a dyadic grid).  A unit is one half
+// (0 = points as given, 1 = x/y swapped) of one image.  With L = 2^lL the
+// smallest power of two >= max(W, H) and K = 2^D the number of leaf cells per
+// side, grid vertex (i, j) is the parameter point m_i = -1 + 2i/K,
+// b_j = -2L + 4Lj/K.  For edge point (x, y) of the unit,
+//     G(i, j) = K * (b_j + x*m_i - y) = 4L*j + 2x*i - 2LK - K*x - K*y
+// is K times F = y0 - m*x0 - b of Section 2 evaluated at that vertex for the
+// parameter-space line of slope -x and intercept y; a vertex is "below" the
+// line exactly when G < 0.  A region at level l is the square of side
+// S = K >> l cells with lower-left vertex (a*S, b*S), (a, b) in [0, 2^l)^2.
+#pragma once
+
+#include <cstdint>
+
+namespace hht {
+
+constexpr int kMaxDepth = 24;
+
+// Quadrant order of the paper's quad1..quad4.
+enum Quad : int { NE = 0, NW = 1, SW = 2, SE = 3 };
+
+// One (image, half) of a job.  Units advance one level per step of the level
+// loop; a unit that joined at step t0 is at level (step - t0), so requests can
+// join a running loop (continuous batching) without changing the kernels.
+struct Unit {
+    int32_t lL;        // log2 of the frame side L
+    int32_t D;         // depth (leaf level)
+    int32_t T;         // threshold: a region passes when votes >= T
+    int32_t image;     // caller's image index
+    int64_t n;         // points of the image
+    uint64_t v0_off;   // offset of this unit's level-0 voters in the stream of step t0 (if D >= 2)
+    int32_t W, H;      // image size (range check)
+    int32_t half;      // 0: (x, y); 1: (y, x)
+    int32_t t0;        // loop step at which the unit's level 0 is current
+    uint32_t root_rec; // record index of the unit's level-0 region at step t0
+    uint32_t pad;
+    uint64_t pad2;
+};
+static_assert(sizeof(Unit) == 64, "unit record is 64 bytes");
+
+// Voter record: the (half-swapped) point and the index of the region whose
+// voter list it belongs to.  Two records form one 16-byte vector load.
+struct Voter {
+    int16_t x, y;
+    uint32_t region;
+};
+static_assert(sizeof(Voter) == 8, "voter record is 8 bytes");
+
+// A region that passed (level-0 regions always do).
+struct Region {
+    uint32_t unit;
+    uint32_t a, b;     // cell indices at the region's level
+    uint32_t count;    // votes = length of its voter list
+};
+static_assert(sizeof(Region) == 16, "region record is 16 bytes");
+
+// Filled by the selection of the next level: where the region's passed
+// children are and which of them keep a voter list.
+struct RegionLink {
+    uint32_t child_base;  // index of the first passed child in the next level's records
+    uint8_t pass_mask;    // bit q: child q (NE, NW, SW, SE) reached T and is a region of the next level
+    uint8_t write_mask;   // bit q: child q's voters are copied to the next voter stream
+    uint16_t pad;
+};
+static_assert(sizeof(RegionLink) == 8, "link record is 8 bytes");
+
+// Leaf as produced on the device (before sorting): unit, cell, votes.
+struct DevLeaf {
+    uint32_t unit, i, j, votes;
+};
+
+// Per-level totals written by the selection kernel's last block.
+struct LevelInfo {
+    uint64_t n_regions;      // passed regions of this level (records)
+    uint64_t n_voters;       // length of this level's voter stream
+    uint64_t Q[4];           // start of each child quadrant's block in the next stream
+    uint64_t kept[4];        // voters copied per quadrant (reduction target)
+    uint64_t n_leaves;       // leaves emitted at this level
+    uint64_t n_records_acc;  // scan total helpers
+    uint64_t pad[4];
+};
+
+// State of one single-pass (decoupled look-back) scan: tile ids are claimed in
+// order with an atomic counter, and tile flags carry an epoch that the last
+// block of each launch advances, so no memset is needed between launches.
+struct ScanState {
+    uint32_t tile_counter;
+    uint32_t done_counter;
+    uint32_t epoch;
+    uint32_t pad;
+};
+
+// Status bits set on the device (checked by the host after a job).
+enum : uint32_t {
+    kErrRange = 1u,        // a point outside the image
+    kErrTimeout = 2u,      // a bounded wait expired
+    kErrOverflow = 4u,     // a capacity was exceeded (host re-runs with more memory)
+    kErrInvariant = 8u     // a line did not cross the level-0 region (cannot happen)
+};
+
+struct DeviceStatus {
+    uint32_t err;
+    uint32_t pad[3];
+};
+
+// Launch parameters of one step of the level loop (host -> kernels).  For
+// a unit that joined at step t0, the parents are its level (step - t0 - 1)
+// regions and the children its level (step - t0) regions.
+struct LevelArgs {
+    const Unit* units;
+    const Region* parents;     // records of level s-1
+    RegionLink* links;         // links of level s-1 (written by select, read by pass)
+    const uint32_t* parent_cnt;// [n_parents][4] vote counters of level-s children
+    Region* children;          // records of level s (written by select)
+    uint32_t* child_cnt;       // [n_children][4] counters of level s+1 (zeroed by select, filled by pass)
+    const Voter* vin;          // voter stream of level s-1
+    Voter* vout;               // voter stream of level s
+    DevLeaf* leaves;
+    uint64_t* stats;           // [n_units][kMaxDepth + 1][4]
+    LevelInfo* info_prev;      // level s-1
+    LevelInfo* info;           // level s
+    uint64_t* leaf_total;      // running leaf count
+    ScanState* scan;
+    uint32_t* tile_flags;
+    uint64_t* tile_data;       // per tile: aggregate[C], inclusive[C]
+    DeviceStatus* status;
+    uint64_t cap_children, cap_voters, cap_leaves, cap_tiles;
+    int32_t level;             // step of the level loop
+    int32_t num_sms;
+};
+
+// Kernel launchers (hht_kernels.cu).  All are asynchronous on `stream`.
+// Level 0 of the images [0, n_images) of `pts` (image g owns points
+// [img_start[g], img_start[g+1]) and the units img_unit[g], img_unit[g] + 1).
+int launch_stage(const int16_t* pts, uint64_t total_points, const Unit* units, int n_images,
+                 const uint64_t* img_start, const uint32_t* img_unit, Voter* vstream, uint32_t* cnt,
+                 uint64_t* stats, uint32_t* img_err, DeviceStatus* status, bool int64_path, void* stream);
+int launch_select(const LevelArgs& a, int threads_per_block, int grid, void* stream);
+int launch_pass(const LevelArgs& a, bool int64_path, int grid, void* stream);
+int occupancy_select();
+int occupancy_pass(bool int64_path);
+
+// Rewrite each leaf's unit (2 * image + half) to its half.
+int launch_unit_to_half(void* leaves, uint64_t n, void* stream);
+
+// Leaf sort (hht_sort.cu): stable LSD radix sort of leaves by (unit, i, j).
+size_t sort_scratch_bytes(uint64_t n);
+int launch_leaf_sort(DevLeaf* leaves, DevLeaf* tmp, uint64_t n, int unit_bits, int depth_bits,
+                     void* scratch, size_t scratch_bytes, DeviceStatus* status, int num_sms, void* stream);
+
+}  // namespace hht

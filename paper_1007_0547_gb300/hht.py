@@ -1,0 +1,293 @@
+"""Python binding of libhht.so (ctypes): argument marshalling only.
+
+Every step of the detection runs in the library's CUDA kernels; PyTorch is
+used here for device memory and the CUDA stream.  Importing this module
+builds nothing and falls back to nothing: when the compiled library is absent
+the import fails with an error that says how to build it.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhht.so")
+MAX_DEPTH = 24
+
+HHT_OK = 0
+HHT_E_ARG = -1
+HHT_E_RANGE = -2
+HHT_E_CAPACITY = -3
+HHT_E_NOMEM = -4
+HHT_E_TIMEOUT = -5
+HHT_E_CUDA = -6
+HHT_E_PENDING = -7
+HHT_E_UNKNOWN_TICKET = -8
+
+# every function the C header declares
+EXPORTS = ("hht_create", "hht_destroy", "hht_detect", "hht_detect_batch", "hht_submit", "hht_poll",
+           "hht_progress", "hht_strerror", "hht_version")
+
+
+class HhtError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})" if what else f"{strerror(code)} ({code})")
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("leaves", ctypes.c_void_p), ("leaf_capacity", ctypes.c_uint64), ("n_leaves", ctypes.c_uint64),
+                ("depth", ctypes.c_int32), ("L", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("stats", ctypes.c_uint64 * (2 * (MAX_DEPTH + 1) * 4))]
+
+
+class _Image(ctypes.Structure):
+    _fields_ = [("points", ctypes.c_void_p), ("n", ctypes.c_int64), ("W", ctypes.c_int32), ("H", ctypes.c_int32),
+                ("depth", ctypes.c_int32), ("T", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libhht.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_1007_0547_gb300.build` "
+                          "(needs nvcc); there is no CPU fallback")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+    lib.hht_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, u64]
+    lib.hht_create.restype = ctypes.c_int
+    lib.hht_destroy.argtypes = [vp]
+    lib.hht_destroy.restype = None
+    lib.hht_detect.argtypes = [vp, vp, i64, i32, i32, i32, i32, ctypes.POINTER(_Result)]
+    lib.hht_detect.restype = ctypes.c_int
+    lib.hht_detect_batch.argtypes = [vp, ctypes.POINTER(_Image), i32, ctypes.POINTER(_Result)]
+    lib.hht_detect_batch.restype = ctypes.c_int
+    lib.hht_submit.argtypes = [vp, ctypes.POINTER(_Image), ctypes.POINTER(u64)]
+    lib.hht_submit.restype = ctypes.c_int
+    lib.hht_poll.argtypes = [vp, u64, ctypes.POINTER(_Result)]
+    lib.hht_poll.restype = ctypes.c_int
+    lib.hht_progress.argtypes = [vp]
+    lib.hht_progress.restype = ctypes.c_int
+    lib.hht_strerror.argtypes = [ctypes.c_int]
+    lib.hht_strerror.restype = ctypes.c_char_p
+    lib.hht_version.argtypes = []
+    lib.hht_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().hht_strerror(int(code)).decode()
+    except ImportError:
+        return f"error {code}"
+
+
+@dataclasses.dataclass
+class Result:
+    leaves: "object"      # [k, 4] int32 (half, i, j, votes): torch tensor (device) or numpy (host)
+    stats: np.ndarray     # uint64 [2, depth + 1, 4]: tested, passed, votes, tests
+    depth: int
+    L: int
+    status: int
+
+    @property
+    def n_leaves(self) -> int:
+        return int(self.leaves.shape[0])
+
+    def total_tests(self) -> int:
+        return int(self.stats[:, :, 3].sum())
+
+    def leaves_numpy(self) -> np.ndarray:
+        lv = self.leaves
+        if hasattr(lv, "detach"):
+            lv = lv.detach().cpu().numpy()
+        return np.asarray(lv).astype(np.uint32).reshape(-1, 4)
+
+
+def _stats_of(r: _Result) -> np.ndarray:
+    st = np.frombuffer(r.stats, dtype=np.uint64).reshape(2, MAX_DEPTH + 1, 4)
+    return st[:, : r.depth + 1].copy()
+
+
+class _Points:
+    """Keeps a contiguous int16 [n, 2] buffer alive and exposes its address."""
+
+    def __init__(self, points):
+        self.keep = None
+        try:
+            import torch
+            if isinstance(points, torch.Tensor):
+                t = points.to(torch.int16).contiguous().reshape(-1, 2)
+                self.keep = t
+                self.ptr = t.data_ptr() if t.numel() else None
+                self.n = t.shape[0]
+                self.device = t.is_cuda
+                return
+        except ImportError:  # pragma: no cover
+            pass
+        a = np.ascontiguousarray(np.asarray(points, dtype=np.int16).reshape(-1, 2))
+        self.keep = a
+        self.ptr = a.ctypes.data if a.size else None
+        self.n = a.shape[0]
+        self.device = False
+
+
+class Context:
+    """One library context: device, CUDA stream (the current torch stream at
+    creation unless given) and the scratch memory it holds."""
+
+    def __init__(self, device: int = 0, stream=None, mem_budget: int = 0):
+        import torch
+        lib = load()
+        self.device = int(device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        handle = ctypes.c_void_p()
+        sp = ctypes.c_void_p(int(stream.cuda_stream)) if hasattr(stream, "cuda_stream") else ctypes.c_void_p(stream)
+        rc = lib.hht_create(ctypes.byref(handle), self.device, sp, int(mem_budget))
+        if rc != HHT_OK:
+            raise HhtError(rc, "hht_create")
+        self._h = handle
+        self._cap_hint = 1 << 12
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().hht_destroy(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _alloc_leaves(self, cap: int, on_device: bool):
+        import torch
+        if on_device:
+            buf = torch.empty((max(cap, 1), 4), dtype=torch.int32, device=f"cuda:{self.device}")
+            return buf, buf.data_ptr()
+        buf = np.empty((max(cap, 1), 4), dtype=np.int32)
+        return buf, buf.ctypes.data
+
+    def detect(self, points, W: int, H: int, depth: int, T: int, leaves_on_device: bool = True,
+               leaf_capacity: Optional[int] = None, raise_on_error: bool = True) -> Result:
+        lib = load()
+        p = _Points(points)
+        cap = int(leaf_capacity or self._cap_hint)
+        while True:
+            buf, ptr = self._alloc_leaves(cap, leaves_on_device)
+            r = _Result()
+            r.leaves = ptr
+            r.leaf_capacity = cap
+            rc = lib.hht_detect(self._h, p.ptr, p.n, int(W), int(H), int(depth), int(T), ctypes.byref(r))
+            if rc == HHT_E_CAPACITY:
+                cap = int(r.n_leaves)
+                self._cap_hint = max(self._cap_hint, cap)
+                continue
+            break
+        if rc != HHT_OK and raise_on_error:
+            raise HhtError(rc, "hht_detect")
+        k = int(r.n_leaves) if rc == HHT_OK else 0
+        return Result(buf[:k], _stats_of(r), int(r.depth), int(r.L), rc)
+
+    def detect_batch(self, images: Sequence[Tuple], leaves_on_device: bool = True,
+                     raise_on_error: bool = True) -> List[Result]:
+        """images: sequence of (points, W, H, depth, T)."""
+        lib = load()
+        pts = [_Points(im[0]) for im in images]
+        arr = (_Image * len(images))()
+        for k, (im, p) in enumerate(zip(images, pts)):
+            arr[k].points = p.ptr
+            arr[k].n = p.n
+            arr[k].W, arr[k].H, arr[k].depth, arr[k].T = (int(v) for v in im[1:5])
+        caps = [self._cap_hint] * len(images)
+        while True:
+            outs = (_Result * len(images))()
+            bufs = []
+            for k in range(len(images)):
+                b, ptr = self._alloc_leaves(caps[k], leaves_on_device)
+                bufs.append(b)
+                outs[k].leaves = ptr
+                outs[k].leaf_capacity = caps[k]
+            rc = lib.hht_detect_batch(self._h, arr, len(images), outs)
+            short = [k for k in range(len(images)) if outs[k].status == HHT_E_CAPACITY]
+            if not short:
+                break
+            for k in short:
+                caps[k] = int(outs[k].n_leaves)
+        res = []
+        for k in range(len(images)):
+            st = int(outs[k].status)
+            if st != HHT_OK and raise_on_error:
+                raise HhtError(st, f"hht_detect_batch[{k}]")
+            nk = int(outs[k].n_leaves) if st == HHT_OK else 0
+            res.append(Result(bufs[k][:nk], _stats_of(outs[k]), int(outs[k].depth), int(outs[k].L), st))
+        if rc != HHT_OK and raise_on_error:
+            raise HhtError(rc, "hht_detect_batch")
+        return res
+
+    # ------------------------------------------------------------ serving
+    def submit(self, points, W: int, H: int, depth: int, T: int) -> int:
+        lib = load()
+        p = _Points(points)
+        im = _Image(p.ptr, p.n, int(W), int(H), int(depth), int(T))
+        t = ctypes.c_uint64()
+        rc = lib.hht_submit(self._h, ctypes.byref(im), ctypes.byref(t))
+        if rc != HHT_OK:
+            raise HhtError(rc, "hht_submit")
+        return int(t.value)
+
+    def progress(self) -> int:
+        rc = load().hht_progress(self._h)
+        if rc < 0:
+            raise HhtError(rc, "hht_progress")
+        return rc
+
+    def poll(self, ticket: int, leaves_on_device: bool = False) -> Optional[Result]:
+        lib = load()
+        cap = self._cap_hint
+        while True:
+            buf, ptr = self._alloc_leaves(cap, leaves_on_device)
+            r = _Result()
+            r.leaves = ptr
+            r.leaf_capacity = cap
+            rc = lib.hht_poll(self._h, int(ticket), ctypes.byref(r))
+            if rc == HHT_E_PENDING:
+                return None
+            if rc == HHT_E_CAPACITY:
+                cap = int(r.n_leaves)
+                continue
+            break
+        if rc != HHT_OK:
+            raise HhtError(rc, "hht_poll")
+        return Result(buf[: int(r.n_leaves)], _stats_of(r), int(r.depth), int(r.L), rc)
+
+
+_default: Optional[Context] = None
+
+
+def default_context() -> Context:
+    global _default
+    if _default is None:
+        _default = Context()
+    return _default
+
+
+def detect(points, W: int, H: int, depth: int, T: int, **kw) -> Result:
+    """Detect lines in one image with the default context (cuda:0)."""
+    return default_context().detect(points, W, H, depth, T, **kw)
+
+
+def version() -> str:
+    return load().hht_version().decode()

@@ -1,0 +1,68 @@
+"""C-ABI library checks that need no GPU: it builds, loads, and exports every
+function that include/hht.h declares; host-only calls behave as documented."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "hht.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hht_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1007_0547_gb300 import build as b
+    b.build()
+    from paper_1007_0547_gb300 import hht
+    return hht.load()
+
+
+def test_header_declares_the_api():
+    assert set(_declared()) == {"hht_create", "hht_destroy", "hht_detect", "hht_detect_batch", "hht_submit",
+                                "hht_poll", "hht_progress", "hht_strerror", "hht_version"}
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_1007_0547_gb300 import hht
+    for name in _declared():
+        assert hasattr(lib, name), name
+        assert name in hht.EXPORTS
+
+
+def test_host_only_calls(lib):
+    from paper_1007_0547_gb300 import hht
+    assert "sm_103a" in hht.version()
+    assert hht.strerror(hht.HHT_E_RANGE) == "point outside the image"
+    assert hht.strerror(12345) == "unknown error"
+    # argument errors are reported before any device work
+    assert lib.hht_create(None, 0, None, 0) == hht.HHT_E_ARG
+    r = hht._Result()
+    assert lib.hht_detect(None, None, 0, 8, 8, 3, 1, ctypes.byref(r)) == hht.HHT_E_ARG
+    assert lib.hht_detect_batch(None, None, 0, None) == hht.HHT_E_ARG
+    assert lib.hht_progress(None) == hht.HHT_E_ARG
+    assert lib.hht_poll(None, 1, ctypes.byref(r)) == hht.HHT_E_ARG
+
+
+def test_result_struct_layout_matches_header(lib):
+    from paper_1007_0547_gb300 import hht
+    # leaves, capacity, n_leaves (3 x 8) + depth, L, status, reserved (4 x 4) + stats 2 x 25 x 4 x 8
+    assert ctypes.sizeof(hht._Result) == 24 + 16 + 2 * 25 * 4 * 8
+    assert ctypes.sizeof(hht._Image) == 8 + 8 + 16
+
+
+def test_package_fails_loudly_without_library(tmp_path):
+    from paper_1007_0547_gb300 import hht
+    saved = hht._lib
+    try:
+        hht._lib = None
+        with pytest.raises(ImportError):
+            hht.load(str(tmp_path / "missing.so"))
+    finally:
+        hht._lib = saved

@@ -1,0 +1,225 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
+
+Results are integers decided by exact comparisons, so every check is
+bit-exact: sorted leaves (half, i, j, votes) and the per-level statistics
+(tested, passed, votes, tests) of both halves.  Full-size workloads, where the
+oracle would take minutes, are checked on sampled cells counted directly by
+the oracle, on the statistics of the levels a shallower oracle run reaches
+(a region's fate at level l does not depend on the depth below it), and on
+properties that hold at any size.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hht():
+    from paper_1007_0547_gb300 import build
+    build.build()
+    from paper_1007_0547_gb300 import hht as mod
+    return mod
+
+
+@pytest.fixture(scope="module")
+def ctx(hht):
+    c = hht.Context(device=0)
+    yield c
+    c.close()
+
+
+def _same(got, want):
+    g = got.leaves_numpy()
+    assert g.shape == want.leaves.shape, (g.shape, want.leaves.shape)
+    assert np.array_equal(g, want.leaves)
+    assert np.array_equal(got.stats, want.stats)
+
+
+def _props(res, T, depth):
+    lv = res.leaves_numpy().astype(np.int64)
+    if len(lv):
+        key = (lv[:, 0] << 50) | (lv[:, 1] << 25) | lv[:, 2]
+        assert np.all(np.diff(key) > 0), "leaves sorted by (half, i, j) and unique"
+        assert np.all(lv[:, 3] >= T)
+        assert np.all(lv[:, 1] < (1 << depth)) and np.all(lv[:, 2] < (1 << depth))
+    st = res.stats.astype(np.int64)
+    for h in (0, 1):
+        assert st[h, 0, 0] == 1 and st[h, 0, 1] == 1
+        for l in range(1, depth + 1):
+            assert st[h, l, 0] == 4 * st[h, l - 1, 1]
+            assert st[h, l, 2] >= T * st[h, l, 1]
+        assert st[h, depth, 1] == int((lv[:, 0] == h).sum()) if len(lv) else st[h, depth, 1] == 0
+
+
+def _sampled_cells(points, W, H, depth, res, k=24, seed=0):
+    lv = res.leaves_numpy()
+    if len(lv) == 0:
+        return
+    rng = np.random.default_rng(seed)
+    for idx in rng.choice(len(lv), size=min(k, len(lv)), replace=False):
+        h, i, j, v = (int(t) for t in lv[idx])
+        assert oracle.count_region(points, W, H, depth, h, i, j, 1) == v, (h, i, j)
+
+
+# ------------------------------------------------------------------ small and plain configs
+@pytest.mark.parametrize("k", range(4))
+def test_plain_128(ctx, k):
+    img = synth.plain_128(index=k)
+    _same(ctx.detect(img.points, img.W, img.H, img.depth, img.T),
+          oracle.detect(img.points, img.W, img.H, img.depth, img.T))
+
+
+def test_plain_1024(ctx):
+    img = synth.plain_1024()
+    got = ctx.detect(img.points, img.W, img.H, img.depth, img.T)
+    _same(got, oracle.detect(img.points, img.W, img.H, img.depth, img.T))
+
+
+@pytest.mark.parametrize("seed", range(48))
+def test_random_shapes(ctx, seed):
+    img = synth.random_small(20000 + seed, max_side=300, max_n=600, max_depth=9, max_T=12)
+    _same(ctx.detect(img.points, img.W, img.H, img.depth, img.T),
+          oracle.detect(img.points, img.W, img.H, img.depth, img.T))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_dense_small_images(ctx, seed):
+    # many points on few cells: long voter lists, many tiles, ragged tails
+    st = synth.Stream(300 + seed)
+    W = int(st.ints(40, 200, 1)[0])
+    H = int(st.ints(40, 200, 1)[0])
+    n = int(st.ints(2000, 9000, 1)[0])
+    pts = np.stack([st.ints(0, W - 1, n), st.ints(0, H - 1, n)], axis=1).astype(np.int16)
+    D = int(st.ints(5, 9, 1)[0])
+    T = int(st.ints(1, 40, 1)[0])
+    _same(ctx.detect(pts, W, H, D, T), oracle.detect(pts, W, H, D, T))
+
+
+# ------------------------------------------------------------------ edge cases
+def test_empty_and_single_point(ctx):
+    r = ctx.detect(np.zeros((0, 2), np.int16), 64, 32, 5, 1)
+    _same(r, oracle.detect(np.zeros((0, 2), np.int16), 64, 32, 5, 1))
+    p = np.array([[17, 3]], np.int16)
+    _same(ctx.detect(p, 64, 32, 6, 1), oracle.detect(p, 64, 32, 6, 1))
+
+
+def test_threshold_above_n_and_depth_one(ctx):
+    img = synth.plain_128(index=5)
+    _same(ctx.detect(img.points, 128, 128, 7, img.n + 1), oracle.detect(img.points, 128, 128, 7, img.n + 1))
+    for T in (1, 50, img.n):
+        _same(ctx.detect(img.points, 128, 128, 1, T), oracle.detect(img.points, 128, 128, 1, T))
+
+
+def test_one_pixel_image_and_thin_images(ctx):
+    p = np.zeros((5, 2), np.int16)
+    _same(ctx.detect(p, 1, 1, 3, 2), oracle.detect(p, 1, 1, 3, 2))
+    st = synth.Stream(8)
+    for W, H in [(1, 300), (300, 1), (3, 77)]:
+        pts = np.stack([st.ints(0, W - 1, 200), st.ints(0, H - 1, 200)], axis=1).astype(np.int16)
+        _same(ctx.detect(pts, W, H, 7, 3), oracle.detect(pts, W, H, 7, 3))
+
+
+def test_int64_corner_arithmetic(ctx):
+    # L * K beyond 2^27 selects the 64-bit corner path
+    st = synth.Stream(12)
+    pts = np.stack([st.ints(0, 32766, 300), st.ints(0, 32766, 300)], axis=1).astype(np.int16)
+    _same(ctx.detect(pts, 32767, 32767, 13, 3), oracle.detect(pts, 32767, 32767, 13, 3))
+    pts2 = np.stack([st.ints(0, 15, 60), st.ints(0, 15, 60)], axis=1).astype(np.int16)
+    _same(ctx.detect(pts2, 16, 16, 24, 4), oracle.detect(pts2, 16, 16, 24, 4))
+
+
+def test_range_error_and_bad_arguments(ctx, hht):
+    with pytest.raises(hht.HhtError) as e:
+        ctx.detect(np.array([[3, 64]], np.int16), 64, 64, 5, 1)
+    assert e.value.code == hht.HHT_E_RANGE
+    for args in [(64, 64, 0, 1), (64, 64, 25, 1), (0, 64, 5, 1), (64, 64, 5, 0)]:
+        with pytest.raises(hht.HhtError) as e:
+            ctx.detect(np.array([[3, 4]], np.int16), *args)
+        assert e.value.code == hht.HHT_E_ARG
+    # the context still works afterwards
+    img = synth.plain_128()
+    _same(ctx.detect(img.points, img.W, img.H, img.depth, img.T),
+          oracle.detect(img.points, img.W, img.H, img.depth, img.T))
+
+
+def test_host_and_device_inputs_and_outputs(ctx):
+    import torch
+    img = synth.plain_128(index=2)
+    want = oracle.detect(img.points, img.W, img.H, img.depth, img.T)
+    dev = torch.from_numpy(img.points).cuda()
+    _same(ctx.detect(dev, img.W, img.H, img.depth, img.T), want)
+    _same(ctx.detect(img.points, img.W, img.H, img.depth, img.T, leaves_on_device=False), want)
+    _same(ctx.detect(dev, img.W, img.H, img.depth, img.T, leaves_on_device=False), want)
+
+
+def test_capacity_two_call_protocol(ctx, hht):
+    import ctypes
+    img = synth.plain_128()
+    want = oracle.detect(img.points, img.W, img.H, img.depth, img.T)
+    lib = hht.load()
+    pts = np.ascontiguousarray(img.points)
+    r = hht._Result()
+    small = np.zeros((3, 4), np.int32)
+    r.leaves = small.ctypes.data
+    r.leaf_capacity = 3
+    rc = lib.hht_detect(ctx._h, pts.ctypes.data, img.n, img.W, img.H, img.depth, img.T, ctypes.byref(r))
+    assert rc == hht.HHT_E_CAPACITY and r.n_leaves == len(want.leaves)
+    _same(ctx.detect(img.points, img.W, img.H, img.depth, img.T, leaf_capacity=1), want)
+
+
+def test_deterministic_repeat(ctx):
+    img = synth.plain_1024(index=1)
+    a = ctx.detect(img.points, img.W, img.H, img.depth, img.T)
+    b = ctx.detect(img.points, img.W, img.H, img.depth, img.T)
+    assert np.array_equal(a.leaves_numpy(), b.leaves_numpy())
+    assert np.array_equal(a.stats, b.stats)
+
+
+# ------------------------------------------------------------------ batches
+def test_batch_of_mixed_images_against_oracle(ctx):
+    imgs = [synth.random_small(40000 + s, max_side=400, max_n=3000, max_depth=9, max_T=20) for s in range(24)]
+    imgs += [synth.plain_128(index=k) for k in range(4)]
+    res = ctx.detect_batch([(im.points, im.W, im.H, im.depth, im.T) for im in imgs])
+    for im, r in zip(imgs, res):
+        _same(r, oracle.detect(im.points, im.W, im.H, im.depth, im.T))
+
+
+def test_batch_equals_single_on_mixed_depths(ctx):
+    imgs = [synth.batch_image(k) for k in (0, 3, 7, 11)] + [synth.plain_128(index=1)]
+    batch = ctx.detect_batch([(im.points, im.W, im.H, im.depth, im.T) for im in imgs])
+    for im, r in zip(imgs, batch):
+        one = ctx.detect(im.points, im.W, im.H, im.depth, im.T)
+        assert np.array_equal(r.leaves_numpy(), one.leaves_numpy())
+        assert np.array_equal(r.stats, one.stats)
+
+
+def test_batch_256_full_size_sampled(ctx):
+    """The 256-image mixed batch at full size, as the benchmark runs it."""
+    imgs = synth.batch_256()
+    res = ctx.detect_batch([(im.points, im.W, im.H, im.depth, im.T) for im in imgs])
+    rng = np.random.default_rng(1)
+    for k in rng.choice(len(imgs), size=24, replace=False):
+        im, r = imgs[k], res[k]
+        _props(r, im.T, im.depth)
+        _sampled_cells(im.points, im.W, im.H, im.depth, r, k=6, seed=int(k))
+        shallow = 5
+        want = oracle.detect(im.points, im.W, im.H, shallow, im.T)
+        # levels 0..shallow-1 do not depend on the depth; at level `shallow` only
+        # the tested / votes / tests columns do not
+        assert np.array_equal(r.stats[:, :shallow], want.stats[:, :shallow])
+        assert np.array_equal(r.stats[:, shallow, [0, 2, 3]], want.stats[:, shallow, [0, 2, 3]])
+
+
+def test_plain_4096_full_size_sampled(ctx):
+    img = synth.plain_4096()
+    r = ctx.detect(img.points, img.W, img.H, img.depth, img.T)
+    _props(r, img.T, img.depth)
+    _sampled_cells(img.points, img.W, img.H, img.depth, r, k=12, seed=4)
+    shallow = 6
+    want = oracle.detect(img.points, img.W, img.H, shallow, img.T)
+    assert np.array_equal(r.stats[:, :shallow], want.stats[:, :shallow])
+    assert np.array_equal(r.stats[:, shallow, [0, 2, 3]], want.stats[:, shallow, [0, 2, 3]])

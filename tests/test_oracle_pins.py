@@ -294,3 +294,16 @@ def test_fht_brute_force_tiny():
                 if g * g * 2 <= S * S * (4 * int(x) ** 2 + 16 * L * L):
                     cnt += 1
             assert cnt == v, (trial, h, l, i0, j0)
+
+
+def test_count_region_matches_hierarchy_and_closed_form():
+    img = synth.plain_128(index=1)
+    r = oracle.detect(img.points, img.W, img.H, img.depth, 1)
+    for h, i, j, v in r.leaves[:: max(1, len(r.leaves) // 40)]:
+        assert oracle.count_region(img.points, img.W, img.H, img.depth, int(h), int(i), int(j), 1) == int(v)
+    for half in (0, 1):
+        c = pins.column_counts(img.points, img.W, img.H, img.depth, 4, half)
+        S = 1 << (img.depth - 4)
+        for a in range(0, 16, 3):
+            for b in range(0, 16, 5):
+                assert oracle.count_region(img.points, img.W, img.H, img.depth, half, a * S, b * S, S) == c[a, b]
