@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Benchmark: line x region tests per second of the hierarchical Hough
+transform on the 256-image mixed batch (side log-uniform in 256-2048, 8-64
+segments, 0.5-5% noise, depth ceil(log2 side), T = 2*side/32), batched through
+one context on one GB300 per rank.
+
+One step = one hht_detect_batch() call over the whole batch (every level of
+every image, both halves, leaves sorted and copied out).  Prints one JSON line
+on rank 0.  `--impl reference` times the CPU oracle instead (rank 0 only).
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 use
+torch.distributed.run with one process per GPU (weak scaling: each rank runs
+its own 256 images).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "line×region tests/s"
+UNIT = "tests/s"
+WORKLOADS = {
+    "batch_256": "256 images, side log-uniform 256-2048, 8-64 segments, noise 0.5-5%, depth ceil(log2 side), "
+                 "T = 2*side/32, both halves",
+    "plain_1024": "1024x1024, 32 segments of 100-1000 px, 2% noise, depth 10, T = 64, both halves",
+    "plain_4096": "4096x4096, 512 segments of 50-4000 px, 1% noise, depth 12, T = 128, both halves",
+    "plain_128": "128x128, 4 segments, 1% noise, depth 7, T = 20, both halves",
+}
+CPU_SAMPLE = [0, 1]   # batch images timed on the CPU oracle (sides 334 and 552)
+
+
+def load_images(workload: str, rank: int):
+    if workload == "batch_256":
+        return synth.batch_256(256, first=256 * rank)
+    fn = {"plain_1024": synth.plain_1024, "plain_4096": synth.plain_4096, "plain_128": synth.plain_128}[workload]
+    return [fn(index=rank)]
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for name in ("hht_kernels.cu", "hht_device.cuh", "hht_internal.h"):
+        with open(os.path.join(ROOT, "paper_1007_0547_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per algorithmic byte of the pass kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "pass_kernel_dram.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return float(d["dram_bytes_per_algorithmic_byte"])
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="hht_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(images, budget_s=None):
+    """Time the CPU oracle, as it stands, on a bounded sample of the workload."""
+    import oracle
+    oracle.build()
+    tests, secs, names = 0, 0.0, []
+    sample = [images[k] for k in CPU_SAMPLE if k < len(images)] if len(images) > 1 else images
+    for im in sample:
+        pts = im.points
+        if len(images) == 1 and im.n > 60000:
+            # single large image: a horizontal band of rows stands in for it
+            pts = im.points[im.points[:, 1] < max(1, im.H // 16)]
+        t = time.perf_counter()
+        r = oracle.detect(pts, im.W, im.H, im.depth, im.T)
+        secs += time.perf_counter() - t
+        tests += r.total_tests()
+        names.append(f"{im.name}(side {im.W}, n {len(pts)})")
+        if budget_s and secs > budget_s:
+            break
+    return tests, secs, ", ".join(names)
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    images = load_images(args.workload, 0)
+    for _ in range(args.warmup):
+        oracle_sample(images)
+    tests = secs = 0.0
+    sample = ""
+    for _ in range(args.steps):
+        t, s, sample = oracle_sample(images)
+        tests += t
+        secs += s
+    v = tests / secs
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
+                                            "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="batch_256")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_1007_0547_gb300 import build as hbuild
+    if rank == 0 or world == 1:
+        hbuild.build()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+        dist.barrier()
+        hbuild.build()  # no-op once rank 0 has built
+    from paper_1007_0547_gb300 import hht
+
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    images = load_images(args.workload, rank)
+    dev_images = [(torch.from_numpy(im.points).to(dev), im.W, im.H, im.depth, im.T) for im in images]
+    host_images = [(np.ascontiguousarray(im.points), im.W, im.H, im.depth, im.T) for im in images]
+    stream = torch.cuda.current_stream(dev)
+    ctx = hht.Context(device=local, stream=stream)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # 512 MB > 129 MB L2
+
+    def step():
+        if len(dev_images) == 1:
+            return [ctx.detect(*dev_images[0])]
+        return ctx.detect_batch(dev_images)
+
+    for _ in range(args.warmup):
+        res = step()
+    torch.cuda.synchronize()
+    tests_per_step = sum(r.total_tests() for r in res)
+    leaves_per_step = sum(r.n_leaves for r in res)
+
+    # ---------------------------------------------------------------- timed region
+    phys = local
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    if vis:
+        ids = [v.strip() for v in vis.split(",")]
+        if local < len(ids) and ids[local].isdigit():
+            phys = int(ids[local])
+    sampler = ClockSampler(phys)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    sampler.start()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    total_ms = sum(times)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        n = torch.tensor([tests_per_step], dtype=torch.float64, device=dev)
+        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+        tests_all = float(n.item())
+        dist.barrier()
+    else:
+        tests_all = float(tests_per_step)
+    value = tests_all * args.steps / (total_ms / 1e3)
+    images_per_s = len(images) * world * args.steps / (total_ms / 1e3)
+
+    # ---------------------------------------------------------------- end to end (host buffers)
+    e2e = None
+    if not args.no_e2e:
+        h2d = sum(im.n for im in images) * 4
+        d2h = leaves_per_step * 16 + len(images) * (2 * 25 * 4 * 8)
+        ts = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if len(host_images) == 1:
+                ctx.detect(*host_images[0], leaves_on_device=False)
+            else:
+                ctx.detect_batch(host_images, leaves_on_device=False)
+            ts.append(time.perf_counter() - t0)
+        e2e_s = sum(ts)
+        if world > 1:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": tests_all * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_s / args.steps}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # ---------------------------------------------------------------- per-image launch sequence
+    per_image = None
+    if len(dev_images) > 1:
+        torch.cuda.synchronize()
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for x in dev_images:
+            ctx.detect(*x)
+        e1.record(stream)
+        e1.synchronize()
+        seq_ms = e0.elapsed_time(e1)
+        per_image = {"images_per_s": len(dev_images) / (seq_ms / 1e3),
+                     "tests_per_s": tests_per_step / (seq_ms / 1e3), "ms": seq_ms}
+
+    # ---------------------------------------------------------------- roofline of the pass kernel
+    peak, peak_kind = read_peaks()
+    achieved = (prof["pass_bytes"] / 1e9) / (prof["pass_ms"] / 1e3) if prof["pass_ms"] > 0 else 0.0
+    ratio = recorded_traffic()
+    per_launch = prof["pass_bytes"] / max(1, prof["pass_launches"])
+    roofline = {"kernel": "pass_kernel<int32_t>", "bound": "hbm", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "peak_source": f"{peak_kind} hbm_gbs",
+                "traffic": (ratio * per_launch) if ratio is not None else None,
+                "algorithmic_bytes_per_launch": per_launch,
+                "launches": prof["pass_launches"], "pass_ms_per_step": prof["pass_ms"] / args.steps,
+                "select_ms_per_step": prof["select_ms"] / args.steps,
+                "stage_ms_per_step": prof["stage_ms"] / args.steps,
+                "sort_ms_per_step": prof["sort_ms"] / args.steps}
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        t, s, sample = oracle_sample(images)
+        cpu = {"value": t / s, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+               "seconds": s}
+
+    srt = sorted(times)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": args.workload, "description": WORKLOADS[args.workload],
+                   "images_per_rank": len(images), "points_per_rank": int(sum(im.n for im in images)),
+                   "tests_per_step_per_rank": int(tests_per_step), "leaves_per_step_per_rank": int(leaves_per_step),
+                   "l2": "512 MB buffer written between timed steps; voter streams are larger than L2"},
+        "images_per_s": images_per_s,
+        "latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
+                       "what": "one step (whole batch)"},
+        "per_image_sequence": per_image,
+        "e2e": e2e,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "gpu_launches": int(prof["launches"]),
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -150,6 +150,30 @@ int hht_submit(hht_ctx *ctx, const hht_image *image, uint64_t *ticket);
 int hht_poll(hht_ctx *ctx, uint64_t ticket, hht_result *out);
 int hht_progress(hht_ctx *ctx);
 
+/*
+ * Kernel timing.  hht_profile_enable(ctx, 1) resets the counters and makes the
+ * context record CUDA events on its stream around every kernel it launches
+ * (0 stops recording).  hht_profile_read() copies the accumulated counters.
+ * "pass" is the per-level kernel that reads a voter stream once; its
+ * algorithmic bytes are 8 per voter record read plus 8 per record written.
+ * Errors: HHT_E_ARG (NULL).
+ */
+typedef struct {
+    uint64_t launches;          /* kernels launched by the context */
+    uint64_t pass_launches;
+    uint64_t select_launches;
+    uint64_t voters_read;       /* voter records read by pass launches */
+    uint64_t voters_written;    /* voter records written by pass launches */
+    uint64_t pass_bytes;        /* 8 * (voters_read + voters_written) */
+    double pass_ms;             /* summed device time of the pass launches */
+    double select_ms;
+    double stage_ms;
+    double sort_ms;             /* leaf sort and output fix-up */
+} hht_profile_counters;
+
+int hht_profile_enable(hht_ctx *ctx, int on);
+int hht_profile_read(hht_ctx *ctx, hht_profile_counters *out);
+
 /* Short description of an HHT_* code (static string). */
 const char *hht_strerror(int code);
 

@@ -61,6 +61,16 @@ struct hht_ctx {
 
     hht::ServeState* serve = nullptr;
     std::mutex mu;
+
+    // kernel timing (hht_profile_enable)
+    bool profile = false;
+    hht_profile_counters prof{};
+    std::vector<cudaEvent_t> ev_pool;
+    struct Pending {
+        cudaEvent_t a, b;
+        int kind;  // 0 stage, 1 select, 2 pass, 3 sort
+    };
+    std::vector<Pending> pending;
 };
 
 namespace {
@@ -135,6 +145,56 @@ void release(hht_ctx* c, DevBuf& b) {
     }
     b.p = nullptr;
     b.bytes = 0;
+}
+
+// ---- kernel timing helpers: event pairs are resolved after the job's last sync
+cudaEvent_t take_event(hht_ctx* c) {
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct ProfScope {
+    hht_ctx* c;
+    int kind;
+    cudaEvent_t a = nullptr;
+    ProfScope(hht_ctx* c_, int kind_) : c(c_), kind(kind_) {
+        if (c->profile) {
+            a = take_event(c);
+            cudaEventRecord(a, c->stream);
+        }
+    }
+    ~ProfScope() {
+        if (c->profile && a) {
+            cudaEvent_t b = take_event(c);
+            cudaEventRecord(b, c->stream);
+            c->pending.push_back({a, b, kind});
+        }
+    }
+};
+
+void resolve_profile(hht_ctx* c) {
+    for (auto& p : c->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) != cudaSuccess) {
+            cudaGetLastError();
+            ms = 0.f;
+        }
+        switch (p.kind) {
+            case 0: c->prof.stage_ms += ms; break;
+            case 1: c->prof.select_ms += ms; break;
+            case 2: c->prof.pass_ms += ms; break;
+            default: c->prof.sort_ms += ms; break;
+        }
+        c->ev_pool.push_back(p.a);
+        c->ev_pool.push_back(p.b);
+    }
+    c->pending.clear();
 }
 
 int check_image(const hht_image& im) {
@@ -246,10 +306,15 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs) {
     DeviceStatus* d_status = (DeviceStatus*)c->status.p;
     ScanState* d_scan = (ScanState*)c->scan_states.p;
 
-    if (launch_stage((const int16_t*)c->pts.p, total, (const Unit*)c->units.p, count, (const uint64_t*)c->img_start.p,
-                     (const uint32_t*)c->img_unit.p, (Voter*)c->vox[0].p, (uint32_t*)c->cnt[0].p,
-                     (uint64_t*)c->stats.p, (uint32_t*)c->img_err.p, d_status, i64, st) != 0)
-        return HHT_E_CUDA;
+    {
+        ProfScope ps(c, 0);
+        if (launch_stage((const int16_t*)c->pts.p, total, (const Unit*)c->units.p, count,
+                         (const uint64_t*)c->img_start.p, (const uint32_t*)c->img_unit.p, (Voter*)c->vox[0].p,
+                         (uint32_t*)c->cnt[0].p, (uint64_t*)c->stats.p, (uint32_t*)c->img_err.p, d_status, i64,
+                         st) != 0)
+            return HHT_E_CUDA;
+        if (total > 0) c->prof.launches += 1;
+    }
 
     // ---- level loop
     uint64_t leaf_total = 0;
@@ -294,7 +359,12 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs) {
         const int sel_grid = (int)std::min<uint64_t>(sel_tiles, (uint64_t)c->num_sms * c->occ_select);
         // select's capacity test on the voter stream is re-done below with the exact size
         a.cap_voters = UINT64_MAX;
-        if (launch_select(a, 256, std::max(sel_grid, 1), st) != 0) return HHT_E_CUDA;
+        {
+            ProfScope ps(c, 1);
+            if (launch_select(a, 256, std::max(sel_grid, 1), st) != 0) return HHT_E_CUDA;
+        }
+        c->prof.launches += 1;
+        c->prof.select_launches += 1;
 
         CK(cudaMemcpyAsync(&c->h_infos[s], d_infos + s, sizeof(LevelInfo), cudaMemcpyDeviceToHost, st));
         DeviceStatus hs{};
@@ -323,7 +393,15 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs) {
         a.cap_tiles = pass_tiles;
         const int occ = i64 ? c->occ_pass64 : c->occ_pass32;
         const int pass_grid = (int)std::min<uint64_t>(pass_tiles, (uint64_t)c->num_sms * occ);
-        if (launch_pass(a, i64, std::max(pass_grid, 1), st) != 0) return HHT_E_CUDA;
+        {
+            ProfScope ps(c, 2);
+            if (launch_pass(a, i64, std::max(pass_grid, 1), st) != 0) return HHT_E_CUDA;
+        }
+        c->prof.launches += 1;
+        c->prof.pass_launches += 1;
+        c->prof.voters_read += nin;
+        c->prof.voters_written += nout;
+        c->prof.pass_bytes += 8 * (nin + nout);
     }
 
     // ---- outputs
@@ -338,17 +416,25 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs) {
     if (err & kErrOverflow) return HHT_E_NOMEM;
     if (err & kErrInvariant) return HHT_E_CUDA;
 
-    if (leaf_total > 1) {
-        RK(ensure(c, c->leaves_tmp, leaf_total * sizeof(DevLeaf)));
-        RK(ensure(c, c->sort_scratch, sort_scratch_bytes(leaf_total)));
-        const int unit_bits = ceil_log2_i(n_units);
-        if (launch_leaf_sort((DevLeaf*)c->leaves.p, (DevLeaf*)c->leaves_tmp.p, leaf_total, unit_bits, Dmax,
-                             c->sort_scratch.p, c->sort_scratch.bytes, d_status, c->num_sms, st) != 0)
-            return HHT_E_CUDA;
+    {
+        ProfScope ps(c, 3);
+        if (leaf_total > 1) {
+            RK(ensure(c, c->leaves_tmp, leaf_total * sizeof(DevLeaf)));
+            RK(ensure(c, c->sort_scratch, sort_scratch_bytes(leaf_total)));
+            const int unit_bits = ceil_log2_i(n_units);
+            int nk = 0;
+            if (launch_leaf_sort((DevLeaf*)c->leaves.p, (DevLeaf*)c->leaves_tmp.p, leaf_total, unit_bits, Dmax,
+                                 c->sort_scratch.p, c->sort_scratch.bytes, d_status, c->num_sms, st, &nk) != 0)
+                return HHT_E_CUDA;
+            c->prof.launches += (uint64_t)nk;
+        }
+        // leaves of image g are the contiguous block of units 2g, 2g+1 (sorted
+        // by unit); a leaf's half is its unit's parity
+        if (leaf_total > 0) {
+            if (launch_unit_to_half(c->leaves.p, leaf_total, st) != 0) return HHT_E_CUDA;
+            c->prof.launches += 1;
+        }
     }
-    // leaves of image g are the contiguous block of units 2g, 2g+1 (sorted by
-    // unit); a leaf's half is its unit's parity
-    if (leaf_total > 0 && launch_unit_to_half(c->leaves.p, leaf_total, st) != 0) return HHT_E_CUDA;
     uint64_t off = 0;
     for (int g = 0; g < count; ++g) {
         hht_result& r = outs[g];
@@ -383,6 +469,7 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs) {
     }
     if (off != leaf_total) return HHT_E_CUDA;
     CK(cudaStreamSynchronize(st));
+    if (c->profile) resolve_profile(c);
     return HHT_OK;
 }
 
@@ -478,6 +565,8 @@ void hht_destroy(hht_ctx* c) {
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     hht::serve_destroy(c->serve);
+    resolve_profile(c);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     DevBuf* all[] = {&c->pts,       &c->img_start,  &c->img_unit, &c->units,        &c->stats,     &c->infos,      &c->status,
                      &c->leaf_total, &c->img_err,   &c->scan_states,  &c->rec[0],    &c->rec[1],     &c->link[0],
                      &c->link[1],   &c->cnt[0],     &c->cnt[1],       &c->vox[0],    &c->vox[1],     &c->leaves,
@@ -510,6 +599,25 @@ int hht_detect_batch(hht_ctx* c, const hht_image* images, int32_t count, hht_res
     std::lock_guard<std::mutex> lk(c->mu);
     cudaSetDevice(c->device);
     return run_job(c, images, count, outs);
+}
+
+int hht_profile_enable(hht_ctx* c, int on) {
+    if (!c) return HHT_E_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaStreamSynchronize(c->stream);
+    resolve_profile(c);
+    c->profile = on != 0;
+    c->prof = hht_profile_counters{};
+    return HHT_OK;
+}
+
+int hht_profile_read(hht_ctx* c, hht_profile_counters* out) {
+    if (!c || !out) return HHT_E_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaStreamSynchronize(c->stream);
+    resolve_profile(c);
+    *out = c->prof;
+    return HHT_OK;
 }
 
 const char* hht_strerror(int code) {

@@ -149,6 +149,7 @@ int launch_unit_to_half(void* leaves, uint64_t n, void* stream);
 // Leaf sort (hht_sort.cu): stable LSD radix sort of leaves by (unit, i, j).
 size_t sort_scratch_bytes(uint64_t n);
 int launch_leaf_sort(DevLeaf* leaves, DevLeaf* tmp, uint64_t n, int unit_bits, int depth_bits,
-                     void* scratch, size_t scratch_bytes, DeviceStatus* status, int num_sms, void* stream);
+                     void* scratch, size_t scratch_bytes, DeviceStatus* status, int num_sms, void* stream,
+                     int* kernels_launched);
 
 }  // namespace hht

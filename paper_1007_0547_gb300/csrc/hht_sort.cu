@@ -162,7 +162,8 @@ SortLayout sort_layout(uint64_t n) {
 size_t sort_scratch_bytes(uint64_t n) { return (size_t)sort_layout(n).bytes; }
 
 int launch_leaf_sort(DevLeaf* leaves, DevLeaf* tmp, uint64_t n, int unit_bits, int depth_bits, void* scratch,
-                     size_t scratch_bytes, DeviceStatus* status, int num_sms, void* stream) {
+                     size_t scratch_bytes, DeviceStatus* status, int num_sms, void* stream, int* kernels_launched) {
+    *kernels_launched = 0;
     if (n <= 1) return 0;
     cudaStream_t st = (cudaStream_t)stream;
     const SortLayout L = sort_layout(n);
@@ -189,6 +190,7 @@ int launch_leaf_sort(DevLeaf* leaves, DevLeaf* tmp, uint64_t n, int unit_bits, i
         scan_kernel<<<scan_grid, kTPB, 0, st>>>(hist, m, ss, flags, data, status);
         scatter_kernel<<<grid, kTPB, 0, st>>>(src, dst, n, shift, depth_bits, hist, (uint32_t)ntiles);
         DevLeaf* sw = src; src = dst; dst = sw;
+        *kernels_launched += 3;
     }
     if (src != leaves) cudaMemcpyAsync(leaves, src, n * sizeof(DevLeaf), cudaMemcpyDeviceToDevice, st);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;

@@ -30,7 +30,7 @@ HHT_E_UNKNOWN_TICKET = -8
 
 # every function the C header declares
 EXPORTS = ("hht_create", "hht_destroy", "hht_detect", "hht_detect_batch", "hht_submit", "hht_poll",
-           "hht_progress", "hht_strerror", "hht_version")
+           "hht_progress", "hht_profile_enable", "hht_profile_read", "hht_strerror", "hht_version")
 
 
 class HhtError(RuntimeError):
@@ -43,6 +43,13 @@ class _Result(ctypes.Structure):
     _fields_ = [("leaves", ctypes.c_void_p), ("leaf_capacity", ctypes.c_uint64), ("n_leaves", ctypes.c_uint64),
                 ("depth", ctypes.c_int32), ("L", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("stats", ctypes.c_uint64 * (2 * (MAX_DEPTH + 1) * 4))]
+
+
+class _Profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64), ("pass_launches", ctypes.c_uint64),
+                ("select_launches", ctypes.c_uint64), ("voters_read", ctypes.c_uint64),
+                ("voters_written", ctypes.c_uint64), ("pass_bytes", ctypes.c_uint64), ("pass_ms", ctypes.c_double),
+                ("select_ms", ctypes.c_double), ("stage_ms", ctypes.c_double), ("sort_ms", ctypes.c_double)]
 
 
 class _Image(ctypes.Structure):
@@ -77,6 +84,10 @@ def load(path: str = LIB_PATH):
     lib.hht_poll.restype = ctypes.c_int
     lib.hht_progress.argtypes = [vp]
     lib.hht_progress.restype = ctypes.c_int
+    lib.hht_profile_enable.argtypes = [vp, ctypes.c_int]
+    lib.hht_profile_enable.restype = ctypes.c_int
+    lib.hht_profile_read.argtypes = [vp, ctypes.POINTER(_Profile)]
+    lib.hht_profile_read.restype = ctypes.c_int
     lib.hht_strerror.argtypes = [ctypes.c_int]
     lib.hht_strerror.restype = ctypes.c_char_p
     lib.hht_version.argtypes = []
@@ -236,6 +247,19 @@ class Context:
         if rc != HHT_OK and raise_on_error:
             raise HhtError(rc, "hht_detect_batch")
         return res
+
+    # ------------------------------------------------------------ kernel timing
+    def profile(self, on: bool = True) -> None:
+        rc = load().hht_profile_enable(self._h, 1 if on else 0)
+        if rc != HHT_OK:
+            raise HhtError(rc, "hht_profile_enable")
+
+    def profile_read(self) -> dict:
+        p = _Profile()
+        rc = load().hht_profile_read(self._h, ctypes.byref(p))
+        if rc != HHT_OK:
+            raise HhtError(rc, "hht_profile_read")
+        return {name: getattr(p, name) for name, _ in _Profile._fields_}
 
     # ------------------------------------------------------------ serving
     def submit(self, points, W: int, H: int, depth: int, T: int) -> int:

@@ -26,7 +26,8 @@ def lib():
 
 def test_header_declares_the_api():
     assert set(_declared()) == {"hht_create", "hht_destroy", "hht_detect", "hht_detect_batch", "hht_submit",
-                                "hht_poll", "hht_progress", "hht_strerror", "hht_version"}
+                                "hht_poll", "hht_progress", "hht_profile_enable", "hht_profile_read",
+                                "hht_strerror", "hht_version"}
 
 
 def test_library_exports_every_declared_symbol(lib):
@@ -48,6 +49,8 @@ def test_host_only_calls(lib):
     assert lib.hht_detect_batch(None, None, 0, None) == hht.HHT_E_ARG
     assert lib.hht_progress(None) == hht.HHT_E_ARG
     assert lib.hht_poll(None, 1, ctypes.byref(r)) == hht.HHT_E_ARG
+    assert lib.hht_profile_enable(None, 1) == hht.HHT_E_ARG
+    assert lib.hht_profile_read(None, None) == hht.HHT_E_ARG
 
 
 def test_result_struct_layout_matches_header(lib):
