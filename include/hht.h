@@ -26,8 +26,10 @@
  *
  * Leaf cell (i, j) of half h spans m in [-1 + 2i/K, -1 + 2(i+1)/K] and
  * b in [-2L + 4Lj/K, -2L + 4L(j+1)/K] (in the half's own coordinates).
- * Every decision is an exact integer comparison, so results are unique:
- * leaves are reported sorted by (half, i, j).
+ * Every decision is an exact integer comparison, so results are unique.
+ * Leaves are reported half 0 first, each half in the order in which the
+ * paper's depth-first traversal reaches them (children quad1..quad4 = NE, NW,
+ * SW, SE at every level), i.e. the order of its solution() calls.
  *
  * Errors: every call returns HHT_OK (0) or a negative HHT_E_* code.  No call
  * aborts, asserts or traps; argument errors are found before any device work.
@@ -117,8 +119,8 @@ void hht_destroy(hht_ctx *ctx);
  * Detect lines in one image (Section 3, both halves).  `points` holds n edge
  * points in host memory or in device memory of the context's device; n = 0 is
  * valid.  On return the work is complete (the call synchronises the stream):
- * out->leaves[0 .. n_leaves) hold the leaves sorted by (half, i, j) and
- * out->stats[h][l] the statistics for levels 0..depth.
+ * out->leaves[0 .. n_leaves) hold the leaves in depth-first order (see above)
+ * and out->stats[h][l] the statistics for levels 0..depth.
  * Errors: HHT_E_ARG (checked before any device work), HHT_E_RANGE (a point
  * outside the image), HHT_E_CAPACITY (out->n_leaves = required count; call
  * again with a larger buffer), HHT_E_NOMEM, HHT_E_TIMEOUT, HHT_E_CUDA.
@@ -168,7 +170,7 @@ typedef struct {
     double pass_ms;             /* summed device time of the pass launches */
     double select_ms;
     double stage_ms;
-    double sort_ms;             /* leaf sort and output fix-up */
+    double sort_ms;             /* leaf output fix-up */
 } hht_profile_counters;
 
 int hht_profile_enable(hht_ctx *ctx, int on);

@@ -43,6 +43,8 @@
  * with one voter list per level instead of one code array per level: a point
  * is only tested for a child when it voted for the parent, which is what the
  * code test "(level-1).linecode != 0000 and != 1111" of step 12.b decides.
+ * Leaves are reported in the order this traversal reaches them (half 0
+ * first), which is the order in which solution() would be called.
  *
  * The FHT mode replaces the code test by the circumscribed-circle test of the
  * prior-art Fast Hough Transform that the paper compares with (Sections 1-2):
@@ -190,15 +192,6 @@ static void subdivide(walk_t *w, int level, int64_t i0, int64_t j0, int64_t S, c
     }
 }
 
-static int leaf_cmp(const void *a, const void *b)
-{
-    const oracle_leaf *x = (const oracle_leaf *)a, *y = (const oracle_leaf *)b;
-    if (x->half != y->half) return x->half < y->half ? -1 : 1;
-    if (x->i != y->i) return x->i < y->i ? -1 : 1;
-    if (x->j != y->j) return x->j < y->j ? -1 : 1;
-    return 0;
-}
-
 /*
  * Run the hierarchy on n points (xy[2k] = x, xy[2k+1] = y) of a W x H image.
  *   stats: caller array of 2 * (depth + 1) * 4 uint64, per half and level:
@@ -206,7 +199,7 @@ static int leaf_cmp(const void *a, const void *b)
  *   leaves: caller array of leaf_cap entries; *n_leaves receives the count
  *          (also when it exceeds leaf_cap, which returns ORACLE_E_CAPACITY).
  *   regions: optional (may be NULL) dump of every tested region.
- * Leaves are sorted by (half, i, j).
+ * Leaves are in depth-first order (children NE, NW, SW, SE), half 0 first.
  */
 int oracle_detect(const int16_t *xy, int64_t n, int32_t W, int32_t H, int32_t depth, int32_t T, int32_t mode,
                   oracle_leaf *leaves, int64_t leaf_cap, int64_t *n_leaves, uint64_t *stats,
@@ -259,7 +252,6 @@ int oracle_detect(const int16_t *xy, int64_t n, int32_t W, int32_t H, int32_t de
     *n_leaves = w.n_leaves;
     if (n_regions) *n_regions = w.n_regions;
     if (w.n_leaves > leaf_cap) { rc = ORACLE_E_CAPACITY; goto done; }
-    if (w.n_leaves > 0) qsort(leaves, (size_t)w.n_leaves, sizeof(oracle_leaf), leaf_cmp);
 
 done:
     free(px); free(py); free(pool); free(lists);

@@ -1,7 +1,8 @@
 """ctypes binding of the C oracle (test infrastructure only).
 
 detect() runs the depth-first hierarchy of Section 3 of the paper on one image
-and returns sorted leaves (half, i, j, votes) and per-level statistics
+and returns its leaves (half, i, j, votes) in depth-first order (children NE,
+NW, SW, SE; half 0 first) and per-level statistics
 stats[half, level] = (regions tested, regions passed, votes, code evaluations).
 """
 from __future__ import annotations
@@ -80,7 +81,7 @@ def _load():
 
 @dataclasses.dataclass
 class OracleResult:
-    leaves: np.ndarray   # uint32 [k, 4]: half, i, j, votes (sorted)
+    leaves: np.ndarray   # uint32 [k, 4]: half, i, j, votes (depth-first order)
     stats: np.ndarray    # uint64 [2, depth + 1, 4]
     regions: Optional[np.ndarray] = None  # uint32 [r, 6]: half, level, i0, j0, size, votes
     rc: int = 0

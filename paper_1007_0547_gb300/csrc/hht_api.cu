@@ -43,6 +43,8 @@ int ceil_log2_i(int v) {
 
 struct hht_ctx {
     int device = 0;
+    bool debug = false;          // HHT_DEBUG=1: wave and allocation trace on stderr
+    uint64_t wave_cap = 0;       // largest wave estimate known to fit (0 = none failed yet)
     cudaStream_t stream = nullptr;
     uint64_t budget = 0;
     uint64_t held = 0;
@@ -51,9 +53,9 @@ struct hht_ctx {
 
     // job buffers
     DevBuf pts, img_start, img_unit, units, stats, infos, status, leaf_total, img_err, scan_states;
-    DevBuf rec[2], link[2], cnt[2], vox[2];
-    DevBuf leaves, leaves_tmp, sort_scratch;
-    DevBuf sel_flags, sel_data, pass_flags, pass_data;
+    DevBuf rec[2], preg[2], cnt[2], vox[2];
+    DevBuf leaves;
+    DevBuf sel_flags, sel_data, cursors;
     // host staging
     std::vector<uint64_t> h_stats;
     std::vector<LevelInfo> h_infos;
@@ -68,7 +70,7 @@ struct hht_ctx {
     std::vector<cudaEvent_t> ev_pool;
     struct Pending {
         cudaEvent_t a, b;
-        int kind;  // 0 stage, 1 select, 2 pass, 3 sort
+        int kind;  // 0 stage, 1 select, 2 pass, 3 output fix-up
     };
     std::vector<Pending> pending;
 };
@@ -101,6 +103,8 @@ int ensure(hht_ctx* c, DevBuf& b, size_t bytes, bool zero = false) {
     cudaError_t e = cudaMalloc(&p, want);
     if (e != cudaSuccess) {
         cudaGetLastError();
+        if (c->debug)
+            fprintf(stderr, "[hht] cudaMalloc of %.3f GB failed (context holds %.3f GB)\n", want / 1e9, c->held / 1e9);
         return HHT_E_NOMEM;
     }
     b.p = p;
@@ -207,7 +211,7 @@ int check_image(const hht_image& im) {
 }
 
 constexpr int kSelTile = 1024;   // parents per select tile
-constexpr int kPassTile = 2048;  // voters per pass tile
+constexpr int kPassTile = 256 * 8;  // voters per pass block below which fewer blocks are launched
 
 #define CK(call)                                   \
     do {                                           \
@@ -323,7 +327,7 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs) {
         const int pi = (s - 1) & 1, ci = s & 1;
         const uint64_t P = c->h_infos[s - 1].n_regions;
         if (P == 0) break;
-        RK(ensure(c, c->link[pi], P * sizeof(RegionLink)));
+        RK(ensure(c, c->preg[pi], P * sizeof(PassRegion)));
         RK(ensure(c, c->rec[ci], 4 * P * sizeof(Region)));
         RK(ensure(c, c->cnt[ci], 4 * P * 4 * sizeof(uint32_t)));
         const uint64_t cap_leaves = leaf_total + 4 * P;
@@ -332,15 +336,17 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs) {
         if ((sel_tiles + 1) * 4 > c->sel_flags.bytes) {
             RK(ensure(c, c->sel_flags, (sel_tiles + 1) * 4, true));
         }
-        RK(ensure(c, c->sel_data, (sel_tiles + 1) * 2 * 2 * sizeof(uint64_t)));
+        RK(ensure(c, c->sel_data, (sel_tiles + 1) * 2 * 3 * sizeof(uint64_t)));
+        RK(ensure(c, c->cursors, 4 * P * sizeof(unsigned long long)));
 
         LevelArgs a{};
         a.units = (const Unit*)c->units.p;
         a.parents = (const Region*)c->rec[pi].p;
-        a.links = (RegionLink*)c->link[pi].p;
+        a.pregions = (PassRegion*)c->preg[pi].p;
         a.parent_cnt = (const uint32_t*)c->cnt[pi].p;
         a.children = (Region*)c->rec[ci].p;
         a.child_cnt = (uint32_t*)c->cnt[ci].p;
+        a.cursor = (unsigned long long*)c->cursors.p;
         a.leaves = (DevLeaf*)c->leaves.p;
         a.stats = (uint64_t*)c->stats.p;
         a.info_prev = d_infos + (s - 1);
@@ -371,6 +377,11 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs) {
         CK(cudaMemcpyAsync(&hs, d_status, sizeof hs, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         err = hs.err;
+        if (c->debug)
+            fprintf(stderr, "[hht]   step %d: parents %llu, regions %llu, voters in %llu, out %llu, leaves %llu, held %.2f GB\n",
+                    s, (unsigned long long)P, (unsigned long long)c->h_infos[s].n_regions,
+                    (unsigned long long)c->h_infos[s - 1].n_voters, (unsigned long long)c->h_infos[s].n_voters,
+                    (unsigned long long)c->h_infos[s].n_leaves, c->held / 1e9);
         if (err) break;
         leaf_total += c->h_infos[s].n_leaves;
         if (s == Dmax) break;
@@ -379,20 +390,13 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs) {
         if (nin == 0) continue;  // no unit needs level s+1 counts
         const uint64_t nout = c->h_infos[s].n_voters;
         RK(ensure(c, c->vox[ci], std::max<uint64_t>(nout, 1) * sizeof(Voter)));
-        const uint64_t pass_tiles = (nin + kPassTile - 1) / kPassTile;
-        if ((pass_tiles + 1) * 4 > c->pass_flags.bytes) {
-            RK(ensure(c, c->pass_flags, (pass_tiles + 1) * 4, true));
-        }
-        RK(ensure(c, c->pass_data, (pass_tiles + 1) * 2 * 4 * sizeof(uint64_t)));
         a.vin = (const Voter*)c->vox[pi].p;
         a.vout = (Voter*)c->vox[ci].p;
         a.cap_voters = nout;
-        a.scan = d_scan + 1;
-        a.tile_flags = (uint32_t*)c->pass_flags.p;
-        a.tile_data = (uint64_t*)c->pass_data.p;
-        a.cap_tiles = pass_tiles;
         const int occ = i64 ? c->occ_pass64 : c->occ_pass32;
-        const int pass_grid = (int)std::min<uint64_t>(pass_tiles, (uint64_t)c->num_sms * occ);
+        // enough 32-voter warp slices to fill the device, no more than the stream needs
+        const uint64_t want_blocks = (nin + kPassTile - 1) / kPassTile;
+        const int pass_grid = (int)std::min<uint64_t>(want_blocks, (uint64_t)c->num_sms * occ);
         {
             ProfScope ps(c, 2);
             if (launch_pass(a, i64, std::max(pass_grid, 1), st) != 0) return HHT_E_CUDA;
@@ -416,27 +420,34 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs) {
     if (err & kErrOverflow) return HHT_E_NOMEM;
     if (err & kErrInvariant) return HHT_E_CUDA;
 
-    {
+    // Leaves need no sort: a step emits the leaves of the units whose depth it
+    // reaches, in record order, and records stay in depth-first order (children
+    // in quadrant order NE, NW, SW, SE under their parent, parents in order), so
+    // every unit's leaves form one block in the order of the paper's
+    // depth-first traversal, and blocks follow (depth, unit).  Only the unit
+    // field is rewritten to the half.
+    if (leaf_total > 0) {
         ProfScope ps(c, 3);
-        if (leaf_total > 1) {
-            RK(ensure(c, c->leaves_tmp, leaf_total * sizeof(DevLeaf)));
-            RK(ensure(c, c->sort_scratch, sort_scratch_bytes(leaf_total)));
-            const int unit_bits = ceil_log2_i(n_units);
-            int nk = 0;
-            if (launch_leaf_sort((DevLeaf*)c->leaves.p, (DevLeaf*)c->leaves_tmp.p, leaf_total, unit_bits, Dmax,
-                                 c->sort_scratch.p, c->sort_scratch.bytes, d_status, c->num_sms, st, &nk) != 0)
-                return HHT_E_CUDA;
-            c->prof.launches += (uint64_t)nk;
-        }
-        // leaves of image g are the contiguous block of units 2g, 2g+1 (sorted
-        // by unit); a leaf's half is its unit's parity
-        if (leaf_total > 0) {
-            if (launch_unit_to_half(c->leaves.p, leaf_total, st) != 0) return HHT_E_CUDA;
-            c->prof.launches += 1;
-        }
+        if (launch_unit_to_half(c->leaves.p, leaf_total, st) != 0) return HHT_E_CUDA;
+        c->prof.launches += 1;
     }
-    uint64_t off = 0;
+    std::vector<uint64_t> img_leaves(count, 0), img_off(count, 0);
+    for (int g = 0; g < count; ++g)
+        for (int h = 0; h < 2; ++h)
+            img_leaves[g] += c->h_stats[((size_t)(2 * g + h) * (kMaxDepth + 1) + im[g].depth) * 4 + 1];
+    {
+        std::vector<int> order(count);
+        for (int g = 0; g < count; ++g) order[g] = g;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return im[x].depth < im[y].depth; });
+        uint64_t acc = 0;
+        for (int g : order) {
+            img_off[g] = acc;
+            acc += img_leaves[g];
+        }
+        if (acc != leaf_total) return HHT_E_CUDA;
+    }
     for (int g = 0; g < count; ++g) {
+        const uint64_t off = img_off[g];
         hht_result& r = outs[g];
         const int D = im[g].depth;
         r.depth = D;
@@ -465,9 +476,7 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs) {
                                    cudaMemcpyDefault, st));
             }
         }
-        off += nl;
     }
-    if (off != leaf_total) return HHT_E_CUDA;
     CK(cudaStreamSynchronize(st));
     if (c->profile) resolve_profile(c);
     return HHT_OK;
@@ -491,6 +500,7 @@ int run_job(hht_ctx* c, const hht_image* im, int count, hht_result* outs) {
         cudaMemGetInfo(&fr, &tot);
         budget = (uint64_t)((double)(fr + c->held) * 0.8);
     }
+    if (c->wave_cap && c->wave_cap < budget) budget = c->wave_cap;
     int first = 0;
     int rc_all = HHT_OK;
     while (first < count) {
@@ -502,9 +512,14 @@ int run_job(hht_ctx* c, const hht_image* im, int count, hht_result* outs) {
             acc += e;
             ++last;
         }
+        if (c->debug)
+            fprintf(stderr, "[hht] wave of images [%d, %d): estimate %.2f GB, budget %.2f GB\n", first, last, acc / 1e9,
+                    budget / 1e9);
         int rc = run_wave(c, im + first, last - first, outs + first);
         if (rc == HHT_E_NOMEM && last - first > 1) {
-            // split the wave and retry each half
+            // remember that this much did not fit, split the wave and retry each half
+            c->wave_cap = acc / 2 > 0 ? acc / 2 : 1;
+            if (c->debug) fprintf(stderr, "[hht] wave did not fit; wave estimate cap now %.2f GB\n", c->wave_cap / 1e9);
             const int mid = first + (last - first) / 2;
             rc = run_job(c, im + first, mid - first, outs + first);
             if (rc == HHT_OK) rc = run_job(c, im + mid, last - mid, outs + mid);
@@ -538,6 +553,7 @@ int hht_create(hht_ctx** out, int device, void* cuda_stream, uint64_t mem_budget
     hht_ctx* c = new (std::nothrow) hht_ctx();
     if (!c) return HHT_E_NOMEM;
     c->device = device;
+    c->debug = getenv("HHT_DEBUG") && getenv("HHT_DEBUG")[0] == '1';
     c->stream = (cudaStream_t)cuda_stream;
     c->budget = mem_budget_bytes;
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
@@ -568,9 +584,9 @@ void hht_destroy(hht_ctx* c) {
     resolve_profile(c);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     DevBuf* all[] = {&c->pts,       &c->img_start,  &c->img_unit, &c->units,        &c->stats,     &c->infos,      &c->status,
-                     &c->leaf_total, &c->img_err,   &c->scan_states,  &c->rec[0],    &c->rec[1],     &c->link[0],
-                     &c->link[1],   &c->cnt[0],     &c->cnt[1],       &c->vox[0],    &c->vox[1],     &c->leaves,
-                     &c->leaves_tmp, &c->sort_scratch, &c->sel_flags, &c->sel_data,  &c->pass_flags, &c->pass_data};
+                     &c->leaf_total, &c->img_err,   &c->scan_states,  &c->rec[0],    &c->rec[1],     &c->preg[0],
+                     &c->preg[1],   &c->cnt[0],     &c->cnt[1],       &c->vox[0],    &c->vox[1],     &c->leaves,
+                     &c->sel_flags, &c->sel_data,   &c->cursors};
     for (DevBuf* b : all) release(c, *b);
     delete c;
 }

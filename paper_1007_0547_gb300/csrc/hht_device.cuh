@@ -107,27 +107,30 @@ constexpr uint32_t kSpinLimit = 1u << 22;  // ~0.5-1 s with the back-off below
 // ----------------------------------------------------------------- look-back scan
 // Per tile: flag word (epoch << 2 | state), state 1 = aggregate published,
 // 2 = inclusive prefix published; data[tile * 2C + c] = aggregate,
-// data[tile * 2C + C + c] = inclusive.  Called by all 32 lanes of one warp;
-// returns the exclusive prefix of tile t (identical in every lane).
+// data[tile * 2C + C + c] = inclusive.
+//
+// The scan is split in two so that a tile can publish its aggregate as soon
+// as it is known and do other work before it needs its prefix:
+// publish_aggregate() (one lane) and resolve_prefix() (all 32 lanes of one
+// warp; returns the exclusive prefix of tile t and publishes its inclusive
+// value).
 template <int C>
-__device__ void tile_lookback(uint32_t* flags, uint64_t* data, uint32_t t, uint32_t epoch, const uint64_t (&agg)[C],
-                              uint64_t (&prefix)[C], DeviceStatus* status) {
+__device__ __forceinline__ void publish_aggregate(uint32_t* flags, uint64_t* data, uint32_t t, uint32_t epoch,
+                                                  const uint64_t (&agg)[C]) {
+    // tile 0's aggregate is already its inclusive prefix
+    const int slot = (t == 0) ? C : 0;
+#pragma unroll
+    for (int c = 0; c < C; ++c) st_relaxed_u64(&data[(size_t)t * 2 * C + slot + c], agg[c]);
+    st_release_u32(&flags[t], (epoch << 2) | (t == 0 ? 2u : 1u));
+}
+
+template <int C>
+__device__ void resolve_prefix(uint32_t* flags, uint64_t* data, uint32_t t, uint32_t epoch, const uint64_t (&agg)[C],
+                               uint64_t (&prefix)[C], DeviceStatus* status) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int c = 0; c < C; ++c) prefix[c] = 0;
-    if (t == 0) {
-        if (lane == 0) {
-#pragma unroll
-            for (int c = 0; c < C; ++c) st_relaxed_u64(&data[(size_t)t * 2 * C + C + c], agg[c]);
-            st_release_u32(&flags[t], (epoch << 2) | 2u);
-        }
-        return;
-    }
-    if (lane == 0) {
-#pragma unroll
-        for (int c = 0; c < C; ++c) st_relaxed_u64(&data[(size_t)t * 2 * C + c], agg[c]);
-        st_release_u32(&flags[t], (epoch << 2) | 1u);
-    }
+    if (t == 0) return;
     int64_t top = (int64_t)t - 1;
     // once any wait of this job has expired, no further wait is started
     bool timed_out = (*reinterpret_cast<volatile uint32_t*>(&status->err) & kErrTimeout) != 0u;
@@ -152,27 +155,33 @@ __device__ void tile_lookback(uint32_t* flags, uint64_t* data, uint32_t t, uint3
         timed_out = __any_sync(0xffffffffu, timed_out);
         const uint32_t inc = __ballot_sync(0xffffffffu, state == 2u);
         const int first = inc ? (__ffs(inc) - 1) : 32;
-        uint64_t v[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-            v[c] = 0;
-            if (idx >= 0 && lane <= first) {
-                const bool use_inc = (lane == first);
-                v[c] = timed_out ? 0 : ld_relaxed_u64(&data[(size_t)idx * 2 * C + (use_inc ? C : 0) + c]);
-            }
+            uint64_t v = 0;
+            if (idx >= 0 && lane <= first && !timed_out)
+                v = ld_relaxed_u64(&data[(size_t)idx * 2 * C + (lane == first ? C : 0) + c]);
 #pragma unroll
-            for (int off = 16; off > 0; off >>= 1) v[c] += __shfl_xor_sync(0xffffffffu, v[c], off);
-            prefix[c] += v[c];
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            prefix[c] += v;
         }
         if (inc) break;
         top -= 32;
     }
-    if (__any_sync(0xffffffffu, timed_out) && lane == 0) atomicOr(&status->err, kErrTimeout);
+    if (timed_out && lane == 0) atomicOr(&status->err, kErrTimeout);
     if (lane == 0) {
 #pragma unroll
         for (int c = 0; c < C; ++c) st_relaxed_u64(&data[(size_t)t * 2 * C + C + c], prefix[c] + agg[c]);
         st_release_u32(&flags[t], (epoch << 2) | 2u);
     }
+}
+
+// Both halves back to back (for kernels with nothing to overlap).
+template <int C>
+__device__ __forceinline__ void tile_lookback(uint32_t* flags, uint64_t* data, uint32_t t, uint32_t epoch,
+                                              const uint64_t (&agg)[C], uint64_t (&prefix)[C], DeviceStatus* status) {
+    if ((threadIdx.x & 31) == 0) publish_aggregate<C>(flags, data, t, epoch, agg);
+    __syncwarp();
+    resolve_prefix<C>(flags, data, t, epoch, agg, prefix, status);
 }
 
 // End-of-launch protocol for a scan: the last block to finish resets the tile

@@ -15,6 +15,11 @@
 
 #include <cstdint>
 
+#ifndef __CUDACC__
+#define __host__
+#define __device__
+#endif
+
 namespace hht {
 
 constexpr int kMaxDepth = 24;
@@ -57,15 +62,22 @@ struct Region {
 };
 static_assert(sizeof(Region) == 16, "region record is 16 bytes");
 
-// Filled by the selection of the next level: where the region's passed
-// children are and which of them keep a voter list.
-struct RegionLink {
-    uint32_t child_base;  // index of the first passed child in the next level's records
-    uint8_t pass_mask;    // bit q: child q (NE, NW, SW, SE) reached T and is a region of the next level
-    uint8_t write_mask;   // bit q: child q's voters are copied to the next voter stream
-    uint16_t pad;
+// Everything the pass kernel needs about a parent region, in one 16-byte
+// record written by the selection of the next level: the parent's cell, its
+// geometry and where its passed children are.
+struct PassRegion {
+    uint32_t a, b;        // parent cell indices at its level
+    uint32_t child_base;  // record index of its first passed child at the next level
+    uint32_t packed;      // see pack_region()
 };
-static_assert(sizeof(RegionLink) == 8, "link record is 8 bytes");
+static_assert(sizeof(PassRegion) == 16, "pass region record is 16 bytes");
+
+// packed: bits 0-3 pass mask (child q reached T and is a region of the next
+// level), 4-7 write mask (child q's voters are copied to the next stream),
+// 8-12 log2 of the parent side S in cells, 13-17 lL, 18-22 depth D.
+__host__ __device__ inline uint32_t pack_region(uint32_t pass, uint32_t write, uint32_t sS, uint32_t lL, uint32_t D) {
+    return pass | (write << 4) | (sS << 8) | (lL << 13) | (D << 18);
+}
 
 // Leaf as produced on the device (before sorting): unit, cell, votes.
 struct DevLeaf {
@@ -76,11 +88,8 @@ struct DevLeaf {
 struct LevelInfo {
     uint64_t n_regions;      // passed regions of this level (records)
     uint64_t n_voters;       // length of this level's voter stream
-    uint64_t Q[4];           // start of each child quadrant's block in the next stream
-    uint64_t kept[4];        // voters copied per quadrant (reduction target)
     uint64_t n_leaves;       // leaves emitted at this level
-    uint64_t n_records_acc;  // scan total helpers
-    uint64_t pad[4];
+    uint64_t pad[12];
 };
 
 // State of one single-pass (decoupled look-back) scan: tile ids are claimed in
@@ -112,10 +121,11 @@ struct DeviceStatus {
 struct LevelArgs {
     const Unit* units;
     const Region* parents;     // records of level s-1
-    RegionLink* links;         // links of level s-1 (written by select, read by pass)
+    PassRegion* pregions;      // pass records of level s-1 (written by select, read by pass)
     const uint32_t* parent_cnt;// [n_parents][4] vote counters of level-s children
     Region* children;          // records of level s (written by select)
     uint32_t* child_cnt;       // [n_children][4] counters of level s+1 (zeroed by select, filled by pass)
+    unsigned long long* cursor;// [n_children] next free slot of each child's voter segment
     const Voter* vin;          // voter stream of level s-1
     Voter* vout;               // voter stream of level s
     DevLeaf* leaves;
@@ -146,10 +156,5 @@ int occupancy_pass(bool int64_path);
 // Rewrite each leaf's unit (2 * image + half) to its half.
 int launch_unit_to_half(void* leaves, uint64_t n, void* stream);
 
-// Leaf sort (hht_sort.cu): stable LSD radix sort of leaves by (unit, i, j).
-size_t sort_scratch_bytes(uint64_t n);
-int launch_leaf_sort(DevLeaf* leaves, DevLeaf* tmp, uint64_t n, int unit_bits, int depth_bits,
-                     void* scratch, size_t scratch_bytes, DeviceStatus* status, int num_sms, void* stream,
-                     int* kernels_launched);
 
 }  // namespace hht

@@ -137,15 +137,13 @@ constexpr int kSelTile = kSelTPB * kSelPPT;
 
 __global__ void __launch_bounds__(kSelTPB) select_kernel(LevelArgs a) {
     __shared__ uint32_t s_slot;
-    __shared__ uint32_t s_wrec[8], s_wleaf[8];
-    __shared__ uint64_t s_prefix[2];
-    __shared__ unsigned long long s_kept[4];
-    __shared__ unsigned long long s_nrec, s_nleaf;
+    __shared__ uint32_t s_wrec[8], s_wleaf[8], s_wvox[8];
+    __shared__ uint64_t s_prefix[3];
+    __shared__ unsigned long long s_nrec, s_nleaf, s_nvox;
 
     const int s = a.level;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid < 4) s_kept[tid] = 0;
-    if (tid == 0) { s_nrec = 0; s_nleaf = 0; }
+    if (tid == 0) { s_nrec = 0; s_nleaf = 0; s_nvox = 0; }
     const uint64_t np = a.info_prev->n_regions;
     const bool aborted = job_aborted(a.status);
     const uint32_t ntiles = aborted ? 0u : (uint32_t)((np + kSelTile - 1) / kSelTile);
@@ -158,10 +156,9 @@ __global__ void __launch_bounds__(kSelTPB) select_kernel(LevelArgs a) {
         const uint64_t base = (uint64_t)t * kSelTile + (uint64_t)tid * kSelPPT;
 
         uint32_t cnt[kSelPPT][4];
-        uint32_t pass[kSelPPT], wmask[kSelPPT];
+        uint32_t pass[kSelPPT], wmask[kSelPPT], geo[kSelPPT];
         bool leafy[kSelPPT];
-        uint32_t my_rec = 0, my_leaf = 0;
-        unsigned long long kept[4] = {0, 0, 0, 0};
+        uint32_t my_rec = 0, my_leaf = 0, my_vox = 0;
         // statistics run (records are sorted by unit)
         uint32_t run_unit = kNoRegion;
         int run_lev = 0;
@@ -169,7 +166,7 @@ __global__ void __launch_bounds__(kSelTPB) select_kernel(LevelArgs a) {
 #pragma unroll
         for (int j = 0; j < kSelPPT; ++j) {
             const uint64_t p = base + j;
-            pass[j] = 0; wmask[j] = 0; leafy[j] = false;
+            pass[j] = 0; wmask[j] = 0; leafy[j] = false; geo[j] = 0;
 #pragma unroll
             for (int q = 0; q < 4; ++q) cnt[j][q] = 0;
             if (p >= np) continue;
@@ -186,11 +183,13 @@ __global__ void __launch_bounds__(kSelTPB) select_kernel(LevelArgs a) {
             // voters of a level-lev child are read by the next pass only when
             // that pass still has a level below lev + 1 to count
             wmask[j] = (!leafy[j] && lev <= U.D - 2) ? pm : 0u;
+            // geometry of this parent for the pass: side S = 2^(D - lev + 1) cells
+            geo[j] = pack_region(0u, 0u, (uint32_t)(U.D - lev + 1), (uint32_t)U.lL, (uint32_t)U.D);
             const uint32_t np_c = __popc(pm);
             if (leafy[j]) my_leaf += np_c; else my_rec += np_c;
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-                if (wmask[j] & (1u << q)) kept[q] += cnt[j][q];
+                if (wmask[j] & (1u << q)) my_vox += cnt[j][q];
             const unsigned long long votes = (unsigned long long)cnt[j][0] + cnt[j][1] + cnt[j][2] + cnt[j][3];
             if (R.unit != run_unit) {
                 if (run_unit != kNoRegion) {
@@ -227,55 +226,58 @@ __global__ void __launch_bounds__(kSelTPB) select_kernel(LevelArgs a) {
                 }
             }
         }
-        // block-wide kept totals
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (kept[q]) atomicAdd(&s_kept[q], kept[q]);
-
-        // scan of (records, leaves) over the tile
-        uint32_t inc_rec = my_rec, inc_leaf = my_leaf;
+        // scan of (records, leaves, copied voters) over the tile
+        uint32_t inc_rec = my_rec, inc_leaf = my_leaf, inc_vox = my_vox;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const uint32_t r = __shfl_up_sync(0xffffffffu, inc_rec, off);
             const uint32_t l = __shfl_up_sync(0xffffffffu, inc_leaf, off);
-            if (lane >= off) { inc_rec += r; inc_leaf += l; }
+            const uint32_t v = __shfl_up_sync(0xffffffffu, inc_vox, off);
+            if (lane >= off) { inc_rec += r; inc_leaf += l; inc_vox += v; }
         }
-        if (lane == 31) { s_wrec[warp] = inc_rec; s_wleaf[warp] = inc_leaf; }
+        if (lane == 31) { s_wrec[warp] = inc_rec; s_wleaf[warp] = inc_leaf; s_wvox[warp] = inc_vox; }
         __syncthreads();
         if (warp == 0) {
-            uint32_t wr = lane < 8 ? s_wrec[lane] : 0u, wl = lane < 8 ? s_wleaf[lane] : 0u;
-            uint32_t ir = wr, il = wl;
+            const uint32_t wr = lane < 8 ? s_wrec[lane] : 0u, wl = lane < 8 ? s_wleaf[lane] : 0u;
+            const uint32_t wv = lane < 8 ? s_wvox[lane] : 0u;
+            uint32_t ir = wr, il = wl, iv = wv;
 #pragma unroll
             for (int off = 1; off < 8; off <<= 1) {
                 const uint32_t r = __shfl_up_sync(0xffffffffu, ir, off);
                 const uint32_t l = __shfl_up_sync(0xffffffffu, il, off);
-                if (lane >= off) { ir += r; il += l; }
+                const uint32_t v = __shfl_up_sync(0xffffffffu, iv, off);
+                if (lane >= off) { ir += r; il += l; iv += v; }
             }
-            const uint64_t agg[2] = {__shfl_sync(0xffffffffu, ir, 7), __shfl_sync(0xffffffffu, il, 7)};
-            if (lane < 8) { s_wrec[lane] = ir - wr; s_wleaf[lane] = il - wl; }
-            uint64_t pre[2];
-            tile_lookback<2>(a.tile_flags, a.tile_data, t, epoch, agg, pre, a.status);
+            const uint64_t agg[3] = {__shfl_sync(0xffffffffu, ir, 7), __shfl_sync(0xffffffffu, il, 7),
+                                     __shfl_sync(0xffffffffu, iv, 7)};
+            __syncwarp();
+            if (lane < 8) { s_wrec[lane] = ir - wr; s_wleaf[lane] = il - wl; s_wvox[lane] = iv - wv; }
+            uint64_t pre[3];
+            tile_lookback<3>(a.tile_flags, a.tile_data, t, epoch, agg, pre, a.status);
             if (lane == 0) {
                 s_prefix[0] = pre[0];
                 s_prefix[1] = pre[1];
+                s_prefix[2] = pre[2];
                 s_nrec += agg[0];
                 s_nleaf += agg[1];
+                s_nvox += agg[2];
             }
         }
         __syncthreads();
         uint64_t rec = s_prefix[0] + s_wrec[warp] + (inc_rec - my_rec);
         uint64_t leaf = leaf_base + s_prefix[1] + s_wleaf[warp] + (inc_leaf - my_leaf);
+        uint64_t vox = s_prefix[2] + s_wvox[warp] + (inc_vox - my_vox);
 #pragma unroll
         for (int j = 0; j < kSelPPT; ++j) {
             const uint64_t p = base + j;
             if (p >= np) continue;
             const Region R = a.parents[p];
-            RegionLink lk;
-            lk.child_base = (uint32_t)rec;
-            lk.pass_mask = leafy[j] ? 0 : (uint8_t)pass[j];
-            lk.write_mask = (uint8_t)wmask[j];
-            lk.pad = 0;
-            a.links[p] = lk;
+            PassRegion pr;
+            pr.a = R.a;
+            pr.b = R.b;
+            pr.child_base = (uint32_t)rec;
+            pr.packed = geo[j] | (leafy[j] ? 0u : pass[j]) | (wmask[j] << 4);
+            a.pregions[p] = pr;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 if (!(pass[j] & (1u << q))) continue;
@@ -295,26 +297,24 @@ __global__ void __launch_bounds__(kSelTPB) select_kernel(LevelArgs a) {
                         c.unit = R.unit; c.a = ca; c.b = cb; c.count = cnt[j][q];
                         a.children[rec] = c;
                         reinterpret_cast<uint4*>(a.child_cnt)[rec] = make_uint4(0, 0, 0, 0);
+                        // the child's voters fill [vox, vox + count) of the next stream
+                        a.cursor[rec] = vox;
                     }
+                    if (wmask[j] & (1u << q)) vox += cnt[j][q];
                     ++rec;
                 }
             }
         }
     }
     __syncthreads();
-    if (tid < 4 && s_kept[tid]) atomicAdd((unsigned long long*)&a.info->kept[tid], s_kept[tid]);
     if (tid == 0) {
         if (s_nrec) atomicAdd((unsigned long long*)&a.info->n_regions, s_nrec);
         if (s_nleaf) atomicAdd((unsigned long long*)&a.info->n_leaves, s_nleaf);
+        if (s_nvox) atomicAdd((unsigned long long*)&a.info->n_voters, s_nvox);
     }
     if (scan_finish(a.scan)) {
         volatile LevelInfo* info = a.info;
-        uint64_t q0 = 0;
-        for (int q = 0; q < 4; ++q) {
-            info->Q[q] = q0;
-            q0 += info->kept[q];
-        }
-        info->n_voters = q0;
+        const uint64_t q0 = info->n_voters;
         const uint64_t nl = info->n_leaves;
         const uint64_t total_leaves = leaf_base + nl;
         if (info->n_regions > a.cap_children || q0 > a.cap_voters || total_leaves > a.cap_leaves)
@@ -327,190 +327,208 @@ __global__ void __launch_bounds__(kSelTPB) select_kernel(LevelArgs a) {
 // ============================================================================ pass
 namespace {
 constexpr int kPassTPB = 256;
-constexpr int kPassVPT = 8;
-constexpr int kPassTile = kPassTPB * kPassVPT;
 
-// Add a run's grandchild counts (byte counters acc[alpha] >> 8*beta) to the
-// level-(s+1) counters of the parent's passed children.
-__device__ __forceinline__ void flush_rows(uint32_t* __restrict__ cnt, const RegionLink lk, const uint32_t (&acc)[4]) {
+// Child record index of quadrant q of a parent (its passed children are
+// stored consecutively in quadrant order).
+__device__ __forceinline__ uint32_t child_index(const PassRegion& pr, int q) {
+    return pr.child_base + __popc(pr.packed & 0xfu & ((1u << q) - 1u));
+}
+
+// Add grandchild counts of one parent to the level-(s+1) counters of its
+// passed children.  c16[2*alpha + (beta & 1)] holds the counts of cells
+// (alpha, beta) and (alpha, beta + 2) in its low and high 16 bits.
+__device__ __forceinline__ void add_counts(uint32_t* __restrict__ cnt, const PassRegion& pr, const uint32_t (&c16)[8]) {
 #pragma unroll
     for (int al = 0; al < 4; ++al) {
-        if (!acc[al]) continue;
 #pragma unroll
         for (int be = 0; be < 4; ++be) {
-            const uint32_t c = (acc[al] >> (8 * be)) & 0xffu;
+            const uint32_t word = c16[2 * al + (be & 1)];
+            const uint32_t c = (be >> 1) ? (word >> 16) : (word & 0xffffu);
             if (!c) continue;
             const int q = quad_of(al >> 1, be >> 1), g = quad_of(al & 1, be & 1);
-            const uint32_t child = lk.child_base + __popc((uint32_t)lk.pass_mask & ((1u << q) - 1u));
-            atomicAdd(&cnt[4 * (size_t)child + g], c);
+            atomicAdd(&cnt[4 * (size_t)child_index(pr, q) + g], c);
         }
     }
 }
+
+// Per-lane byte counters rows[alpha] (byte beta) -> 16-bit pairs summed over
+// the lanes of `mask` (every lane of the mask must call this).
+__device__ __forceinline__ void reduce_rows(const uint32_t (&rows)[4], uint32_t mask, uint32_t (&c16)[8]) {
+#pragma unroll
+    for (int al = 0; al < 4; ++al) {
+        c16[2 * al] = __reduce_add_sync(mask, rows[al] & 0x00ff00ffu);             // beta 0 and 2
+        c16[2 * al + 1] = __reduce_add_sync(mask, (rows[al] >> 8) & 0x00ff00ffu);  // beta 1 and 3
+    }
+}
+
+// Grandchild votes of one voter as byte counters: row alpha of the 4 x 4
+// cells, byte beta.
+__device__ __forceinline__ void add_rows(uint32_t (&rows)[4], uint32_t gv) {
+#pragma unroll
+    for (int al = 0; al < 4; ++al) rows[al] += spread4((gv >> (5 * al)) & 0xfu);
+}
+
+// Shift counts and grid constants of one parent region for the corner grid
+// of its voters.
+template <typename I>
+struct ParentGeo {
+    PassRegion pr;
+    I Gr;
+    int32_t ra;
+    int sh_xa, sh_dI, k_dJ, D;
+    __device__ __forceinline__ void load(const PassRegion* p, uint32_t r) {
+        pr = p[r];
+        const int sS = (pr.packed >> 8) & 31, lL = (pr.packed >> 13) & 31;
+        D = (pr.packed >> 18) & 31;
+        // G at the parent's SW vertex (aS, bS): 4L*bS + 2x*aS - 2LK - K(x+y)
+        Gr = (I(pr.b) << (sS + lL + 2)) - (I(1) << (lL + D + 1));
+        ra = (int32_t)pr.a;
+        sh_xa = sS + 1;
+        sh_dI = sS - 1;  // quarter step h = S/4: 2x*h = x << (sS - 1)
+        k_dJ = lL + sS;  // 4L*h = 2^(lL + sS)
+    }
+};
 }  // namespace
 
+// One step of the level loop over the voter stream of the parents.  Every
+// warp owns a contiguous slice of the stream and walks it 32 voters at a
+// time (one coalesced 8-byte record per lane):
+//   - the exact 5 x 5 corner-sign grid of the voter's parent gives the 4-bit
+//     codes of the four children and of the sixteen grandchildren;
+//   - a voter of a passed child whose list is kept is appended to that
+//     child's segment of the next stream (segments were sized by the
+//     selection; one atomic per child and warp step reserves the slots);
+//   - grandchild votes of passed children are accumulated in per-lane byte
+//     counters while the parent stays the same, then summed across the warp
+//     (redux.sync) and added to the next level's counters.
+// Within a child's segment the voter order depends on scheduling; no result
+// depends on it (counts, leaves and statistics are order-free).
 template <typename I>
 __global__ void __launch_bounds__(kPassTPB) pass_kernel(LevelArgs a) {
-    __shared__ uint32_t s_slot;
-    __shared__ uint32_t s_wlo[8], s_whi[8];
-    __shared__ uint64_t s_prefix[4];
-
-    const int s = a.level;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
     const uint64_t nin = a.info_prev->n_voters;
-    const bool aborted = job_aborted(a.status);
-    const uint32_t ntiles = aborted ? 0u : (uint32_t)((nin + kPassTile - 1) / kPassTile);
-    const uint32_t epoch = a.scan->epoch;
-    uint64_t Q[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) Q[q] = a.info->Q[q];
+    if (job_aborted(a.status)) return;
+    const uint64_t nwarps = (uint64_t)gridDim.x * (kPassTPB / 32);
+    const uint64_t wid = (uint64_t)blockIdx.x * (kPassTPB / 32) + (threadIdx.x >> 5);
+    const uint64_t per = (((nin + nwarps - 1) / nwarps) + 31) & ~uint64_t(31);
+    const uint64_t beg = wid * per;
+    const uint64_t end = beg + per < nin ? beg + per : nin;
+    if (beg >= end) return;
+    const uint2* __restrict__ vin = reinterpret_cast<const uint2*>(a.vin);
+    uint2* __restrict__ vout = reinterpret_cast<uint2*>(a.vout);
 
-    while (true) {
-        const uint32_t t = claim_tile(a.scan, &s_slot);
-        if (t >= ntiles) break;
-        const uint64_t base = (uint64_t)t * kPassTile + (uint64_t)tid * kPassVPT;
+    // the run being counted: warp-uniform parent and per-lane byte counters
+    uint32_t cur = kNoRegion;
+    ParentGeo<I> cg;
+    uint32_t rows[4] = {0u, 0u, 0u, 0u};
+    uint32_t steps = 0;
 
-        Voter v[kPassVPT];
-        if (base + kPassVPT <= nin) {
-            const uint4* src = reinterpret_cast<const uint4*>(a.vin + base);
+    uint2 nxt = (beg + lane < end) ? vin[beg + lane] : make_uint2(0u, kNoRegion);
+    for (uint64_t s0 = beg; s0 < end; s0 += 32) {
+        const uint2 rec = nxt;
+        nxt = (s0 + 32 + lane < end) ? vin[s0 + 32 + lane] : make_uint2(0u, kNoRegion);
+        const uint32_t r = rec.y;
+        const bool valid = r != kNoRegion;
+        const int last = (int)((end - s0 < 32 ? end - s0 : 32) - 1);
+        const uint32_t r0 = __shfl_sync(0xffffffffu, r, 0);
+        const uint32_t rl = __shfl_sync(0xffffffffu, r, last);
+        const bool uni = (r0 == rl);  // the stream is grouped by parent
+
+        // ---- parent geometry of this lane's voter
+        if (rl != cur && uni) {
+            // a new run starts with this step: settle the old one first
+            if (cur != kNoRegion) {
+                uint32_t c16[8];
+                reduce_rows(rows, 0xffffffffu, c16);
+                if (lane == 0) add_counts(a.child_cnt, cg.pr, c16);
+            }
+            rows[0] = rows[1] = rows[2] = rows[3] = 0u;
+            steps = 0;
+            cur = rl;
+            cg.load(a.pregions, cur);
+        }
+        ParentGeo<I> g = cg;
+        if (!uni && valid && r != cur) g.load(a.pregions, r);
+
+        // ---- codes
+        uint32_t kw = 0u, gv = 0u;
+        const int32_t x = (int16_t)(rec.x & 0xffffu), y = (int16_t)(rec.x >> 16);
+        if (valid) {
+            const I G0 = g.Gr + ((I(x) * I(g.ra)) << g.sh_xa) - (I(x + y) << g.D);
+            const uint32_t M = below_mask<I, 5>(G0, I(x) << g.sh_dI, g.k_dJ);
+            const uint32_t cv = child_votes5(M);
+            kw = cv & (g.pr.packed >> 4) & 0xfu;
+            gv = crossing_cells<5, 1>(M) & grandchild_mask(cv & g.pr.packed & 0xfu);
+        }
+
+        // ---- copies into the children's segments
+        const uint32_t peers = uni ? 0xffffffffu : __match_any_sync(0xffffffffu, r);
 #pragma unroll
-            for (int k = 0; k < kPassVPT / 2; ++k) {
-                const uint4 w = src[k];
-                v[2 * k].x = (int16_t)(w.x & 0xffffu); v[2 * k].y = (int16_t)(w.x >> 16); v[2 * k].region = w.y;
-                v[2 * k + 1].x = (int16_t)(w.z & 0xffffu); v[2 * k + 1].y = (int16_t)(w.z >> 16); v[2 * k + 1].region = w.w;
+        for (int q = 0; q < 4; ++q) {
+            const bool keep = (kw >> q) & 1u;
+            const uint32_t b = __ballot_sync(0xffffffffu, keep);
+            if (!b) continue;
+            const uint32_t gm = b & peers;
+            const int leader = keep ? __ffs(gm) - 1 : lane;
+            unsigned long long base = 0;
+            if (keep && lane == leader) base = atomicAdd(&a.cursor[child_index(g.pr, q)], (unsigned long long)__popc(gm));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (keep) {
+                const uint64_t p = base + __popc(gm & lt);
+                if (p < a.cap_voters) vout[p] = make_uint2(rec.x, child_index(g.pr, q));
+            }
+        }
+
+        // ---- grandchild counts
+        if (uni) {
+            add_rows(rows, gv);
+            if (++steps == 255) {  // byte counters are full: settle the run so far
+                uint32_t c16[8];
+                reduce_rows(rows, 0xffffffffu, c16);
+                if (lane == 0) add_counts(a.child_cnt, cg.pr, c16);
+                rows[0] = rows[1] = rows[2] = rows[3] = 0u;
+                steps = 0;
             }
         } else {
-#pragma unroll
-            for (int j = 0; j < kPassVPT; ++j) {
-                if (base + j < nin) v[j] = a.vin[base + j];
-                else { v[j].x = 0; v[j].y = 0; v[j].region = kNoRegion; }
+            // a run boundary inside the step: settle the current run, count
+            // every other parent's lanes of this step on their own, and start
+            // the run of the last lane's parent
+            if (cur != kNoRegion) {
+                uint32_t c16[8];
+                reduce_rows(rows, 0xffffffffu, c16);
+                if (lane == 0) add_counts(a.child_cnt, cg.pr, c16);
+                rows[0] = rows[1] = rows[2] = rows[3] = 0u;
+                steps = 0;
             }
-        }
-
-        // ---- codes, grandchild counts (run-length by region), copy masks
-        uint32_t cur = kNoRegion;
-        RegionLink lk{};
-        I Gr = 0;
-        uint32_t ra = 0;
-        int sh_xa = 0, D = 0, sh_dI = 0, k_dJ = 0;
-        uint32_t acc[4] = {0u, 0u, 0u, 0u};
-        uint32_t kw_all = 0, tsum = 0;
-#pragma unroll
-        for (int j = 0; j < kPassVPT; ++j) {
-            const uint32_t r = v[j].region;
-            if (r == kNoRegion) continue;
-            if (r != cur) {
-                if (cur != kNoRegion) {
-                    flush_rows(a.child_cnt, lk, acc);
-                    acc[0] = acc[1] = acc[2] = acc[3] = 0u;
+            uint32_t own[4] = {0u, 0u, 0u, 0u};
+            add_rows(own, gv);
+            const bool mine = valid && r == rl;
+            uint32_t rest = __ballot_sync(0xffffffffu, valid && !mine);
+            while (rest) {
+                const int leader = __ffs(rest) - 1;
+                const uint32_t rg = __shfl_sync(0xffffffffu, r, leader);
+                const uint32_t gmask = __ballot_sync(0xffffffffu, valid && r == rg);
+                if (gmask & (1u << lane)) {
+                    uint32_t c16[8];
+                    reduce_rows(own, gmask, c16);
+                    if (lane == leader) add_counts(a.child_cnt, g.pr, c16);
                 }
-                cur = r;
-                const Region R = a.parents[r];
-                lk = a.links[r];
-                const Unit U = a.units[R.unit];
-                D = U.D;
-                const int lL = U.lL;
-                const int sS = D - (s - U.t0) + 1;  // parent region side S = 2^sS cells
-                // G at the parent's SW vertex (aS, bS): 4L*bS + 2x*aS - 2LK - K(x+y)
-                Gr = (I(R.b) << (sS + lL + 2)) - (I(1) << (lL + D + 1));
-                ra = R.a;
-                sh_xa = sS + 1;
-                sh_dI = sS - 1;   // quarter step h = S/4: 2x*h = x << (sS - 1)
-                k_dJ = lL + sS;   // 4L*h = 2^(lL + sS)
+                rest &= ~gmask;
             }
-            const int32_t x = v[j].x, y = v[j].y;
-            const I G0 = Gr + (I(x) * I(ra) << sh_xa) - (I(x + y) << D);
-            const uint32_t M = below_mask<I, 5>(G0, I(x) << sh_dI, k_dJ);
-            const uint32_t cv = child_votes5(M);
-            const uint32_t kc = cv & lk.pass_mask;
-            const uint32_t kw = cv & lk.write_mask;
-            const uint32_t gv = crossing_cells<5, 1>(M) & grandchild_mask(kc);
-#pragma unroll
-            for (int al = 0; al < 4; ++al) acc[al] += spread4((gv >> (5 * al)) & 0xfu);
-            kw_all |= kw << (4 * j);
-            tsum += spread4(kw);
-        }
-        // tail run: merge equal regions across the warp, first lane adds
-        {
-            uint32_t w[8];
-#pragma unroll
-            for (int al = 0; al < 4; ++al) {
-                w[2 * al] = acc[al] & 0x00ff00ffu;             // beta 0 and 2
-                w[2 * al + 1] = (acc[al] >> 8) & 0x00ff00ffu;  // beta 1 and 3
+            cur = rl;
+            cg.load(a.pregions, cur);
+            if (mine) {
+                rows[0] = own[0]; rows[1] = own[1]; rows[2] = own[2]; rows[3] = own[3];
             }
-            warp_segmented_total<8>(cur, w);
-            if (run_head(cur)) {
-                const RegionLink hl = a.links[cur];
-                // 16-bit sums per (alpha, beta): a warp total may exceed 255
-#pragma unroll
-                for (int al = 0; al < 4; ++al) {
-#pragma unroll
-                    for (int be = 0; be < 4; ++be) {
-                        const uint32_t word = w[2 * al + (be & 1)];
-                        const uint32_t c = (be >> 1) ? (word >> 16) : (word & 0xffffu);
-                        if (!c) continue;
-                        const int q = quad_of(al >> 1, be >> 1), g = quad_of(al & 1, be & 1);
-                        const uint32_t child = hl.child_base + __popc((uint32_t)hl.pass_mask & ((1u << q) - 1u));
-                        atomicAdd(&a.child_cnt[4 * (size_t)child + g], c);
-                    }
-                }
-            }
-        }
-
-        // ---- stable copy: scan of per-quadrant copy counts over the tile
-        uint32_t lo = (tsum & 0xffu) | ((tsum & 0xff00u) << 8);          // quadrants 0, 1
-        uint32_t hi = ((tsum >> 16) & 0xffu) | ((tsum >> 8) & 0xff0000u); // quadrants 2, 3
-        const uint32_t own_lo = lo, own_hi = hi;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const uint32_t l2 = __shfl_up_sync(0xffffffffu, lo, off);
-            const uint32_t h2 = __shfl_up_sync(0xffffffffu, hi, off);
-            if (lane >= off) { lo += l2; hi += h2; }
-        }
-        if (lane == 31) { s_wlo[warp] = lo; s_whi[warp] = hi; }
-        __syncthreads();
-        if (warp == 0) {
-            const uint32_t wl = lane < 8 ? s_wlo[lane] : 0u, wh = lane < 8 ? s_whi[lane] : 0u;
-            uint32_t il = wl, ih = wh;
-#pragma unroll
-            for (int off = 1; off < 8; off <<= 1) {
-                const uint32_t l2 = __shfl_up_sync(0xffffffffu, il, off);
-                const uint32_t h2 = __shfl_up_sync(0xffffffffu, ih, off);
-                if (lane >= off) { il += l2; ih += h2; }
-            }
-            const uint32_t tl = __shfl_sync(0xffffffffu, il, 7), th = __shfl_sync(0xffffffffu, ih, 7);
-            if (lane < 8) { s_wlo[lane] = il - wl; s_whi[lane] = ih - wh; }
-            const uint64_t agg[4] = {tl & 0xffffu, tl >> 16, th & 0xffffu, th >> 16};
-            uint64_t pre[4];
-            tile_lookback<4>(a.tile_flags, a.tile_data, t, epoch, agg, pre, a.status);
-            if (lane < 4) s_prefix[lane] = pre[lane == 0 ? 0 : lane == 1 ? 1 : lane == 2 ? 2 : 3];
-        }
-        __syncthreads();
-        if (kw_all) {
-            const uint32_t el = lo - own_lo + s_wlo[warp], eh = hi - own_hi + s_whi[warp];
-            uint64_t pos[4] = {Q[0] + s_prefix[0] + (el & 0xffffu), Q[1] + s_prefix[1] + (el >> 16),
-                               Q[2] + s_prefix[2] + (eh & 0xffffu), Q[3] + s_prefix[3] + (eh >> 16)};
-            uint32_t lr = kNoRegion;
-            RegionLink ll{};
-#pragma unroll
-            for (int j = 0; j < kPassVPT; ++j) {
-                const uint32_t kw = (kw_all >> (4 * j)) & 0xfu;
-                if (!kw) continue;
-                if (v[j].region != lr) { lr = v[j].region; ll = a.links[lr]; }
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    if (!(kw & (1u << q))) continue;
-                    const uint64_t p = pos[q]++;
-                    if (p < a.cap_voters) {
-                        Voter o;
-                        o.x = v[j].x; o.y = v[j].y;
-                        o.region = ll.child_base + __popc((uint32_t)ll.pass_mask & ((1u << q) - 1u));
-                        a.vout[p] = o;
-                    }
-                }
-            }
+            steps = 1;
         }
     }
-    scan_finish(a.scan);
+    if (cur != kNoRegion) {
+        uint32_t c16[8];
+        reduce_rows(rows, 0xffffffffu, c16);
+        if (lane == 0) add_counts(a.child_cnt, cg.pr, c16);
+    }
 }
 
 // ============================================================================ output fix-up

@@ -156,3 +156,25 @@ def closed_form(points, W: int, H: int, D: int, T: int):
             passed_prev, prev_counts = passed, counts
     leaves.sort()
     return leaves, stats
+
+
+def dfs_key(i: int, j: int, depth: int) -> int:
+    """Position of leaf cell (i, j) in the depth-first order of Section 3:
+    at each level the child digit is quad1..quad4 = NE, NW, SW, SE."""
+    key = 0
+    for l in range(depth - 1, -1, -1):
+        east, north = (i >> l) & 1, (j >> l) & 1
+        q = (0 if east else 1) if north else (3 if east else 2)
+        key = key * 4 + q
+    return key
+
+
+def dfs_keys(leaves: np.ndarray, depth: int) -> np.ndarray:
+    """Vectorised (half, dfs_key) as one int64 per leaf row (half, i, j, votes)."""
+    lv = np.asarray(leaves, dtype=np.int64).reshape(-1, 4)
+    key = np.zeros(len(lv), dtype=np.int64)
+    for l in range(depth - 1, -1, -1):
+        east, north = (lv[:, 1] >> l) & 1, (lv[:, 2] >> l) & 1
+        q = np.where(north == 1, np.where(east == 1, 0, 1), np.where(east == 1, 3, 2))
+        key = key * 4 + q
+    return (lv[:, 0] << 50) | key

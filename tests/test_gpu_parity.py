@@ -1,8 +1,9 @@
 """GPU parity: the CUDA library (through its C ABI) against the CPU oracle.
 
 Results are integers decided by exact comparisons, so every check is
-bit-exact: sorted leaves (half, i, j, votes) and the per-level statistics
-(tested, passed, votes, tests) of both halves.  Full-size workloads, where the
+bit-exact: the leaves (half, i, j, votes) in the order both sides emit them
+(the paper's depth-first order) and the per-level statistics (tested, passed,
+votes, tests) of both halves.  Full-size workloads, where the
 oracle would take minutes, are checked on sampled cells counted directly by
 the oracle, on the statistics of the levels a shallower oracle run reaches
 (a region's fate at level l does not depend on the depth below it), and on
@@ -13,6 +14,7 @@ import pytest
 
 import oracle
 import synth
+from tests import pins
 
 pytestmark = pytest.mark.gpu
 
@@ -42,8 +44,8 @@ def _same(got, want):
 def _props(res, T, depth):
     lv = res.leaves_numpy().astype(np.int64)
     if len(lv):
-        key = (lv[:, 0] << 50) | (lv[:, 1] << 25) | lv[:, 2]
-        assert np.all(np.diff(key) > 0), "leaves sorted by (half, i, j) and unique"
+        key = pins.dfs_keys(lv, depth)
+        assert np.all(np.diff(key) > 0), "leaves unique and in depth-first order, half 0 first"
         assert np.all(lv[:, 3] >= T)
         assert np.all(lv[:, 1] < (1 << depth)) and np.all(lv[:, 2] < (1 << depth))
     st = res.stats.astype(np.int64)

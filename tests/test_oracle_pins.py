@@ -28,7 +28,9 @@ def _load(name):
 
 
 def _as_list(leaves):
-    return [tuple(int(v) for v in r) for r in np.asarray(leaves).reshape(-1, 4)]
+    """Leaves as a list sorted by (half, i, j) (the pins produce that order)."""
+    return sorted(tuple(int(v) for v in r) for r in np.asarray(leaves).reshape(-1, 4))
+
 
 
 # ----------------------------------------------------------------- hand-worked examples
@@ -153,14 +155,21 @@ def test_code_alphabet():
         assert oracle.getcode(x, y, a * S, b * S, S, L, D) in allowed
 
 
+def test_leaves_come_in_depth_first_order():
+    for k in range(3):
+        img = synth.plain_128(index=k)
+        r = oracle.detect(img.points, img.W, img.H, img.depth, img.T)
+        keys = [(int(h), pins.dfs_key(int(i), int(j), img.depth)) for h, i, j, v in r.leaves]
+        assert keys == sorted(keys) and len(set(keys)) == len(keys)
+
+
 def test_transpose_symmetry():
     img = synth.plain_128(index=2)
     r = oracle.detect(img.points, img.W, img.H, img.depth, img.T)
     rt = oracle.detect(img.points[:, ::-1], img.H, img.W, img.depth, img.T)
     swapped = rt.leaves.copy()
     swapped[:, 0] = 1 - swapped[:, 0]
-    order = np.lexsort((swapped[:, 2], swapped[:, 1], swapped[:, 0]))
-    assert np.array_equal(r.leaves, swapped[order])
+    assert _as_list(r.leaves) == _as_list(swapped)
     assert np.array_equal(r.stats[0], rt.stats[1]) and np.array_equal(r.stats[1], rt.stats[0])
 
 
