@@ -122,8 +122,8 @@ void hht_destroy(hht_ctx *ctx);
  * out->leaves[0 .. n_leaves) hold the leaves in depth-first order (see above)
  * and out->stats[h][l] the statistics for levels 0..depth.
  * Errors: HHT_E_ARG (checked before any device work), HHT_E_RANGE (a point
- * outside the image), HHT_E_CAPACITY (out->n_leaves = required count; call
- * again with a larger buffer), HHT_E_NOMEM, HHT_E_TIMEOUT, HHT_E_CUDA.
+ * outside the image), HHT_E_CAPACITY (out->n_leaves = required count; fetch
+ * them with hht_fetch_leaves), HHT_E_NOMEM, HHT_E_TIMEOUT, HHT_E_CUDA.
  */
 int hht_detect(hht_ctx *ctx, const hht_point *points, int64_t n, int32_t W, int32_t H, int32_t depth,
                int32_t T, hht_result *out);
@@ -137,6 +137,18 @@ int hht_detect(hht_ctx *ctx, const hht_point *points, int64_t n, int32_t W, int3
  * outs[k].status holds that image's own code).
  */
 int hht_detect_batch(hht_ctx *ctx, const hht_image *images, int32_t count, hht_result *outs);
+
+/*
+ * Copy the leaves of image `index` (0 for hht_detect) of the last
+ * hht_detect / hht_detect_batch call on this context into `leaves` (host or
+ * device memory, `capacity` entries), without running anything again.  This
+ * completes the two-call protocol: after HHT_E_CAPACITY the caller allocates
+ * n_leaves entries and fetches them.  Valid until the next call that runs a
+ * detection on the context.  Errors: HHT_E_ARG (no such image, NULL buffer),
+ * HHT_E_CAPACITY (buffer smaller than the image's leaf count; nothing copied),
+ * HHT_E_CUDA.
+ */
+int hht_fetch_leaves(hht_ctx *ctx, int32_t index, hht_leaf *leaves, uint64_t capacity);
 
 /*
  * Serving interface.  hht_submit() queues one request and returns at once;

@@ -64,6 +64,11 @@ struct hht_ctx {
     hht::ServeState* serve = nullptr;
     std::mutex mu;
 
+    // leaves of the last job stay in `leaves` until the next job
+    // (hht_fetch_leaves): per image offset and count
+    std::vector<uint64_t> job_off, job_n;
+    uint64_t job_leaves = 0;
+
     // kernel timing (hht_profile_enable)
     bool profile = false;
     hht_profile_counters prof{};
@@ -227,7 +232,7 @@ constexpr int kPassTile = 256 * 8;  // voters per pass block below which fewer b
 // Run one wave of images through the level loop; fills outs[k] for k in
 // [0, count).  Returns HHT_OK or a job-level error (per-image errors are in
 // outs[k].status).
-int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs) {
+int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int job_first) {
     cudaStream_t st = c->stream;
     const int n_units = 2 * count;
     int Dmax = 0;
@@ -303,7 +308,9 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs) {
     CK(cudaMemcpyAsync(c->rec[0].p, roots.data(), n_units * sizeof(Region), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(c->cnt[0].p, 0, n_units * 4 * sizeof(uint32_t), st));
     CK(cudaMemsetAsync(c->status.p, 0, sizeof(DeviceStatus), st));
-    CK(cudaMemsetAsync(c->leaf_total.p, 0, sizeof(uint64_t), st));
+    // this wave's leaves follow those of the job's earlier waves
+    const uint64_t wave_leaf_base = c->job_leaves;
+    CK(cudaMemcpyAsync(c->leaf_total.p, &c->job_leaves, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(c->img_err.p, 0, count * sizeof(uint32_t), st));
 
     LevelInfo* d_infos = (LevelInfo*)c->infos.p;
@@ -321,7 +328,7 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs) {
     }
 
     // ---- level loop
-    uint64_t leaf_total = 0;
+    uint64_t leaf_total = wave_leaf_base;
     uint32_t err = 0;
     for (int s = 1; s <= Dmax; ++s) {
         const int pi = (s - 1) & 1, ci = s & 1;
@@ -426,9 +433,10 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs) {
     // every unit's leaves form one block in the order of the paper's
     // depth-first traversal, and blocks follow (depth, unit).  Only the unit
     // field is rewritten to the half.
-    if (leaf_total > 0) {
+    const uint64_t wave_leaves = leaf_total - wave_leaf_base;
+    if (wave_leaves > 0) {
         ProfScope ps(c, 3);
-        if (launch_unit_to_half(c->leaves.p, leaf_total, st) != 0) return HHT_E_CUDA;
+        if (launch_unit_to_half((DevLeaf*)c->leaves.p + wave_leaf_base, wave_leaves, st) != 0) return HHT_E_CUDA;
         c->prof.launches += 1;
     }
     std::vector<uint64_t> img_leaves(count, 0), img_off(count, 0);
@@ -439,13 +447,14 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs) {
         std::vector<int> order(count);
         for (int g = 0; g < count; ++g) order[g] = g;
         std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return im[x].depth < im[y].depth; });
-        uint64_t acc = 0;
+        uint64_t acc = wave_leaf_base;
         for (int g : order) {
             img_off[g] = acc;
             acc += img_leaves[g];
         }
         if (acc != leaf_total) return HHT_E_CUDA;
     }
+    c->job_leaves = leaf_total;
     for (int g = 0; g < count; ++g) {
         const uint64_t off = img_off[g];
         hht_result& r = outs[g];
@@ -465,6 +474,8 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs) {
             nl += su[4 * D + 1];
         }
         r.n_leaves = nl;
+        c->job_off[job_first + g] = off;
+        c->job_n[job_first + g] = c->h_img_err[g] ? 0 : nl;
         if (c->h_img_err[g]) {
             r.status = HHT_E_RANGE;
         } else if (nl > r.leaf_capacity || (nl > 0 && !r.leaves)) {
@@ -492,7 +503,7 @@ uint64_t estimate_bytes(const hht_image& im) {
     return (uint64_t)(2.0 * 8.0 * dense * 1.2 + 64.0 * n + 4096);
 }
 
-int run_job(hht_ctx* c, const hht_image* im, int count, hht_result* outs) {
+int run_waves(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int job_first) {
     // wave split by the memory budget (or 80% of the free device memory)
     uint64_t budget = c->budget;
     if (!budget) {
@@ -515,14 +526,16 @@ int run_job(hht_ctx* c, const hht_image* im, int count, hht_result* outs) {
         if (c->debug)
             fprintf(stderr, "[hht] wave of images [%d, %d): estimate %.2f GB, budget %.2f GB\n", first, last, acc / 1e9,
                     budget / 1e9);
-        int rc = run_wave(c, im + first, last - first, outs + first);
+        const uint64_t leaves_before = c->job_leaves;
+        int rc = run_wave(c, im + first, last - first, outs + first, job_first + first);
         if (rc == HHT_E_NOMEM && last - first > 1) {
             // remember that this much did not fit, split the wave and retry each half
             c->wave_cap = acc / 2 > 0 ? acc / 2 : 1;
             if (c->debug) fprintf(stderr, "[hht] wave did not fit; wave estimate cap now %.2f GB\n", c->wave_cap / 1e9);
+            c->job_leaves = leaves_before;
             const int mid = first + (last - first) / 2;
-            rc = run_job(c, im + first, mid - first, outs + first);
-            if (rc == HHT_OK) rc = run_job(c, im + mid, last - mid, outs + mid);
+            rc = run_waves(c, im + first, mid - first, outs + first, job_first + first);
+            if (rc == HHT_OK) rc = run_waves(c, im + mid, last - mid, outs + mid, job_first + mid);
         }
         if (rc != HHT_OK) {
             for (int g = first; g < last; ++g) outs[g].status = rc;
@@ -533,6 +546,13 @@ int run_job(hht_ctx* c, const hht_image* im, int count, hht_result* outs) {
         first = last;
     }
     return rc_all;
+}
+
+int run_job(hht_ctx* c, const hht_image* im, int count, hht_result* outs) {
+    c->job_off.assign(count, 0);
+    c->job_n.assign(count, 0);
+    c->job_leaves = 0;
+    return run_waves(c, im, count, outs, 0);
 }
 
 }  // namespace
@@ -615,6 +635,21 @@ int hht_detect_batch(hht_ctx* c, const hht_image* images, int32_t count, hht_res
     std::lock_guard<std::mutex> lk(c->mu);
     cudaSetDevice(c->device);
     return run_job(c, images, count, outs);
+}
+
+int hht_fetch_leaves(hht_ctx* c, int32_t index, hht_leaf* leaves, uint64_t capacity) {
+    if (!c) return HHT_E_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (index < 0 || (size_t)index >= c->job_n.size()) return HHT_E_ARG;
+    const uint64_t n = c->job_n[index];
+    if (n == 0) return HHT_OK;
+    if (!leaves) return HHT_E_ARG;
+    if (capacity < n) return HHT_E_CAPACITY;
+    cudaSetDevice(c->device);
+    CK(cudaMemcpyAsync(leaves, (const char*)c->leaves.p + c->job_off[index] * sizeof(DevLeaf), n * sizeof(hht_leaf),
+                       cudaMemcpyDefault, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return HHT_OK;
 }
 
 int hht_profile_enable(hht_ctx* c, int on) {

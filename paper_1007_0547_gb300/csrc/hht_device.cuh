@@ -36,6 +36,15 @@ __device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
 // G < 0 in that column is t = ceil(-G_column_base / dJ) clamped to [0, N],
 // an exact shift.  The result is an N*N-bit mask M with bit (alpha*N + beta)
 // set when vertex (column alpha, row beta) lies strictly below the line.
+// Column alpha contributes bits [N*alpha, N*alpha + t): summed as
+// 2^(N*alpha + t) - 2^(N*alpha) over the columns.
+template <int N>
+__device__ __forceinline__ constexpr uint32_t column_bases() {
+    uint32_t b = 0;
+    for (int alpha = 0; alpha < N; ++alpha) b += 1u << (N * alpha);
+    return b;
+}
+
 template <typename I, int N>
 __device__ __forceinline__ uint32_t below_mask(I G0, I dI, int k) {
     const I dJm1 = (I(1) << k) - I(1);
@@ -44,11 +53,17 @@ __device__ __forceinline__ uint32_t below_mask(I G0, I dI, int k) {
 #pragma unroll
     for (int alpha = 0; alpha < N; ++alpha) {
         I t = (dJm1 - G) >> k;  // floor((-G + dJ - 1) / dJ) = ceil(-G / dJ)
-        t = t < I(0) ? I(0) : (t > I(N) ? I(N) : t);
-        M |= ((1u << static_cast<int>(t)) - 1u) << (N * alpha);
+        int ti;
+        if constexpr (sizeof(I) == 4) {
+            ti = __vimin_s32_relu((int)t, N);  // clamp to [0, N]
+        } else {
+            t = t < I(0) ? I(0) : (t > I(N) ? I(N) : t);
+            ti = (int)t;
+        }
+        M += 1u << (N * alpha + ti);
         G += dI;
     }
-    return M;
+    return M - column_bases<N>();
 }
 
 // Bit-sliced 4-bit codes: for cells of side `sz` sub-grid steps, the word

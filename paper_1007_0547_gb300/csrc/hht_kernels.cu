@@ -391,18 +391,41 @@ struct ParentGeo {
 }  // namespace
 
 // One step of the level loop over the voter stream of the parents.  Every
-// warp owns a contiguous slice of the stream and walks it 32 voters at a
-// time (one coalesced 8-byte record per lane):
+// warp owns a contiguous slice of the stream and walks it in chunks of four
+// steps of 32 voters (one coalesced 8-byte record per lane and step):
 //   - the exact 5 x 5 corner-sign grid of the voter's parent gives the 4-bit
 //     codes of the four children and of the sixteen grandchildren;
 //   - a voter of a passed child whose list is kept is appended to that
 //     child's segment of the next stream (segments were sized by the
-//     selection; one atomic per child and warp step reserves the slots);
+//     selection; one atomic per child and chunk reserves the slots);
 //   - grandchild votes of passed children are accumulated in per-lane byte
 //     counters while the parent stays the same, then summed across the warp
 //     (redux.sync) and added to the next level's counters.
-// Within a child's segment the voter order depends on scheduling; no result
-// depends on it (counts, leaves and statistics are order-free).
+// A chunk whose voters do not all share one parent goes step by step with
+// per-parent lane groups.  Within a child's segment the voter order depends
+// on scheduling; no result depends on it (counts, leaves and statistics are
+// order-free).
+namespace {
+constexpr int kChunkSteps = 4;
+
+template <typename I>
+struct Classified {
+    uint32_t kw, gv;  // copy mask (children), grandchild votes of passed children
+};
+
+template <typename I>
+__device__ __forceinline__ Classified<I> classify(const ParentGeo<I>& g, uint32_t xy) {
+    Classified<I> c{0u, 0u};
+    const int32_t x = (int16_t)(xy & 0xffffu), y = (int16_t)(xy >> 16);
+    const I G0 = g.Gr + ((I(x) * I(g.ra)) << g.sh_xa) - (I(x + y) << g.D);
+    const uint32_t M = below_mask<I, 5>(G0, I(x) << g.sh_dI, g.k_dJ);
+    const uint32_t cv = child_votes5(M);
+    c.kw = cv & (g.pr.packed >> 4) & 0xfu;
+    c.gv = crossing_cells<5, 1>(M) & grandchild_mask(cv & g.pr.packed & 0xfu);
+    return c;
+}
+}  // namespace
+
 template <typename I>
 __global__ void __launch_bounds__(kPassTPB) pass_kernel(LevelArgs a) {
     const int lane = threadIdx.x & 31;
@@ -421,86 +444,163 @@ __global__ void __launch_bounds__(kPassTPB) pass_kernel(LevelArgs a) {
     // the run being counted: warp-uniform parent and per-lane byte counters
     uint32_t cur = kNoRegion;
     ParentGeo<I> cg;
+    uint32_t ci[4] = {0u, 0u, 0u, 0u};  // child record index per quadrant of cur
     uint32_t rows[4] = {0u, 0u, 0u, 0u};
     uint32_t steps = 0;
 
-    uint2 nxt = (beg + lane < end) ? vin[beg + lane] : make_uint2(0u, kNoRegion);
-    for (uint64_t s0 = beg; s0 < end; s0 += 32) {
-        const uint2 rec = nxt;
-        nxt = (s0 + 32 + lane < end) ? vin[s0 + 32 + lane] : make_uint2(0u, kNoRegion);
-        const uint32_t r = rec.y;
-        const bool valid = r != kNoRegion;
-        const int last = (int)((end - s0 < 32 ? end - s0 : 32) - 1);
-        const uint32_t r0 = __shfl_sync(0xffffffffu, r, 0);
-        const uint32_t rl = __shfl_sync(0xffffffffu, r, last);
-        const bool uni = (r0 == rl);  // the stream is grouped by parent
-
-        // ---- parent geometry of this lane's voter
-        if (rl != cur && uni) {
-            // a new run starts with this step: settle the old one first
-            if (cur != kNoRegion) {
-                uint32_t c16[8];
-                reduce_rows(rows, 0xffffffffu, c16);
-                if (lane == 0) add_counts(a.child_cnt, cg.pr, c16);
-            }
-            rows[0] = rows[1] = rows[2] = rows[3] = 0u;
-            steps = 0;
-            cur = rl;
-            cg.load(a.pregions, cur);
+    auto settle = [&]() {
+        if (cur != kNoRegion) {
+            uint32_t c16[8];
+            reduce_rows(rows, 0xffffffffu, c16);
+            if (lane == 0) add_counts(a.child_cnt, cg.pr, c16);
         }
-        ParentGeo<I> g = cg;
-        if (!uni && valid && r != cur) g.load(a.pregions, r);
-
-        // ---- codes
-        uint32_t kw = 0u, gv = 0u;
-        const int32_t x = (int16_t)(rec.x & 0xffffu), y = (int16_t)(rec.x >> 16);
-        if (valid) {
-            const I G0 = g.Gr + ((I(x) * I(g.ra)) << g.sh_xa) - (I(x + y) << g.D);
-            const uint32_t M = below_mask<I, 5>(G0, I(x) << g.sh_dI, g.k_dJ);
-            const uint32_t cv = child_votes5(M);
-            kw = cv & (g.pr.packed >> 4) & 0xfu;
-            gv = crossing_cells<5, 1>(M) & grandchild_mask(cv & g.pr.packed & 0xfu);
-        }
-
-        // ---- copies into the children's segments
-        const uint32_t peers = uni ? 0xffffffffu : __match_any_sync(0xffffffffu, r);
+        rows[0] = rows[1] = rows[2] = rows[3] = 0u;
+        steps = 0;
+    };
+    auto start_run = [&](uint32_t r) {
+        cur = r;
+        cg.load(a.pregions, r);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const bool keep = (kw >> q) & 1u;
-            const uint32_t b = __ballot_sync(0xffffffffu, keep);
-            if (!b) continue;
-            const uint32_t gm = b & peers;
-            const int leader = keep ? __ffs(gm) - 1 : lane;
-            unsigned long long base = 0;
-            if (keep && lane == leader) base = atomicAdd(&a.cursor[child_index(g.pr, q)], (unsigned long long)__popc(gm));
-            base = __shfl_sync(0xffffffffu, base, leader);
-            if (keep) {
-                const uint64_t p = base + __popc(gm & lt);
-                if (p < a.cap_voters) vout[p] = make_uint2(rec.x, child_index(g.pr, q));
+        for (int q = 0; q < 4; ++q) ci[q] = child_index(cg.pr, q);
+    };
+
+    uint2 nxt[kChunkSteps];
+#pragma unroll
+    for (int k = 0; k < kChunkSteps; ++k) {
+        const uint64_t i = beg + 32 * k + lane;
+        nxt[k] = i < end ? vin[i] : make_uint2(0u, kNoRegion);
+    }
+    for (uint64_t c0 = beg; c0 < end; c0 += 32 * kChunkSteps) {
+        uint2 rec[kChunkSteps];
+#pragma unroll
+        for (int k = 0; k < kChunkSteps; ++k) {
+            rec[k] = nxt[k];
+            const uint64_t i = c0 + 32 * (kChunkSteps + k) + lane;
+            nxt[k] = i < end ? vin[i] : make_uint2(0u, kNoRegion);
+        }
+        const uint64_t left = end - c0;
+        const int nvalid = (int)(left < 32 * kChunkSteps ? left : 32 * kChunkSteps);
+        const uint32_t r_first = __shfl_sync(0xffffffffu, rec[0].y, 0);
+        const int lk = (nvalid - 1) >> 5, ll = (nvalid - 1) & 31;
+        uint32_t r_last = rec[0].y;
+#pragma unroll
+        for (int k = 1; k < kChunkSteps; ++k)
+            if (k == lk) r_last = rec[k].y;
+        r_last = __shfl_sync(0xffffffffu, r_last, ll);
+
+        if (r_first == r_last) {
+            // ---- the whole chunk belongs to one parent (the stream is grouped by parent)
+            if (r_first != cur) {
+                settle();
+                start_run(r_first);
             }
+            uint32_t kw[kChunkSteps];
+#pragma unroll
+            for (int k = 0; k < kChunkSteps; ++k) {
+                kw[k] = 0u;
+                if (rec[k].y != kNoRegion) {
+                    const Classified<I> c = classify(cg, rec[k].x);
+                    kw[k] = c.kw;
+                    add_rows(rows, c.gv);
+                }
+            }
+            steps += kChunkSteps;
+            if (steps >= 255 - kChunkSteps) settle();  // byte counters nearly full
+            // reserve each kept child's slots for the whole chunk (one atomic
+            // per child), then write in step and lane order
+            unsigned long long base[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t tot = 0;
+#pragma unroll
+                for (int k = 0; k < kChunkSteps; ++k) tot += __popc(__ballot_sync(0xffffffffu, (kw[k] >> q) & 1u));
+                base[q] = 0;
+                if (tot && lane == 0) base[q] = atomicAdd(&a.cursor[ci[q]], (unsigned long long)tot);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                unsigned long long p = __shfl_sync(0xffffffffu, base[q], 0);
+#pragma unroll
+                for (int k = 0; k < kChunkSteps; ++k) {
+                    const bool keep = (kw[k] >> q) & 1u;
+                    const uint32_t bq = __ballot_sync(0xffffffffu, keep);
+                    if (keep) {
+                        const uint64_t at = p + __popc(bq & lt);
+                        if (at < a.cap_voters) vout[at] = make_uint2(rec[k].x, ci[q]);
+                    }
+                    p += __popc(bq);
+                }
+            }
+            continue;
         }
 
-        // ---- grandchild counts
-        if (uni) {
-            add_rows(rows, gv);
-            if (++steps == 255) {  // byte counters are full: settle the run so far
-                uint32_t c16[8];
-                reduce_rows(rows, 0xffffffffu, c16);
-                if (lane == 0) add_counts(a.child_cnt, cg.pr, c16);
-                rows[0] = rows[1] = rows[2] = rows[3] = 0u;
-                steps = 0;
+        // ---- a parent boundary inside the chunk: step by step, lanes grouped by
+        // parent (kept rolled: this cold path must not crowd the instruction cache)
+#pragma unroll 1
+        for (int k = 0; k < kChunkSteps; ++k) {
+            uint2 rk = rec[0];
+#pragma unroll
+            for (int kk = 1; kk < kChunkSteps; ++kk)
+                if (kk == k) rk = rec[kk];
+            const uint32_t r = rk.y;
+            const bool valid = r != kNoRegion;
+            const uint32_t active = __ballot_sync(0xffffffffu, valid);
+            if (!active) break;
+            const int last = 31 - __clz(active);
+            const uint32_t r0 = __shfl_sync(0xffffffffu, r, 0);
+            const uint32_t rl = __shfl_sync(0xffffffffu, r, last);
+            if (r0 == rl && rl == cur) {
+                // still the current run
+                uint32_t kw = 0u;
+                if (valid) {
+                    const Classified<I> c = classify(cg, rk.x);
+                    kw = c.kw;
+                    add_rows(rows, c.gv);
+                }
+                ++steps;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const bool keep = (kw >> q) & 1u;
+                    const uint32_t bq = __ballot_sync(0xffffffffu, keep);
+                    if (!bq) continue;
+                    unsigned long long p = 0;
+                    if (lane == 0) p = atomicAdd(&a.cursor[ci[q]], (unsigned long long)__popc(bq));
+                    p = __shfl_sync(0xffffffffu, p, 0);
+                    if (keep) {
+                        const uint64_t at = p + __popc(bq & lt);
+                        if (at < a.cap_voters) vout[at] = make_uint2(rk.x, ci[q]);
+                    }
+                }
+                continue;
             }
-        } else {
-            // a run boundary inside the step: settle the current run, count
-            // every other parent's lanes of this step on their own, and start
-            // the run of the last lane's parent
-            if (cur != kNoRegion) {
-                uint32_t c16[8];
-                reduce_rows(rows, 0xffffffffu, c16);
-                if (lane == 0) add_counts(a.child_cnt, cg.pr, c16);
-                rows[0] = rows[1] = rows[2] = rows[3] = 0u;
-                steps = 0;
+            // settle the current run; every lane classifies with its own parent
+            settle();
+            ParentGeo<I> g = cg;
+            if (valid && r != cur) g.load(a.pregions, r);
+            uint32_t kw = 0u, gv = 0u;
+            if (valid) {
+                const Classified<I> c = classify(g, rk.x);
+                kw = c.kw;
+                gv = c.gv;
             }
+            const uint32_t peers = __match_any_sync(0xffffffffu, r);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const bool keep = (kw >> q) & 1u;
+                const uint32_t bq = __ballot_sync(0xffffffffu, keep);
+                if (!bq) continue;
+                const uint32_t gm = bq & peers;
+                const int leader = keep ? __ffs(gm) - 1 : lane;
+                unsigned long long p = 0;
+                if (keep && lane == leader) p = atomicAdd(&a.cursor[child_index(g.pr, q)], (unsigned long long)__popc(gm));
+                p = __shfl_sync(0xffffffffu, p, leader);
+                if (keep) {
+                    const uint64_t at = p + __popc(gm & lt);
+                    if (at < a.cap_voters) vout[at] = make_uint2(rk.x, child_index(g.pr, q));
+                }
+            }
+            // count every parent but the last lane's on its own; the last one
+            // continues as the current run
             uint32_t own[4] = {0u, 0u, 0u, 0u};
             add_rows(own, gv);
             const bool mine = valid && r == rl;
@@ -516,19 +616,14 @@ __global__ void __launch_bounds__(kPassTPB) pass_kernel(LevelArgs a) {
                 }
                 rest &= ~gmask;
             }
-            cur = rl;
-            cg.load(a.pregions, cur);
+            start_run(rl);
             if (mine) {
                 rows[0] = own[0]; rows[1] = own[1]; rows[2] = own[2]; rows[3] = own[3];
             }
             steps = 1;
         }
     }
-    if (cur != kNoRegion) {
-        uint32_t c16[8];
-        reduce_rows(rows, 0xffffffffu, c16);
-        if (lane == 0) add_counts(a.child_cnt, cg.pr, c16);
-    }
+    settle();
 }
 
 // ============================================================================ output fix-up

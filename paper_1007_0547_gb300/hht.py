@@ -29,8 +29,8 @@ HHT_E_PENDING = -7
 HHT_E_UNKNOWN_TICKET = -8
 
 # every function the C header declares
-EXPORTS = ("hht_create", "hht_destroy", "hht_detect", "hht_detect_batch", "hht_submit", "hht_poll",
-           "hht_progress", "hht_profile_enable", "hht_profile_read", "hht_strerror", "hht_version")
+EXPORTS = ("hht_create", "hht_destroy", "hht_detect", "hht_detect_batch", "hht_fetch_leaves", "hht_submit",
+           "hht_poll", "hht_progress", "hht_profile_enable", "hht_profile_read", "hht_strerror", "hht_version")
 
 
 class HhtError(RuntimeError):
@@ -78,6 +78,8 @@ def load(path: str = LIB_PATH):
     lib.hht_detect.restype = ctypes.c_int
     lib.hht_detect_batch.argtypes = [vp, ctypes.POINTER(_Image), i32, ctypes.POINTER(_Result)]
     lib.hht_detect_batch.restype = ctypes.c_int
+    lib.hht_fetch_leaves.argtypes = [vp, i32, vp, u64]
+    lib.hht_fetch_leaves.restype = ctypes.c_int
     lib.hht_submit.argtypes = [vp, ctypes.POINTER(_Image), ctypes.POINTER(u64)]
     lib.hht_submit.restype = ctypes.c_int
     lib.hht_poll.argtypes = [vp, u64, ctypes.POINTER(_Result)]
@@ -191,22 +193,29 @@ class Context:
         buf = np.empty((max(cap, 1), 4), dtype=np.int32)
         return buf, buf.ctypes.data
 
+    def _fetch(self, index: int, n: int, on_device: bool):
+        """Leaves of image `index` of the last job (no recomputation)."""
+        buf, ptr = self._alloc_leaves(n, on_device)
+        rc = load().hht_fetch_leaves(self._h, int(index), ptr, n)
+        if rc != HHT_OK:
+            raise HhtError(rc, "hht_fetch_leaves")
+        return buf
+
     def detect(self, points, W: int, H: int, depth: int, T: int, leaves_on_device: bool = True,
                leaf_capacity: Optional[int] = None, raise_on_error: bool = True) -> Result:
         lib = load()
         p = _Points(points)
         cap = int(leaf_capacity or self._cap_hint)
-        while True:
-            buf, ptr = self._alloc_leaves(cap, leaves_on_device)
-            r = _Result()
-            r.leaves = ptr
-            r.leaf_capacity = cap
-            rc = lib.hht_detect(self._h, p.ptr, p.n, int(W), int(H), int(depth), int(T), ctypes.byref(r))
-            if rc == HHT_E_CAPACITY:
-                cap = int(r.n_leaves)
-                self._cap_hint = max(self._cap_hint, cap)
-                continue
-            break
+        buf, ptr = self._alloc_leaves(cap, leaves_on_device)
+        r = _Result()
+        r.leaves = ptr
+        r.leaf_capacity = cap
+        rc = lib.hht_detect(self._h, p.ptr, p.n, int(W), int(H), int(depth), int(T), ctypes.byref(r))
+        if rc == HHT_E_CAPACITY:
+            # the leaves are kept by the context: copy them into a buffer of the right size
+            self._cap_hint = max(self._cap_hint, int(r.n_leaves))
+            buf = self._fetch(0, int(r.n_leaves), leaves_on_device)
+            rc = HHT_OK
         if rc != HHT_OK and raise_on_error:
             raise HhtError(rc, "hht_detect")
         k = int(r.n_leaves) if rc == HHT_OK else 0
@@ -222,21 +231,20 @@ class Context:
             arr[k].points = p.ptr
             arr[k].n = p.n
             arr[k].W, arr[k].H, arr[k].depth, arr[k].T = (int(v) for v in im[1:5])
-        caps = [self._cap_hint] * len(images)
-        while True:
-            outs = (_Result * len(images))()
-            bufs = []
-            for k in range(len(images)):
-                b, ptr = self._alloc_leaves(caps[k], leaves_on_device)
-                bufs.append(b)
-                outs[k].leaves = ptr
-                outs[k].leaf_capacity = caps[k]
-            rc = lib.hht_detect_batch(self._h, arr, len(images), outs)
-            short = [k for k in range(len(images)) if outs[k].status == HHT_E_CAPACITY]
-            if not short:
-                break
-            for k in short:
-                caps[k] = int(outs[k].n_leaves)
+        # no leaves are copied by the batch call itself: every image's leaves
+        # are fetched afterwards into a buffer of exactly the right size
+        outs = (_Result * len(images))()
+        rc = lib.hht_detect_batch(self._h, arr, len(images), outs)
+        bufs = []
+        for k in range(len(images)):
+            if outs[k].status == HHT_E_CAPACITY:
+                outs[k].status = HHT_OK
+                if rc == HHT_E_CAPACITY:
+                    rc = HHT_OK
+            bufs.append(self._fetch(k, int(outs[k].n_leaves), leaves_on_device) if outs[k].status == HHT_OK
+                        else self._alloc_leaves(0, leaves_on_device)[0])
+        if rc == HHT_E_CAPACITY:
+            rc = HHT_OK
         res = []
         for k in range(len(images)):
             st = int(outs[k].status)

@@ -25,8 +25,8 @@ def lib():
 
 
 def test_header_declares_the_api():
-    assert set(_declared()) == {"hht_create", "hht_destroy", "hht_detect", "hht_detect_batch", "hht_submit",
-                                "hht_poll", "hht_progress", "hht_profile_enable", "hht_profile_read",
+    assert set(_declared()) == {"hht_create", "hht_destroy", "hht_detect", "hht_detect_batch", "hht_fetch_leaves",
+                                "hht_submit", "hht_poll", "hht_progress", "hht_profile_enable", "hht_profile_read",
                                 "hht_strerror", "hht_version"}
 
 
@@ -51,6 +51,7 @@ def test_host_only_calls(lib):
     assert lib.hht_poll(None, 1, ctypes.byref(r)) == hht.HHT_E_ARG
     assert lib.hht_profile_enable(None, 1) == hht.HHT_E_ARG
     assert lib.hht_profile_read(None, None) == hht.HHT_E_ARG
+    assert lib.hht_fetch_leaves(None, 0, None, 0) == hht.HHT_E_ARG
 
 
 def test_result_struct_layout_matches_header(lib):

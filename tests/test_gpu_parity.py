@@ -170,6 +170,12 @@ def test_capacity_two_call_protocol(ctx, hht):
     r.leaf_capacity = 3
     rc = lib.hht_detect(ctx._h, pts.ctypes.data, img.n, img.W, img.H, img.depth, img.T, ctypes.byref(r))
     assert rc == hht.HHT_E_CAPACITY and r.n_leaves == len(want.leaves)
+    # the second call of the protocol copies the kept leaves without a new run
+    full = np.zeros((int(r.n_leaves), 4), np.int32)
+    assert lib.hht_fetch_leaves(ctx._h, 0, full.ctypes.data, 3) == hht.HHT_E_CAPACITY
+    assert lib.hht_fetch_leaves(ctx._h, 1, full.ctypes.data, len(full)) == hht.HHT_E_ARG
+    assert lib.hht_fetch_leaves(ctx._h, 0, full.ctypes.data, len(full)) == hht.HHT_OK
+    assert np.array_equal(full.astype(np.uint32), want.leaves)
     _same(ctx.detect(img.points, img.W, img.H, img.depth, img.T, leaf_capacity=1), want)
 
 
@@ -225,3 +231,18 @@ def test_plain_4096_full_size_sampled(ctx):
     want = oracle.detect(img.points, img.W, img.H, shallow, img.T)
     assert np.array_equal(r.stats[:, :shallow], want.stats[:, :shallow])
     assert np.array_equal(r.stats[:, shallow, [0, 2, 3]], want.stats[:, shallow, [0, 2, 3]])
+
+
+def test_small_budget_splits_the_batch_into_waves(hht):
+    """A context whose memory budget holds only part of the batch runs it in
+    several waves; every image's result is unchanged."""
+    imgs = [synth.batch_image(k) for k in (0, 1, 2, 4, 5, 6)]
+    big = hht.Context(device=0)
+    ref = [big.detect(im.points, im.W, im.H, im.depth, im.T) for im in imgs]
+    big.close()
+    small = hht.Context(device=0, mem_budget=1_500_000_000)
+    got = small.detect_batch([(im.points, im.W, im.H, im.depth, im.T) for im in imgs])
+    small.close()
+    for a, b in zip(ref, got):
+        assert np.array_equal(a.leaves_numpy(), b.leaves_numpy())
+        assert np.array_equal(a.stats, b.stats)
