@@ -188,6 +188,37 @@ typedef struct {
 int hht_profile_enable(hht_ctx *ctx, int on);
 int hht_profile_read(hht_ctx *ctx, hht_profile_counters *out);
 
+/*
+ * Single-image detection that allocates no memory (no paper counterpart:
+ * this is a library-integration variant of hht_detect).  For callers that
+ * cannot let a library call cudaMalloc: code being captured into a CUDA
+ * graph (allocations and frees cannot be captured, and cudaFree synchronises
+ * the device), processes whose device memory belongs to another allocator,
+ * and latency-critical paths.  All scratch lives in one static device array
+ * of HHT_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * the process exits; no context is needed.
+ *   points: n points in host or device memory; leaves: caller buffer (host or
+ *   device) of leaf_capacity entries; out: statistics and n_leaves (host);
+ *   cuda_stream: the stream to run on (NULL = legacy default stream).
+ * The call synchronises `cuda_stream` before it returns.  The first call on a
+ * device looks up the array's device address (make it before any stream
+ * capture).  The array keeps the previous call's contents; each call clears
+ * what it needs.  Calls that overlap on the GPU (other streams or threads on
+ * the same device) race on the array and must not be made.
+ * Limits: n <= HHT_NOALLOC_MAX_POINTS, depth <= HHT_NOALLOC_MAX_DEPTH, at most
+ * HHT_NOALLOC_MAX_LEAVES leaves, and the per-level voter lists must fit the
+ * array; beyond them the call returns HHT_E_NOMEM (the limits on n and depth
+ * are checked before any device work).
+ * Errors: as hht_detect (HHT_E_CAPACITY leaves nothing to fetch: call again
+ * with a larger buffer).
+ */
+#define HHT_NOALLOC_SCRATCH_BYTES (64u << 20)
+#define HHT_NOALLOC_MAX_POINTS (1 << 20)
+#define HHT_NOALLOC_MAX_DEPTH 16
+#define HHT_NOALLOC_MAX_LEAVES (1 << 18)
+int hht_detect_noalloc(const hht_point *points, int64_t n, int32_t W, int32_t H, int32_t depth, int32_t T,
+                       hht_leaf *leaves, uint64_t leaf_capacity, hht_result *out, void *cuda_stream);
+
 /* Short description of an HHT_* code (static string). */
 const char *hht_strerror(int code);
 

@@ -30,7 +30,8 @@ HHT_E_UNKNOWN_TICKET = -8
 
 # every function the C header declares
 EXPORTS = ("hht_create", "hht_destroy", "hht_detect", "hht_detect_batch", "hht_fetch_leaves", "hht_submit",
-           "hht_poll", "hht_progress", "hht_profile_enable", "hht_profile_read", "hht_strerror", "hht_version")
+           "hht_poll", "hht_progress", "hht_profile_enable", "hht_profile_read", "hht_strerror", "hht_version",
+           "hht_detect_noalloc")
 
 
 class HhtError(RuntimeError):

@@ -27,7 +27,7 @@ def lib():
 def test_header_declares_the_api():
     assert set(_declared()) == {"hht_create", "hht_destroy", "hht_detect", "hht_detect_batch", "hht_fetch_leaves",
                                 "hht_submit", "hht_poll", "hht_progress", "hht_profile_enable", "hht_profile_read",
-                                "hht_strerror", "hht_version"}
+                                "hht_strerror", "hht_version", "hht_detect_noalloc"}
 
 
 def test_library_exports_every_declared_symbol(lib):
