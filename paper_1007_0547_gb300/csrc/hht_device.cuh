@@ -102,6 +102,42 @@ __device__ __forceinline__ uint32_t region_code3(uint32_t M) {
     return (((M >> 8) & 1u) << 3) | (((M >> 2) & 1u) << 2) | (((M >> 0) & 1u) << 1) | ((M >> 6) & 1u);
 }
 
+// ---------------------------------------------------------------- pass-kernel bit layouts
+// The corner-sign mask M of the 5 x 5 quarter-step grid holds vertex
+// (alpha, beta) at bit 5*alpha + beta.  The bit-sliced codes are formed with
+// left shifts (multiplies, which run on the FMA pipe) so that the result for
+// the cell whose SW vertex is p lands on the cell's NE vertex bit p + 6*sz:
+// the NE corner bit is M itself, NW is M << 5*sz, SW is M << 6*sz and SE is
+// M << sz.  A line votes for the cell when its code is neither 0000 nor 1111.
+template <int sz>
+__device__ __forceinline__ uint32_t code_votes(uint32_t M) {
+    const uint32_t ne = M, nw = M * (1u << (5 * sz)), sw = M * (1u << (6 * sz)), se = M * (1u << sz);
+    return (ne | nw | sw | se) & ~(ne & nw & sw & se);
+}
+
+// Children (2 x 2 steps) of quadrant q = NE, NW, SW, SE have SW vertices
+// 12, 2, 0, 10 and so vote at bits 24, 14, 12, 22 of code_votes<2>.
+__host__ __device__ __forceinline__ constexpr int quad_bit(int q) { return q == 0 ? 24 : q == 1 ? 14 : q == 2 ? 12 : 22; }
+// Grandchild (alpha, beta), alpha, beta < 4, votes at bit kGrandBase + 5*alpha + beta of code_votes<1>.
+constexpr int kGrandBase = 6;
+
+// The four quadrant bits of `q4` (bit q = quadrant q) at quad_bit positions.
+__device__ __forceinline__ uint32_t spread_quads(uint32_t q4) {
+    return ((q4 & 1u) << 24) | ((q4 & 2u) << 13) | ((q4 & 4u) << 10) | ((q4 & 8u) << 19);
+}
+
+// Grandchild cells of the children whose vote bits (quad_bit positions) are
+// set in `kids`: child q's 2 x 2 grandchildren sit at its bit - 6 + {0, 1, 5, 6}
+// (one multiply; the four children's cells are disjoint, so nothing carries).
+__device__ __forceinline__ uint32_t grand_cells(uint32_t kids) { return (kids >> 6) * 0x63u; }
+
+// Low t bits set (0 <= t <= 31).
+__device__ __forceinline__ uint32_t prefix_bits(int t) {
+    uint32_t r;
+    asm("bmsk.clamp.b32 %0, 0, %1;" : "=r"(r) : "r"(t));
+    return r;
+}
+
 // Grandchild cells (1 x 1 steps of the 5 x 5 grid, bits alpha*5 + beta with
 // alpha, beta < 4) that lie inside the children whose bit is set in `kids`.
 __device__ __forceinline__ uint32_t grandchild_mask(uint32_t kids) {

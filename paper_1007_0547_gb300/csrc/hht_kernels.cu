@@ -365,27 +365,30 @@ __device__ __forceinline__ void reduce_rows(const uint32_t (&rows)[4], uint32_t 
 // cells, byte beta.
 __device__ __forceinline__ void add_rows(uint32_t (&rows)[4], uint32_t gv) {
 #pragma unroll
-    for (int al = 0; al < 4; ++al) rows[al] += spread4((gv >> (5 * al)) & 0xfu);
+    for (int al = 0; al < 4; ++al) rows[al] += spread4((gv >> (kGrandBase + 5 * al)) & 0xfu);
 }
 
-// Shift counts and grid constants of one parent region for the corner grid
-// of its voters.
+// Constants of one parent region for the corner grid of its voters.  With
+// u0 = dJ - 1 - G(SW vertex) = W0 - x*A + (x + y)*Kc and column step
+// d = x*dmul, the number of below-the-line vertices in column alpha of the
+// 5 x 5 quarter-step grid is t = clamp((u0 - alpha*d) >> k, 0, 5).
 template <typename I>
 struct ParentGeo {
     PassRegion pr;
-    I Gr;
-    int32_t ra;
-    int sh_xa, sh_dI, k_dJ, D;
+    I W0, A, Kc, dmul;
+    int k;
+    uint32_t pspread, wspread;  // pass / write masks at the children's vote bits
     __device__ __forceinline__ void load(const PassRegion* p, uint32_t r) {
         pr = p[r];
-        const int sS = (pr.packed >> 8) & 31, lL = (pr.packed >> 13) & 31;
-        D = (pr.packed >> 18) & 31;
-        // G at the parent's SW vertex (aS, bS): 4L*bS + 2x*aS - 2LK - K(x+y)
-        Gr = (I(pr.b) << (sS + lL + 2)) - (I(1) << (lL + D + 1));
-        ra = (int32_t)pr.a;
-        sh_xa = sS + 1;
-        sh_dI = sS - 1;  // quarter step h = S/4: 2x*h = x << (sS - 1)
-        k_dJ = lL + sS;  // 4L*h = 2^(lL + sS)
+        const int sS = (pr.packed >> 8) & 31, lL = (pr.packed >> 13) & 31, D = (pr.packed >> 18) & 31;
+        k = lL + sS;                                                    // dJ = 4L * S/4 = 2^(lL + sS)
+        const I Gr = (I(pr.b) << (sS + lL + 2)) - (I(1) << (lL + D + 1));  // 4L*bS - 2LK
+        W0 = ((I(1) << k) - I(1)) - Gr;
+        A = I(pr.a) << (sS + 1);                                        // 2*aS: G gains 2x*aS
+        Kc = I(1) << D;                                                 // G loses K(x + y)
+        dmul = I(1) << (sS - 1);                                        // 2x * S/4
+        pspread = spread_quads(pr.packed & 0xfu);
+        wspread = spread_quads((pr.packed >> 4) & 0xfu);
     }
 };
 }  // namespace
@@ -410,24 +413,43 @@ constexpr int kChunkSteps = 4;
 
 template <typename I>
 struct Classified {
-    uint32_t kw, gv;  // copy mask (children), grandchild votes of passed children
+    uint32_t kw;  // children whose list keeps this voter, at the children's vote bits (quad_bit)
+    uint32_t gv;  // grandchild cells of passed children the voter crosses, at kGrandBase + 5*alpha + beta
 };
 
+// Classify one voter against its parent: the exact 5 x 5 corner-sign grid,
+// then the 4-bit codes of the four children and the sixteen grandchildren
+// (vote when the code is neither 0000 nor 1111).
 template <typename I>
 __device__ __forceinline__ Classified<I> classify(const ParentGeo<I>& g, uint32_t xy) {
-    Classified<I> c{0u, 0u};
-    const int32_t x = (int16_t)(xy & 0xffffu), y = (int16_t)(xy >> 16);
-    const I G0 = g.Gr + ((I(x) * I(g.ra)) << g.sh_xa) - (I(x + y) << g.D);
-    const uint32_t M = below_mask<I, 5>(G0, I(x) << g.sh_dI, g.k_dJ);
-    const uint32_t cv = child_votes5(M);
-    c.kw = cv & (g.pr.packed >> 4) & 0xfu;
-    c.gv = crossing_cells<5, 1>(M) & grandchild_mask(cv & g.pr.packed & 0xfu);
+    const I x = I(xy & 0xffffu), y = I(xy >> 16);
+    const I u0 = g.W0 - x * g.A + (x + y) * g.Kc;
+    const I d = x * g.dmul;
+    uint32_t M = 0;
+#pragma unroll
+    for (int alpha = 0; alpha < 5; ++alpha) {
+        const I w = u0 - I(alpha) * d;
+        int t;
+        if constexpr (sizeof(I) == 4) {
+            t = __vimin_s32_relu((int)(w >> g.k), 5);
+        } else {
+            I tt = w >> g.k;
+            tt = tt < I(0) ? I(0) : (tt > I(5) ? I(5) : tt);
+            t = (int)tt;
+        }
+        M += prefix_bits(t) * (1u << (5 * alpha));
+    }
+    const uint32_t v2 = code_votes<2>(M);  // children: vote bits at quad_bit(q)
+    const uint32_t v1 = code_votes<1>(M);  // grandchildren: vote bits at kGrandBase + 5*alpha + beta
+    Classified<I> c;
+    c.kw = v2 & g.wspread;
+    c.gv = v1 & grand_cells(v2 & g.pspread);
     return c;
 }
 }  // namespace
 
 template <typename I>
-__global__ void __launch_bounds__(kPassTPB) pass_kernel(LevelArgs a) {
+__global__ void __launch_bounds__(kPassTPB, 4) pass_kernel(LevelArgs a) {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
     const uint64_t nin = a.info_prev->n_voters;
@@ -513,7 +535,7 @@ __global__ void __launch_bounds__(kPassTPB) pass_kernel(LevelArgs a) {
             for (int q = 0; q < 4; ++q) {
                 uint32_t tot = 0;
 #pragma unroll
-                for (int k = 0; k < kChunkSteps; ++k) tot += __popc(__ballot_sync(0xffffffffu, (kw[k] >> q) & 1u));
+                for (int k = 0; k < kChunkSteps; ++k) tot += __popc(__ballot_sync(0xffffffffu, (kw[k] >> quad_bit(q)) & 1u));
                 base[q] = 0;
                 if (tot && lane == 0) base[q] = atomicAdd(&a.cursor[ci[q]], (unsigned long long)tot);
             }
@@ -522,7 +544,7 @@ __global__ void __launch_bounds__(kPassTPB) pass_kernel(LevelArgs a) {
                 unsigned long long p = __shfl_sync(0xffffffffu, base[q], 0);
 #pragma unroll
                 for (int k = 0; k < kChunkSteps; ++k) {
-                    const bool keep = (kw[k] >> q) & 1u;
+                    const bool keep = (kw[k] >> quad_bit(q)) & 1u;
                     const uint32_t bq = __ballot_sync(0xffffffffu, keep);
                     if (keep) {
                         const uint64_t at = p + __popc(bq & lt);
@@ -560,7 +582,7 @@ __global__ void __launch_bounds__(kPassTPB) pass_kernel(LevelArgs a) {
                 ++steps;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const bool keep = (kw >> q) & 1u;
+                    const bool keep = (kw >> quad_bit(q)) & 1u;
                     const uint32_t bq = __ballot_sync(0xffffffffu, keep);
                     if (!bq) continue;
                     unsigned long long p = 0;
@@ -586,7 +608,7 @@ __global__ void __launch_bounds__(kPassTPB) pass_kernel(LevelArgs a) {
             const uint32_t peers = __match_any_sync(0xffffffffu, r);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const bool keep = (kw >> q) & 1u;
+                const bool keep = (kw >> quad_bit(q)) & 1u;
                 const uint32_t bq = __ballot_sync(0xffffffffu, keep);
                 if (!bq) continue;
                 const uint32_t gm = bq & peers;
