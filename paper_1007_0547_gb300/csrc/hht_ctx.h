@@ -1,0 +1,77 @@
+// Context of libhht.so (hht_ctx) and the device-buffer helpers shared by the
+// batch path (hht_api.cu) and the serving engine (hht_serve.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+#include <vector>
+
+#include "../../include/hht.h"
+#include "hht_internal.h"
+
+namespace hht {
+struct ServeState;
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+inline int ceil_log2_i(int v) {
+    int e = 0;
+    while ((1 << e) < v) ++e;
+    return e;
+}
+}  // namespace hht
+
+struct hht_ctx {
+    using DevBuf = hht::DevBuf;
+    int device = 0;
+    bool debug = false;          // HHT_DEBUG=1: wave and allocation trace on stderr
+    uint64_t wave_cap = 0;       // largest wave estimate known to fit (0 = none failed yet)
+    cudaStream_t stream = nullptr;
+    uint64_t budget = 0;
+    uint64_t held = 0;
+    int num_sms = 0;
+    int occ_select = 1, occ_pass32 = 1, occ_pass64 = 1;
+
+    // job buffers
+    DevBuf pts, img_start, img_unit, units, stats, infos, status, leaf_total, img_err, scan_states;
+    DevBuf rec[2], preg[2], cnt[2], vox[2];
+    DevBuf leaves;
+    DevBuf sel_flags, sel_data, cursors;
+    // host staging
+    std::vector<uint64_t> h_stats;
+    std::vector<hht::LevelInfo> h_infos;
+    std::vector<uint32_t> h_img_err;
+
+    hht::ServeState* serve = nullptr;
+    std::mutex mu;
+
+    // leaves of the last job stay in `leaves` until the next job
+    // (hht_fetch_leaves): per image offset and count
+    std::vector<uint64_t> job_off, job_n;
+    uint64_t job_leaves = 0;
+
+    // kernel timing (hht_profile_enable)
+    bool profile = false;
+    hht_profile_counters prof{};
+    std::vector<cudaEvent_t> ev_pool;
+    struct Pending {
+        cudaEvent_t a, b;
+        int kind;  // 0 stage, 1 select, 2 pass, 3 output fix-up
+    };
+    std::vector<Pending> pending;
+};
+
+
+namespace hht {
+int cuda_fail(cudaError_t e);
+// Grow a device buffer to at least `bytes` (contents are not kept; zeroed when asked).
+int ensure(hht_ctx* c, DevBuf& b, size_t bytes, bool zero = false);
+// Grow a device buffer keeping its first `keep` bytes.
+int ensure_keep(hht_ctx* c, DevBuf& b, size_t bytes, size_t keep);
+void release(hht_ctx* c, DevBuf& b);
+}  // namespace hht

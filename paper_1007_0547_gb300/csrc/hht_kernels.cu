@@ -91,6 +91,19 @@ __global__ void __launch_bounds__(256) stage_kernel(const int16_t* __restrict__ 
         for (int h = 0; h < 2; ++h) {
             const uint32_t u = active ? img_unit[img] + (uint32_t)h : 0u;
             uint32_t key = (active && ok) ? u : kNoRegion;
+            if (active && !ok) {
+                // a point outside its image fails the image; its level-0 slot
+                // still gets a record, marked as belonging to no region, so
+                // that the stream holds no uninitialised entries
+                const Unit& U = units[u];
+                if (U.D >= 2) {
+                    Voter dead;
+                    dead.x = 0;
+                    dead.y = 0;
+                    dead.region = kNoRegion;
+                    v0[U.v0_off + (k - img_start[img])] = dead;
+                }
+            }
             uint32_t vals[2] = {0u, 0u};  // [0]: child votes as 4 bytes, [1]: level-0 votes
             if (active && ok) {
                 const Unit& U = units[u];
@@ -567,7 +580,7 @@ __global__ void __launch_bounds__(kPassTPB, 4) pass_kernel(LevelArgs a) {
             const uint32_t r = rk.y;
             const bool valid = r != kNoRegion;
             const uint32_t active = __ballot_sync(0xffffffffu, valid);
-            if (!active) break;
+            if (!active) continue;  // past the end, or only records of points outside their image
             const int last = 31 - __clz(active);
             const uint32_t r0 = __shfl_sync(0xffffffffu, r, 0);
             const uint32_t rl = __shfl_sync(0xffffffffu, r, last);

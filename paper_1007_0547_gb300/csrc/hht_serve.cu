@@ -1,18 +1,35 @@
-// Serving entry points: hht_submit / hht_progress / hht_poll.
+// Serving: hht_submit / hht_progress / hht_poll with continuous batching.
 //
-// Requests are copied into library-owned host memory at submit time.  Each
-// hht_progress() call takes every queued request and runs them together as
-// one batch through the level loop; results wait in a table until polled.
+// The engine keeps a level loop running on the device.  Every unit (one half
+// of one request) carries the loop step t0 at which it was admitted and is at
+// level (step - t0); the stage / select / pass kernels read that per unit, so
+// units of different ages share every launch.  One hht_progress() call is one
+// step:
+//   1. admit waiting requests while request slots and the memory budget allow:
+//      their level-0 regions, vote counters and voter streams are appended to
+//      the current step's (stage kernel);
+//   2. select: children of every current region (or leaves, for units that
+//      reach their depth now);
+//   3. pass: the next step's voter stream and vote counters;
+//   4. requests whose units reached their depth at this step are complete:
+//      their leaves (one block per unit, in the paper's depth-first order) and
+//      statistics are copied out and their slot and budget are released.
+// Requests that arrive while others run are admitted at the next step and
+// overlap with them on the device; results do not depend on the mix.
 #include <cuda_runtime.h>
 
-#include <cstdint>
 #include <algorithm>
+#include <cmath>
+#include <cstdint>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <mutex>
 #include <vector>
 
 #include "../../include/hht.h"
+#include "hht_ctx.h"
+#include "hht_internal.h"
 #include "hht_serve.h"
 
 namespace hht {
@@ -20,17 +37,36 @@ namespace hht {
 struct Request {
     std::vector<hht_point> pts;
     hht_image im{};
+    int slot = -1;
+    int64_t t0 = 0;
+    uint64_t est = 0;
     bool done = false;
+    bool range_error = false;
     int status = HHT_E_PENDING;
-    hht_result res{};
     std::vector<hht_leaf> leaves;
+    hht_result res{};
 };
 
 struct ServeState {
+    static constexpr int kSlots = 1024;  // requests in flight at most (two units each)
+
+    std::mutex mu;
     uint64_t next_ticket = 1;
     std::map<uint64_t, Request> reqs;
-    std::vector<uint64_t> queue;
-    std::mutex mu;
+    std::deque<uint64_t> waiting;
+
+    // engine
+    bool init = false;
+    std::vector<int> free_slots;
+    std::vector<uint64_t> order;  // tickets in flight, in admission order (= record order)
+    uint64_t in_flight_bytes = 0, budget = 0;
+    int n_i64 = 0;
+    int64_t step = 0;
+    int par = 0;
+    uint64_t P = 0, NV = 0;  // regions and voters of the current step
+    DevBuf units, stats, infos, status, leaf_total, img_err, scan, pts, img_start, img_unit;
+    DevBuf rec[2], preg[2], cnt[2], vox[2], cursors, leaves, sel_flags, sel_data;
+    std::vector<hht_leaf> h_leaves;
 };
 
 void serve_destroy(ServeState* s) { delete s; }
@@ -40,11 +76,281 @@ void serve_destroy(ServeState* s) { delete s; }
 using namespace hht;
 
 namespace {
+
 ServeState* serve_of(hht_ctx* c) {
     ServeState** slot = hht_internal_serve_slot(c);
     if (!*slot) *slot = new ServeState();
     return *slot;
 }
+
+uint64_t request_bytes(const hht_image& im) {
+    // voter streams of the two deepest written levels, both halves, dense regime
+    const double n = (double)im.n;
+    const int D = im.depth;
+    const double dense = D < 3 ? n : 1.25 * n * (std::ldexp(1.0, D - 2) + std::ldexp(1.0, D - 3));
+    return (uint64_t)(2.0 * 8.0 * dense * 1.2 + 64.0 * n + (1 << 16));
+}
+
+#define SV_CK(call)                     \
+    do {                                \
+        cudaError_t e_ = (call);        \
+        if (e_ != cudaSuccess) {        \
+            cudaGetLastError();         \
+            return HHT_E_CUDA;          \
+        }                               \
+    } while (0)
+#define SV_RK(call)                  \
+    do {                             \
+        int r_ = (call);             \
+        if (r_ != HHT_OK) return r_; \
+    } while (0)
+
+int engine_init(hht_ctx* c, ServeState* S) {
+    const int U = 2 * ServeState::kSlots;
+    SV_RK(ensure(c, S->units, U * sizeof(Unit), true));
+    SV_RK(ensure(c, S->stats, (size_t)U * (kMaxDepth + 1) * 4 * sizeof(uint64_t), true));
+    SV_RK(ensure(c, S->infos, 2 * sizeof(LevelInfo), true));
+    SV_RK(ensure(c, S->status, sizeof(DeviceStatus), true));
+    SV_RK(ensure(c, S->leaf_total, sizeof(uint64_t), true));
+    SV_RK(ensure(c, S->scan, sizeof(ScanState), true));
+    for (int s = ServeState::kSlots - 1; s >= 0; --s) S->free_slots.push_back(s);
+    if (c->budget) {
+        S->budget = c->budget;
+    } else {
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        S->budget = (uint64_t)(0.5 * (double)fr);
+    }
+    S->init = true;
+    return HHT_OK;
+}
+
+// Admit waiting requests into the current step.
+int engine_admit(hht_ctx* c, ServeState* S) {
+    std::vector<uint64_t> adm;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        while (!S->waiting.empty() && !S->free_slots.empty()) {
+            Request& r = S->reqs[S->waiting.front()];
+            if (!S->order.empty() || !adm.empty()) {
+                if (S->in_flight_bytes + r.est > S->budget) break;
+            }
+            adm.push_back(S->waiting.front());
+            S->waiting.pop_front();
+            S->in_flight_bytes += r.est;
+        }
+    }
+    if (adm.empty()) return HHT_OK;
+    cudaStream_t st = c->stream;
+    const int m = (int)adm.size();
+    std::vector<Unit> nu(2 * m);
+    std::vector<uint64_t> img_start(m + 1);
+    std::vector<uint32_t> img_unit(m);
+    std::vector<Region> roots(2 * m);
+    std::vector<hht_point> pts;
+    uint64_t total = 0, v0 = 0;
+    for (int k = 0; k < m; ++k) {
+        Request& r = S->reqs[adm[k]];
+        r.slot = S->free_slots.back();
+        S->free_slots.pop_back();
+        r.t0 = S->step;
+        const int lL = ceil_log2_i(std::max(r.im.W, r.im.H));
+        if (lL + r.im.depth > 27) ++S->n_i64;
+        img_start[k] = total;
+        img_unit[k] = (uint32_t)(2 * r.slot);
+        for (int h = 0; h < 2; ++h) {
+            Unit& U = nu[2 * k + h];
+            std::memset(&U, 0, sizeof U);
+            U.lL = lL; U.D = r.im.depth; U.T = r.im.T; U.image = k; U.n = r.im.n;
+            U.W = r.im.W; U.H = r.im.H; U.half = h; U.t0 = (int32_t)S->step;
+            U.root_rec = (uint32_t)(S->P + 2 * k + h);
+            U.v0_off = S->NV + v0;
+            if (U.D >= 2) v0 += (uint64_t)r.im.n;
+            roots[2 * k + h] = Region{(uint32_t)(2 * r.slot + h), 0u, 0u, (uint32_t)r.im.n};
+        }
+        pts.insert(pts.end(), r.pts.begin(), r.pts.end());
+        total += (uint64_t)r.im.n;
+        S->order.push_back(adm[k]);
+    }
+    img_start[m] = total;
+    // device buffers: the current step's records, counters and stream grow in place
+    const int cp = S->par;
+    SV_RK(ensure_keep(c, S->rec[cp], (S->P + 2 * m) * sizeof(Region), S->P * sizeof(Region)));
+    SV_RK(ensure_keep(c, S->cnt[cp], (S->P + 2 * m) * 16, S->P * 16));
+    SV_RK(ensure_keep(c, S->vox[cp], std::max<uint64_t>(S->NV + v0, 1) * sizeof(Voter), S->NV * sizeof(Voter)));
+    SV_RK(ensure(c, S->pts, std::max<uint64_t>(total, 1) * sizeof(hht_point)));
+    SV_RK(ensure(c, S->img_start, (m + 1) * sizeof(uint64_t)));
+    SV_RK(ensure(c, S->img_unit, m * sizeof(uint32_t)));
+    SV_RK(ensure(c, S->img_err, m * sizeof(uint32_t)));
+    for (int k = 0; k < m; ++k) {
+        const Request& r = S->reqs[adm[k]];
+        SV_CK(cudaMemcpyAsync((Unit*)S->units.p + 2 * r.slot, &nu[2 * k], 2 * sizeof(Unit), cudaMemcpyHostToDevice, st));
+        // statistics rows of the two units: level 0 tested 1, passed 1, n codes
+        std::vector<uint64_t> rows(2 * (kMaxDepth + 1) * 4, 0);
+        for (int h = 0; h < 2; ++h) {
+            rows[(size_t)h * (kMaxDepth + 1) * 4 + 0] = 1;
+            rows[(size_t)h * (kMaxDepth + 1) * 4 + 1] = 1;
+            rows[(size_t)h * (kMaxDepth + 1) * 4 + 3] = (uint64_t)r.im.n;
+        }
+        SV_CK(cudaMemcpyAsync((uint64_t*)S->stats.p + (size_t)2 * r.slot * (kMaxDepth + 1) * 4, rows.data(),
+                              rows.size() * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+    }
+    if (total > 0)
+        SV_CK(cudaMemcpyAsync(S->pts.p, pts.data(), total * sizeof(hht_point), cudaMemcpyHostToDevice, st));
+    SV_CK(cudaMemcpyAsync(S->img_start.p, img_start.data(), (m + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+    SV_CK(cudaMemcpyAsync(S->img_unit.p, img_unit.data(), m * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    SV_CK(cudaMemsetAsync(S->img_err.p, 0, m * sizeof(uint32_t), st));
+    SV_CK(cudaMemcpyAsync((Region*)S->rec[cp].p + S->P, roots.data(), 2 * m * sizeof(Region), cudaMemcpyHostToDevice, st));
+    SV_CK(cudaMemsetAsync((char*)S->cnt[cp].p + S->P * 16, 0, 2 * m * 16, st));
+    if (launch_stage((const int16_t*)S->pts.p, total, (const Unit*)S->units.p, m, (const uint64_t*)S->img_start.p,
+                     (const uint32_t*)S->img_unit.p, (Voter*)S->vox[cp].p, (uint32_t*)S->cnt[cp].p,
+                     (uint64_t*)S->stats.p, (uint32_t*)S->img_err.p, (DeviceStatus*)S->status.p, S->n_i64 > 0,
+                     st) != 0)
+        return HHT_E_CUDA;
+    std::vector<uint32_t> err(m, 0);
+    SV_CK(cudaMemcpyAsync(err.data(), S->img_err.p, m * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    SV_CK(cudaStreamSynchronize(st));
+    for (int k = 0; k < m; ++k)
+        if (err[k]) S->reqs[adm[k]].range_error = true;
+    S->P += 2 * (uint64_t)m;
+    S->NV += v0;
+    return HHT_OK;
+}
+
+// Copy out the requests whose units reached their depth in the step just run.
+int engine_complete(hht_ctx* c, ServeState* S, uint64_t step_leaves) {
+    cudaStream_t st = c->stream;
+    std::vector<uint64_t> fin;
+    for (uint64_t t : S->order) {
+        const Request& r = S->reqs[t];
+        if (r.t0 + r.im.depth == S->step) fin.push_back(t);
+    }
+    if (fin.empty()) return HHT_OK;
+    if (step_leaves > 0) {
+        if (launch_unit_to_half(S->leaves.p, step_leaves, st) != 0) return HHT_E_CUDA;
+        S->h_leaves.resize(step_leaves);
+        SV_CK(cudaMemcpyAsync(S->h_leaves.data(), S->leaves.p, step_leaves * sizeof(hht_leaf), cudaMemcpyDeviceToHost, st));
+    }
+    std::vector<std::vector<uint64_t>> rows(fin.size(), std::vector<uint64_t>(2 * (kMaxDepth + 1) * 4));
+    for (size_t k = 0; k < fin.size(); ++k) {
+        const Request& r = S->reqs[fin[k]];
+        SV_CK(cudaMemcpyAsync(rows[k].data(), (uint64_t*)S->stats.p + (size_t)2 * r.slot * (kMaxDepth + 1) * 4,
+                              rows[k].size() * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    }
+    SV_CK(cudaStreamSynchronize(st));
+    // the step's leaves are one block per finishing unit, in record (= admission) order
+    uint64_t off = 0;
+    std::lock_guard<std::mutex> lk(S->mu);
+    for (size_t k = 0; k < fin.size(); ++k) {
+        Request& r = S->reqs[fin[k]];
+        const int D = r.im.depth;
+        hht_result& res = r.res;
+        std::memset(&res, 0, sizeof res);
+        res.depth = D;
+        res.L = 1 << ceil_log2_i(std::max(r.im.W, r.im.H));
+        uint64_t nl = 0;
+        for (int h = 0; h < 2; ++h) {
+            const uint64_t* su = rows[k].data() + (size_t)h * (kMaxDepth + 1) * 4;
+            for (int l = 0; l <= D; ++l) {
+                res.stats[h][l].tested = su[4 * l + 0];
+                res.stats[h][l].passed = su[4 * l + 1];
+                res.stats[h][l].votes = su[4 * l + 2];
+                res.stats[h][l].tests = su[4 * l + 3];
+            }
+            nl += su[4 * D + 1];
+        }
+        res.n_leaves = nl;
+        if (off + nl > step_leaves) return HHT_E_CUDA;
+        r.leaves.assign(S->h_leaves.begin() + off, S->h_leaves.begin() + off + nl);
+        off += nl;
+        r.status = r.range_error ? HHT_E_RANGE : HHT_OK;
+        r.done = true;
+        r.pts.clear();
+        r.pts.shrink_to_fit();
+        S->free_slots.push_back(r.slot);
+        S->in_flight_bytes -= r.est;
+        if (ceil_log2_i(std::max(r.im.W, r.im.H)) + D > 27) --S->n_i64;
+    }
+    if (off != step_leaves) return HHT_E_CUDA;
+    std::vector<uint64_t> keep;
+    for (uint64_t t : S->order)
+        if (!S->reqs[t].done) keep.push_back(t);
+    S->order.swap(keep);
+    return HHT_OK;
+}
+
+int engine_step(hht_ctx* c, ServeState* S) {
+    cudaStream_t st = c->stream;
+    if (!S->init) SV_RK(engine_init(c, S));
+    SV_RK(engine_admit(c, S));
+    if (S->order.empty()) return HHT_OK;
+    const int cp = S->par, np = cp ^ 1;
+    const uint64_t P = S->P;
+    LevelInfo* d_infos = (LevelInfo*)S->infos.p;
+    // the parents' totals (after admission) for the kernels
+    SV_CK(cudaMemcpyAsync(&d_infos[cp].n_regions, &S->P, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+    SV_CK(cudaMemcpyAsync(&d_infos[cp].n_voters, &S->NV, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+    SV_CK(cudaMemsetAsync(&d_infos[np], 0, sizeof(LevelInfo), st));
+    SV_CK(cudaMemsetAsync(S->leaf_total.p, 0, sizeof(uint64_t), st));
+    LevelInfo h_next{};
+    if (P > 0) {
+        const uint64_t sel_tiles = (P + 1023) / 1024;
+        SV_RK(ensure(c, S->preg[cp], P * sizeof(PassRegion)));
+        SV_RK(ensure(c, S->rec[np], 4 * P * sizeof(Region)));
+        SV_RK(ensure(c, S->cnt[np], 4 * P * 16));
+        SV_RK(ensure(c, S->cursors, 4 * P * sizeof(unsigned long long)));
+        SV_RK(ensure(c, S->leaves, 4 * P * sizeof(DevLeaf)));
+        if ((sel_tiles + 1) * 4 > S->sel_flags.bytes) SV_RK(ensure(c, S->sel_flags, (sel_tiles + 1) * 4, true));
+        SV_RK(ensure(c, S->sel_data, (sel_tiles + 1) * 2 * 3 * sizeof(uint64_t)));
+        LevelArgs a{};
+        a.units = (const Unit*)S->units.p;
+        a.parents = (const Region*)S->rec[cp].p;
+        a.pregions = (PassRegion*)S->preg[cp].p;
+        a.parent_cnt = (const uint32_t*)S->cnt[cp].p;
+        a.children = (Region*)S->rec[np].p;
+        a.child_cnt = (uint32_t*)S->cnt[np].p;
+        a.cursor = (unsigned long long*)S->cursors.p;
+        a.leaves = (DevLeaf*)S->leaves.p;
+        a.stats = (uint64_t*)S->stats.p;
+        a.info_prev = d_infos + cp;
+        a.info = d_infos + np;
+        a.leaf_total = (uint64_t*)S->leaf_total.p;
+        a.scan = (ScanState*)S->scan.p;
+        a.tile_flags = (uint32_t*)S->sel_flags.p;
+        a.tile_data = (uint64_t*)S->sel_data.p;
+        a.status = (DeviceStatus*)S->status.p;
+        a.cap_children = 4 * P;
+        a.cap_leaves = 4 * P;
+        a.cap_voters = UINT64_MAX;
+        a.level = (int32_t)(S->step + 1);
+        a.num_sms = c->num_sms;
+        const int sel_grid = (int)std::min<uint64_t>(sel_tiles, (uint64_t)c->num_sms * c->occ_select);
+        if (launch_select(a, 256, std::max(sel_grid, 1), st) != 0) return HHT_E_CUDA;
+        DeviceStatus hs{};
+        SV_CK(cudaMemcpyAsync(&h_next, d_infos + np, sizeof h_next, cudaMemcpyDeviceToHost, st));
+        SV_CK(cudaMemcpyAsync(&hs, S->status.p, sizeof hs, cudaMemcpyDeviceToHost, st));
+        SV_CK(cudaStreamSynchronize(st));
+        if (hs.err & kErrTimeout) return HHT_E_TIMEOUT;
+        if (hs.err) return HHT_E_CUDA;
+        if (S->NV > 0) {
+            SV_RK(ensure(c, S->vox[np], std::max<uint64_t>(h_next.n_voters, 1) * sizeof(Voter)));
+            a.vin = (const Voter*)S->vox[cp].p;
+            a.vout = (Voter*)S->vox[np].p;
+            a.cap_voters = h_next.n_voters;
+            const bool i64 = S->n_i64 > 0;
+            const uint64_t want = (S->NV + 2047) / 2048;
+            const int grid = (int)std::min<uint64_t>(want, (uint64_t)c->num_sms * (i64 ? c->occ_pass64 : c->occ_pass32));
+            if (launch_pass(a, i64, std::max(grid, 1), st) != 0) return HHT_E_CUDA;
+        }
+    }
+    S->step += 1;
+    SV_RK(engine_complete(c, S, h_next.n_leaves));
+    S->P = h_next.n_regions;
+    S->NV = h_next.n_voters;
+    S->par = np;
+    return HHT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -56,17 +362,22 @@ int hht_submit(hht_ctx* c, const hht_image* image, uint64_t* ticket) {
         im.H > HHT_MAX_SIDE || im.depth < 1 || im.depth > HHT_MAX_DEPTH || im.T < 1)
         return HHT_E_ARG;
     ServeState* s = serve_of(c);
+    std::vector<hht_point> pts((size_t)im.n);
+    if (im.n > 0) {
+        cudaSetDevice(c->device);
+        if (cudaMemcpy(pts.data(), im.points, (size_t)im.n * sizeof(hht_point), cudaMemcpyDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return HHT_E_CUDA;
+        }
+    }
     std::lock_guard<std::mutex> lk(s->mu);
     const uint64_t t = s->next_ticket++;
     Request& r = s->reqs[t];
-    r.pts.resize((size_t)im.n);
-    if (im.n > 0 && cudaMemcpy(r.pts.data(), im.points, (size_t)im.n * sizeof(hht_point), cudaMemcpyDefault) != cudaSuccess) {
-        s->reqs.erase(t);
-        return HHT_E_CUDA;
-    }
+    r.pts.swap(pts);
     r.im = im;
     r.im.points = r.pts.data();
-    s->queue.push_back(t);
+    r.est = request_bytes(im);
+    s->waiting.push_back(t);
     *ticket = t;
     return HHT_OK;
 }
@@ -74,36 +385,27 @@ int hht_submit(hht_ctx* c, const hht_image* image, uint64_t* ticket) {
 int hht_progress(hht_ctx* c) {
     if (!c) return HHT_E_ARG;
     ServeState* s = serve_of(c);
-    std::vector<uint64_t> batch;
-    {
-        std::lock_guard<std::mutex> lk(s->mu);
-        batch.swap(s->queue);
-    }
-    if (batch.empty()) return 0;
-    std::vector<hht_image> ims(batch.size());
-    std::vector<hht_result> outs(batch.size());
-    {
-        std::lock_guard<std::mutex> lk(s->mu);
-        for (size_t k = 0; k < batch.size(); ++k) {
-            Request& r = s->reqs[batch[k]];
-            ims[k] = r.im;
-            // leaf capacity: every leaf is a cell of one of the two K x K grids
-            const uint64_t K = 1ull << r.im.depth;
-            const uint64_t cap = std::min<uint64_t>(2 * K * K, 1ull << 26);
-            r.leaves.resize((size_t)cap);
-            outs[k].leaves = r.leaves.data();
-            outs[k].leaf_capacity = cap;
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    const int rc = engine_step(c, s);
+    if (rc != HHT_OK) {
+        // the running loop is lost: fail every request in it and start afresh
+        std::lock_guard<std::mutex> lk2(s->mu);
+        for (uint64_t t : s->order) {
+            Request& r = s->reqs[t];
+            r.done = true;
+            r.status = rc;
+            s->free_slots.push_back(r.slot);
         }
+        s->order.clear();
+        s->in_flight_bytes = 0;
+        s->n_i64 = 0;
+        s->P = s->NV = 0;
+        cudaMemsetAsync(s->status.p, 0, sizeof(DeviceStatus), c->stream);
+        return rc;
     }
-    hht_internal_run_job(c, ims.data(), (int)ims.size(), outs.data());
-    std::lock_guard<std::mutex> lk(s->mu);
-    for (size_t k = 0; k < batch.size(); ++k) {
-        Request& r = s->reqs[batch[k]];
-        r.res = outs[k];
-        r.status = outs[k].status;
-        r.done = true;
-    }
-    return 0;
+    std::lock_guard<std::mutex> lk2(s->mu);
+    return (int)(s->order.size() + s->waiting.size());
 }
 
 int hht_poll(hht_ctx* c, uint64_t ticket, hht_result* out) {
@@ -125,8 +427,13 @@ int hht_poll(hht_ctx* c, uint64_t ticket, hht_result* out) {
             out->n_leaves = res.n_leaves;
             return HHT_E_CAPACITY;  // the ticket stays valid: poll again with a larger buffer
         }
-        if (res.n_leaves && cudaMemcpy(dst, r.leaves.data(), res.n_leaves * sizeof(hht_leaf), cudaMemcpyDefault) != cudaSuccess)
-            rc = HHT_E_CUDA;
+        if (res.n_leaves) {
+            cudaSetDevice(c->device);
+            if (cudaMemcpy(dst, r.leaves.data(), res.n_leaves * sizeof(hht_leaf), cudaMemcpyDefault) != cudaSuccess) {
+                cudaGetLastError();
+                rc = HHT_E_CUDA;
+            }
+        }
     }
     *out = res;
     out->status = rc;

@@ -246,3 +246,17 @@ def test_small_budget_splits_the_batch_into_waves(hht):
     for a, b in zip(ref, got):
         assert np.array_equal(a.leaves_numpy(), b.leaves_numpy())
         assert np.array_equal(a.stats, b.stats)
+
+
+def test_range_error_in_a_batch_leaves_other_images_intact(ctx, hht):
+    """Points outside an image (more than a warp step of them, between valid
+    ones) fail that image only; the images around it in the same level
+    streams are unchanged."""
+    imgs = [synth.plain_128(index=k) for k in range(3)]
+    bad = np.concatenate([imgs[1].points[:50], np.full((70, 2), 200, np.int16), imgs[1].points[50:]])
+    batch = [(imgs[0].points, 128, 128, 7, 20), (bad, 128, 128, 7, 20), (imgs[2].points, 128, 128, 7, 20)]
+    res = ctx.detect_batch(batch, raise_on_error=False)
+    assert res[1].status == hht.HHT_E_RANGE
+    for k in (0, 2):
+        assert res[k].status == hht.HHT_OK
+        _same(res[k], oracle.detect(imgs[k].points, 128, 128, 7, 20))

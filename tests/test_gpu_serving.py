@@ -1,0 +1,112 @@
+"""Serving with continuous batching (hht_submit / hht_progress / hht_poll).
+
+Requests join a running level loop at different steps and share every launch
+with the requests already in flight; each result must be identical to the
+same image run alone with hht_detect (exact: results are integers)."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hht():
+    from paper_1007_0547_gb300 import build
+    build.build()
+    from paper_1007_0547_gb300 import hht as mod
+    return mod
+
+
+def _alone(hht, imgs):
+    ctx = hht.Context(device=0)
+    out = [ctx.detect(im.points, im.W, im.H, im.depth, im.T, leaves_on_device=False) for im in imgs]
+    ctx.close()
+    return out
+
+
+def _same(a, b):
+    assert np.array_equal(a.leaves_numpy(), b.leaves_numpy())
+    assert np.array_equal(a.stats, b.stats)
+
+
+def _mixed_requests():
+    imgs = [synth.plain_128(index=k) for k in range(3)]
+    imgs += [synth.random_small(900 + s, max_side=300, max_n=2000, max_depth=9, max_T=10) for s in range(6)]
+    imgs += [synth.batch_image(k) for k in (0, 1)]
+    imgs += [synth.serving_request(k) for k in range(4) if synth.serving_request(k).W <= 1024]
+    return imgs
+
+
+def test_requests_joining_mid_flight_match_alone(hht):
+    imgs = _mixed_requests()
+    want = _alone(hht, imgs)
+    ctx = hht.Context(device=0)
+    tickets = {}
+    # stagger arrivals: a few requests per step while earlier ones run
+    pending = list(range(len(imgs)))
+    steps = 0
+    results = {}
+    while pending or len(results) < len(imgs):
+        for _ in range(2):
+            if pending:
+                k = pending.pop(0)
+                im = imgs[k]
+                tickets[ctx.submit(im.points, im.W, im.H, im.depth, im.T)] = k
+        ctx.progress()
+        steps += 1
+        for t, k in list(tickets.items()):
+            r = ctx.poll(t)
+            if r is not None:
+                results[k] = r
+                del tickets[t]
+        assert steps < 500
+    for k in range(len(imgs)):
+        _same(results[k], want[k])
+    ctx.close()
+
+
+def test_small_budget_admits_gradually(hht):
+    imgs = [synth.batch_image(k) for k in (2, 4, 5)] + [synth.plain_128(index=4)]
+    want = _alone(hht, imgs)
+    ctx = hht.Context(device=0, mem_budget=600_000_000)
+    tickets = [ctx.submit(im.points, im.W, im.H, im.depth, im.T) for im in imgs]
+    got = [None] * len(imgs)
+    for _ in range(400):
+        left = ctx.progress()
+        for i, t in enumerate(tickets):
+            if got[i] is None:
+                got[i] = ctx.poll(t)
+        if all(g is not None for g in got):
+            break
+    for a, b in zip(got, want):
+        _same(a, b)
+    ctx.close()
+
+
+def test_bad_request_fails_alone(hht):
+    good = synth.plain_128(index=1)
+    want = _alone(hht, [good])[0]
+    ctx = hht.Context(device=0)
+    bad_pts = np.array([[5, 3], [40, 2]], np.int16)
+    tb = ctx.submit(bad_pts, 32, 32, 5, 1)
+    tg = ctx.submit(good.points, good.W, good.H, good.depth, good.T)
+    res_g, err = None, None
+    for _ in range(50):
+        ctx.progress()
+        if err is None:
+            try:
+                if ctx.poll(tb) is not None:
+                    err = "no error"
+            except hht.HhtError as e:
+                err = e.code
+        if res_g is None:
+            res_g = ctx.poll(tg)
+        if res_g is not None and err is not None:
+            break
+    assert err == hht.HHT_E_RANGE
+    _same(res_g, want)
+    with pytest.raises(hht.HhtError):
+        ctx.poll(tb)  # the ticket was released
+    ctx.close()
