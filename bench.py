@@ -174,6 +174,70 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args, rank):
+    """Open-loop Poisson stream of detection requests through hht_submit /
+    hht_progress / hht_poll (continuous batching).  Rate = --serve-load x the
+    saturated request rate measured first on the same requests."""
+    import torch
+    from paper_1007_0547_gb300 import build as hbuild
+    hbuild.build()
+    from paper_1007_0547_gb300 import hht
+    if rank != 0:
+        return
+    reqs = synth.serving_requests(args.serve_requests)
+    ctx = hht.Context(device=0)
+
+    def drain(arrivals):
+        """Submit request k at arrivals[k] (s after start); return per-request
+        (arrival, done) wall times and the total time."""
+        n = len(reqs)
+        t_arr = [0.0] * n
+        t_done = [0.0] * n
+        tickets = {}
+        k = 0
+        done = 0
+        t0 = time.perf_counter()
+        while done < n:
+            now = time.perf_counter() - t0
+            while k < n and arrivals[k] <= now:
+                im = reqs[k]
+                tickets[ctx.submit(im.points, im.W, im.H, im.depth, im.T)] = k
+                t_arr[k] = arrivals[k]
+                k += 1
+            if tickets:
+                ctx.progress()
+                now = time.perf_counter() - t0
+                for t, j in list(tickets.items()):
+                    if ctx.poll(t) is not None:
+                        t_done[j] = now
+                        del tickets[t]
+                        done += 1
+            elif k < n:
+                time.sleep(max(0.0, min(0.01, arrivals[k] - now)))
+        return t_arr, t_done, time.perf_counter() - t0
+
+    # warm-up on a few requests, then the saturated rate (everything at t = 0)
+    for im in reqs[:8]:
+        ctx.detect(im.points, im.W, im.H, im.depth, im.T)
+    torch.cuda.synchronize()
+    _, _, sat_s = drain([0.0] * len(reqs))
+    sat_rate = len(reqs) / sat_s
+    rate = args.serve_load * sat_rate
+    arrivals = list(synth.poisson_arrivals(len(reqs), rate))
+    t_arr, t_done, total_s = drain(arrivals)
+    lat = sorted((d - a) * 1e3 for a, d in zip(t_arr, t_done))
+    line = {"metric": "serving latency p50/p99 (ms) and images/s", "value": lat[len(lat) // 2], "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+            "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "images_per_s": len(reqs) / total_s, "saturated_images_per_s": sat_rate,
+            "offered_rate_per_s": rate, "load": args.serve_load,
+            "config": {"workload": "serving", "requests": len(reqs),
+                       "description": "side log-uniform 64-4096, 1-256 segments, noise 0-3%, depth ceil(log2 side), "
+                                      "T uniform 16-256; Poisson arrivals"}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -183,6 +247,9 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="batch_256")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serve", action="store_true", help="open-loop serving benchmark instead of the batch line")
+    ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--serve-load", type=float, default=0.8, help="offered rate as a fraction of the saturated rate")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
@@ -192,6 +259,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.serve:
+        run_serving(args, rank)
         return
 
     import torch
