@@ -247,6 +247,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="batch_256")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--serve", action="store_true", help="open-loop serving benchmark instead of the batch line")
     ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--serve-load", type=float, default=0.8, help="offered rate as a fraction of the saturated rate")
@@ -289,6 +290,11 @@ def main():
             return [ctx.detect(*dev_images[0])]
         return ctx.detect_batch(dev_images)
 
+    tuning = None
+    if not args.no_autotune:
+        # tile shape of the level kernel for this workload (cached per device and workload class)
+        shape, times = ctx.autotune(dev_images, cache=os.environ.get("HHT_TUNE_CACHE"))
+        tuning = {"shape": shape, "pass_ms_per_shape": times}
     for _ in range(args.warmup):
         res = step()
     torch.cuda.synchronize()
@@ -416,6 +422,7 @@ def main():
         "cpu_baseline": cpu,
         "clocks": clocks,
         "gpu_launches": int(prof["launches"]),
+        "autotune": tuning,
     }
     print(json.dumps(line), flush=True)
     ctx.close()

@@ -219,6 +219,21 @@ int hht_profile_read(hht_ctx *ctx, hht_profile_counters *out);
 int hht_detect_noalloc(const hht_point *points, int64_t n, int32_t W, int32_t H, int32_t depth, int32_t T,
                        hht_leaf *leaves, uint64_t leaf_capacity, hht_result *out, void *cuda_stream);
 
+/*
+ * Autotuning of the level kernel's tile shape: voters per warp chunk (one
+ * segment reservation per child and chunk), threads per block and resident
+ * blocks per SM; HHT_TUNE_SHAPES shapes are compiled, shape 0 is the default.
+ * hht_autotune() runs `images` once per shape (plus one warm-up run), keeps
+ * the shape whose level kernels took the least device time for this context,
+ * stores it in *best and, if ms_per_shape is not NULL, the per-shape times
+ * (HHT_TUNE_SHAPES doubles).  hht_set_tuning() selects a shape directly (for
+ * instance one cached from an earlier hht_autotune).  Results never depend on
+ * the shape.  Errors: HHT_E_ARG, and those of hht_detect_batch.
+ */
+#define HHT_TUNE_SHAPES 6
+int hht_autotune(hht_ctx *ctx, const hht_image *images, int32_t count, int32_t *best, double *ms_per_shape);
+int hht_set_tuning(hht_ctx *ctx, int32_t shape);
+
 /* Short description of an HHT_* code (static string). */
 const char *hht_strerror(int code);
 

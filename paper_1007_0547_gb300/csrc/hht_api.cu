@@ -351,13 +351,15 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
         a.vin = (const Voter*)c->vox[pi].p;
         a.vout = (Voter*)c->vox[ci].p;
         a.cap_voters = nout;
-        const int occ = i64 ? c->occ_pass64 : c->occ_pass32;
-        // enough 32-voter warp slices to fill the device, no more than the stream needs
-        const uint64_t want_blocks = (nin + kPassTile - 1) / kPassTile;
+        const int shape = i64 ? 0 : c->pass_shape;
+        const int occ = i64 ? c->occ_pass64 : c->occ_shape[shape];
+        // enough warp slices to fill the device, no more than the stream needs
+        const uint64_t tile = 8ull * (uint64_t)pass_threads(i64, shape);
+        const uint64_t want_blocks = (nin + tile - 1) / tile;
         const int pass_grid = (int)std::min<uint64_t>(want_blocks, (uint64_t)c->num_sms * occ);
         {
             ProfScope ps(c, 2);
-            if (launch_pass(a, i64, std::max(pass_grid, 1), st) != 0) return HHT_E_CUDA;
+            if (launch_pass(a, i64, std::max(pass_grid, 1), st, shape) != 0) return HHT_E_CUDA;
         }
         c->prof.launches += 1;
         c->prof.pass_launches += 1;
@@ -531,6 +533,11 @@ int hht_create(hht_ctx** out, int device, void* cuda_stream, uint64_t mem_budget
     c->occ_select = occupancy_select();
     c->occ_pass32 = occupancy_pass(false);
     c->occ_pass64 = occupancy_pass(true);
+    for (int k = 0; k < kPassShapeCount; ++k) c->occ_shape[k] = occupancy_pass(false, k);
+    if (const char* e = getenv("HHT_PASS_SHAPE")) {
+        const int k = atoi(e);
+        if (k >= 0 && k < kPassShapeCount) c->pass_shape = k;
+    }
     int rc = ensure(c, c->scan_states, 8 * sizeof(ScanState), true);
     if (rc == HHT_OK) {
         std::vector<ScanState> init(8, ScanState{0u, 0u, 1u, 0u});
@@ -600,6 +607,53 @@ int hht_fetch_leaves(hht_ctx* c, int32_t index, hht_leaf* leaves, uint64_t capac
     CK(cudaMemcpyAsync(leaves, (const char*)c->leaves.p + c->job_off[index] * sizeof(DevLeaf), n * sizeof(hht_leaf),
                        cudaMemcpyDefault, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    return HHT_OK;
+}
+
+int hht_set_tuning(hht_ctx* c, int32_t shape) {
+    if (!c || shape < 0 || shape >= kPassShapeCount) return HHT_E_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->pass_shape = shape;
+    return HHT_OK;
+}
+
+int hht_autotune(hht_ctx* c, const hht_image* images, int32_t count, int32_t* best, double* ms_per_shape) {
+    if (!c || !best || count < 1 || !images) return HHT_E_ARG;
+    for (int g = 0; g < count; ++g) {
+        const int rc = check_image(images[g]);
+        if (rc != HHT_OK) return rc;
+    }
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    std::vector<hht_result> outs((size_t)count);
+    const bool was_profiling = c->profile;
+    const hht_profile_counters saved = c->prof;
+    double best_ms = 1e300;
+    int best_shape = c->pass_shape;
+    int rc = HHT_OK;
+    // warm-up with the current shape (allocations), then every shape timed by
+    // its pass launches; no leaves are copied out (HHT_E_CAPACITY is expected)
+    rc = run_job(c, images, count, outs.data());
+    if (rc == HHT_E_CAPACITY) rc = HHT_OK;
+    for (int k = 0; k < kPassShapeCount && rc == HHT_OK; ++k) {
+        c->pass_shape = k;
+        c->profile = true;
+        c->prof = hht_profile_counters{};
+        rc = run_job(c, images, count, outs.data());
+        if (rc == HHT_E_CAPACITY) rc = HHT_OK;
+        resolve_profile(c);
+        const double ms = c->prof.pass_ms;
+        if (ms_per_shape) ms_per_shape[k] = ms;
+        if (rc == HHT_OK && ms < best_ms) {
+            best_ms = ms;
+            best_shape = k;
+        }
+    }
+    c->pass_shape = best_shape;
+    c->profile = was_profiling;
+    c->prof = saved;
+    if (rc != HHT_OK) return rc;
+    *best = best_shape;
     return HHT_OK;
 }
 

@@ -36,6 +36,8 @@ struct hht_ctx {
     uint64_t held = 0;
     int num_sms = 0;
     int occ_select = 1, occ_pass32 = 1, occ_pass64 = 1;
+    int pass_shape = 0;                                   // pass-kernel tile shape (autotuned)
+    int occ_shape[hht::kPassShapeCount] = {1, 1, 1, 1, 1, 1};  // resident blocks per SM of each shape
 
     // job buffers
     DevBuf pts, img_start, img_unit, units, stats, infos, status, leaf_total, img_err, scan_states;

@@ -149,9 +149,12 @@ int launch_stage(const int16_t* pts, uint64_t total_points, const Unit* units, i
                  const uint64_t* img_start, const uint32_t* img_unit, Voter* vstream, uint32_t* cnt,
                  uint64_t* stats, uint32_t* img_err, DeviceStatus* status, bool int64_path, void* stream);
 int launch_select(const LevelArgs& a, int threads_per_block, int grid, void* stream);
-int launch_pass(const LevelArgs& a, bool int64_path, int grid, void* stream);
+// Pass-kernel tile shapes for the autotuner; shape 0 is the default.
+constexpr int kPassShapeCount = 6;
+int launch_pass(const LevelArgs& a, bool int64_path, int grid, void* stream, int shape = 0);
+int pass_threads(bool int64_path, int shape = 0);
 int occupancy_select();
-int occupancy_pass(bool int64_path);
+int occupancy_pass(bool int64_path, int shape = 0);
 
 // Rewrite each leaf's unit (2 * image + half) to its half.
 int launch_unit_to_half(void* leaves, uint64_t n, void* stream);

@@ -339,7 +339,6 @@ __global__ void __launch_bounds__(kSelTPB) select_kernel(LevelArgs a) {
 
 // ============================================================================ pass
 namespace {
-constexpr int kPassTPB = 256;
 
 // Child record index of quadrant q of a parent (its passed children are
 // stored consecutively in quadrant order).
@@ -422,7 +421,6 @@ struct ParentGeo {
 // on scheduling; no result depends on it (counts, leaves and statistics are
 // order-free).
 namespace {
-constexpr int kChunkSteps = 4;
 
 template <typename I>
 struct Classified {
@@ -461,8 +459,13 @@ __device__ __forceinline__ Classified<I> classify(const ParentGeo<I>& g, uint32_
 }
 }  // namespace
 
-template <typename I>
-__global__ void __launch_bounds__(kPassTPB, 4) pass_kernel(LevelArgs a) {
+// Tile shape (autotuned): STEPS warp steps of 32 voters per chunk (one
+// cursor reservation per child and chunk), TPB threads per block, at least
+// MINB resident blocks per SM (register budget).
+template <typename I, int STEPS, int TPB, int MINB>
+__global__ void __launch_bounds__(TPB, MINB) pass_kernel(LevelArgs a) {
+    constexpr int kChunkSteps = STEPS;
+    constexpr int kPassTPB = TPB;
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
     const uint64_t nin = a.info_prev->n_voters;
@@ -689,15 +692,6 @@ int occupancy_select() {
     return per_sm < 1 ? 1 : per_sm;
 }
 
-int occupancy_pass(bool int64_path) {
-    int per_sm = 0;
-    if (int64_path)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pass_kernel<int64_t>, kPassTPB, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pass_kernel<int32_t>, kPassTPB, 0);
-    return per_sm < 1 ? 1 : per_sm;
-}
-
 int launch_stage(const int16_t* pts, uint64_t total_points, const Unit* units, int n_images,
                  const uint64_t* img_start, const uint32_t* img_unit, Voter* v0, uint32_t* root_cnt,
                  uint64_t* stats, uint32_t* img_err, DeviceStatus* status, bool int64_path, void* stream) {
@@ -720,12 +714,48 @@ int launch_select(const LevelArgs& a, int tpb_unused, int grid, void* stream) {
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int launch_pass(const LevelArgs& a, bool int64_path, int grid, void* stream) {
-    if (int64_path)
-        pass_kernel<int64_t><<<grid, kPassTPB, 0, (cudaStream_t)stream>>>(a);
-    else
-        pass_kernel<int32_t><<<grid, kPassTPB, 0, (cudaStream_t)stream>>>(a);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+// Pass-kernel tile shapes: {steps per chunk, threads per block, min blocks per SM}.
+struct PassShape {
+    int steps, tpb, minb;
+};
+constexpr PassShape kPassShapes[kPassShapeCount] = {{4, 256, 4}, {2, 256, 4}, {8, 256, 3},
+                                                    {4, 128, 8}, {4, 256, 3}, {4, 512, 2}};
+
+namespace {
+template <int S>
+const void* pass_fn32() {
+    constexpr PassShape p = kPassShapes[S];
+    return (const void*)pass_kernel<int32_t, p.steps, p.tpb, p.minb>;
+}
+const void* pass_fn(bool int64_path, int shape) {
+    if (int64_path) return (const void*)pass_kernel<int64_t, 4, 256, 4>;
+    switch (shape) {
+        case 1: return pass_fn32<1>();
+        case 2: return pass_fn32<2>();
+        case 3: return pass_fn32<3>();
+        case 4: return pass_fn32<4>();
+        case 5: return pass_fn32<5>();
+        default: return pass_fn32<0>();
+    }
+}
+}  // namespace
+
+int pass_threads(bool int64_path, int shape) {
+    return int64_path ? 256 : kPassShapes[(shape >= 0 && shape < kPassShapeCount) ? shape : 0].tpb;
+}
+
+int occupancy_pass(bool int64_path, int shape) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pass_fn(int64_path, shape), pass_threads(int64_path, shape),
+                                                  0);
+    return per_sm < 1 ? 1 : per_sm;
+}
+
+int launch_pass(const LevelArgs& a, bool int64_path, int grid, void* stream, int shape) {
+    void* args[] = {(void*)&a};
+    const cudaError_t e = cudaLaunchKernel(pass_fn(int64_path, shape), dim3(grid), dim3(pass_threads(int64_path, shape)),
+                                           args, 0, (cudaStream_t)stream);
+    return e == cudaSuccess ? 0 : -1;
 }
 
 }  // namespace hht

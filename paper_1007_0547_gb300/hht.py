@@ -31,7 +31,8 @@ HHT_E_UNKNOWN_TICKET = -8
 # every function the C header declares
 EXPORTS = ("hht_create", "hht_destroy", "hht_detect", "hht_detect_batch", "hht_fetch_leaves", "hht_submit",
            "hht_poll", "hht_progress", "hht_profile_enable", "hht_profile_read", "hht_strerror", "hht_version",
-           "hht_detect_noalloc")
+           "hht_detect_noalloc", "hht_autotune", "hht_set_tuning")
+TUNE_SHAPES = 6
 
 
 class HhtError(RuntimeError):
@@ -91,6 +92,10 @@ def load(path: str = LIB_PATH):
     lib.hht_profile_enable.restype = ctypes.c_int
     lib.hht_profile_read.argtypes = [vp, ctypes.POINTER(_Profile)]
     lib.hht_profile_read.restype = ctypes.c_int
+    lib.hht_autotune.argtypes = [vp, ctypes.POINTER(_Image), i32, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)]
+    lib.hht_autotune.restype = ctypes.c_int
+    lib.hht_set_tuning.argtypes = [vp, i32]
+    lib.hht_set_tuning.restype = ctypes.c_int
     lib.hht_strerror.argtypes = [ctypes.c_int]
     lib.hht_strerror.restype = ctypes.c_char_p
     lib.hht_version.argtypes = []
@@ -256,6 +261,54 @@ class Context:
         if rc != HHT_OK and raise_on_error:
             raise HhtError(rc, "hht_detect_batch")
         return res
+
+    # ------------------------------------------------------------ autotuning
+    def set_tuning(self, shape: int) -> None:
+        rc = load().hht_set_tuning(self._h, int(shape))
+        if rc != HHT_OK:
+            raise HhtError(rc, "hht_set_tuning")
+
+    def autotune(self, images: Sequence[Tuple], cache: Optional[str] = None) -> Tuple[int, Optional[List[float]]]:
+        """Pick the level kernel's tile shape for workloads like `images`
+        ((points, W, H, depth, T) tuples).  With `cache` (a JSON file, default
+        $HHT_TUNE_CACHE), the choice is stored per (device, workload class) and
+        reused without timing."""
+        import json
+        import math
+        import torch
+        cache = cache or os.environ.get("HHT_TUNE_CACHE")
+        n_total = sum(_Points(im[0]).n for im in images)
+        key = (f"{torch.cuda.get_device_name(self.device)}|images={len(images)}|"
+               f"points~2^{int(math.log2(max(1, n_total)))}|depth<={max(int(im[3]) for im in images)}")
+        table = {}
+        if cache and os.path.exists(cache):
+            try:
+                with open(cache) as f:
+                    table = json.load(f)
+            except (OSError, ValueError):
+                table = {}
+        if key in table:
+            self.set_tuning(int(table[key]["shape"]))
+            return int(table[key]["shape"]), None
+        pts = [_Points(im[0]) for im in images]
+        arr = (_Image * len(images))()
+        for k, (im, p) in enumerate(zip(images, pts)):
+            arr[k].points = p.ptr
+            arr[k].n = p.n
+            arr[k].W, arr[k].H, arr[k].depth, arr[k].T = (int(v) for v in im[1:5])
+        best = ctypes.c_int32()
+        ms = (ctypes.c_double * TUNE_SHAPES)()
+        rc = load().hht_autotune(self._h, arr, len(images), ctypes.byref(best), ms)
+        if rc != HHT_OK:
+            raise HhtError(rc, "hht_autotune")
+        times = [float(v) for v in ms]
+        if cache:
+            table[key] = {"shape": int(best.value), "pass_ms": times}
+            tmp = cache + f".tmp{os.getpid()}"
+            with open(tmp, "w") as f:
+                json.dump(table, f, indent=1)
+            os.replace(tmp, cache)
+        return int(best.value), times
 
     # ------------------------------------------------------------ kernel timing
     def profile(self, on: bool = True) -> None:

@@ -260,3 +260,35 @@ def test_range_error_in_a_batch_leaves_other_images_intact(ctx, hht):
     for k in (0, 2):
         assert res[k].status == hht.HHT_OK
         _same(res[k], oracle.detect(imgs[k].points, 128, 128, 7, 20))
+
+
+@pytest.mark.parametrize("shape", range(6))
+def test_every_tile_shape_gives_the_same_result(hht, shape):
+    """The autotuner may pick any compiled tile shape of the level kernel;
+    every shape must give the oracle's result."""
+    c = hht.Context(device=0)
+    c.set_tuning(shape)
+    imgs = [synth.plain_128(index=shape), synth.plain_1024(index=shape % 2),
+            synth.random_small(60000 + shape, max_side=300, max_n=3000, max_depth=9, max_T=8)]
+    for im in imgs:
+        _same(c.detect(im.points, im.W, im.H, im.depth, im.T), oracle.detect(im.points, im.W, im.H, im.depth, im.T))
+    res = c.detect_batch([(im.points, im.W, im.H, im.depth, im.T) for im in imgs])
+    for im, r in zip(imgs, res):
+        _same(r, oracle.detect(im.points, im.W, im.H, im.depth, im.T))
+    c.close()
+
+
+def test_autotune_picks_a_shape_and_caches_it(hht, tmp_path):
+    imgs = [synth.batch_image(k) for k in (0, 1, 2)]
+    batch = [(im.points, im.W, im.H, im.depth, im.T) for im in imgs]
+    cache = str(tmp_path / "tune.json")
+    c = hht.Context(device=0)
+    best, times = c.autotune(batch, cache=cache)
+    assert 0 <= best < hht.TUNE_SHAPES and len(times) == hht.TUNE_SHAPES and all(t > 0 for t in times)
+    assert times[best] == min(times)
+    again, t2 = c.autotune(batch, cache=cache)
+    assert again == best and t2 is None  # served from the cache
+    got = c.detect_batch(batch)
+    for im, r in zip(imgs, got):
+        _props(r, im.T, im.depth)
+    c.close()
