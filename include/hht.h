@@ -183,6 +183,8 @@ typedef struct {
     double select_ms;
     double stage_ms;
     double sort_ms;             /* leaf output fix-up */
+    uint64_t persistent_launches;   /* batches run as one persistent launch (its time counts as pass_ms) */
+    uint64_t persistent_fallbacks;  /* persistent launches that ran out of room and were rerun level by level */
 } hht_profile_counters;
 
 int hht_profile_enable(hht_ctx *ctx, int on);
@@ -233,6 +235,20 @@ int hht_detect_noalloc(const hht_point *points, int64_t n, int32_t W, int32_t H,
 #define HHT_TUNE_SHAPES 6
 int hht_autotune(hht_ctx *ctx, const hht_image *images, int32_t count, int32_t *best, double *ms_per_shape);
 int hht_set_tuning(hht_ctx *ctx, int32_t shape);
+
+/*
+ * Batch execution form.  HHT_BATCH_LEVELS (default): one selection and one
+ * level-kernel launch per level, buffers sized exactly between levels.
+ * HHT_BATCH_PERSISTENT: a job that this context has already run level by
+ * level (same images, sizes, depths and thresholds) runs as one persistent
+ * cooperative kernel launch for the whole level loop, with buffers sized from
+ * that earlier run; if the data needs more room, the launch reports it and the
+ * job is rerun level by level.  Results are the same in both forms.
+ * Errors: HHT_E_ARG.
+ */
+#define HHT_BATCH_LEVELS 0
+#define HHT_BATCH_PERSISTENT 1
+int hht_set_batch_mode(hht_ctx *ctx, int32_t mode);
 
 /* Short description of an HHT_* code (static string). */
 const char *hht_strerror(int code);

@@ -167,6 +167,7 @@ int check_image(const hht_image& im) {
 }
 
 constexpr int kSelTile = 1024;   // parents per select tile
+constexpr int kPersistentRetry = 1;  // run_wave: persistent capacities too small, run again level by level
 constexpr int kPassTile = 256 * 8;  // voters per pass block below which fewer blocks are launched
 
 #define CK(call)                                   \
@@ -248,6 +249,34 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
     std::vector<Region> roots(n_units);
     for (int u = 0; u < n_units; ++u) roots[u] = Region{(uint32_t)u, 0u, 0u, (uint32_t)units[u].n};
 
+    // job signature for the persistent form's size plan
+    uint64_t sig = 1469598103934665603ull;
+    auto mix = [&](uint64_t v) { sig = (sig ^ v) * 1099511628211ull; };
+    mix((uint64_t)count);
+    for (int g = 0; g < count; ++g) {
+        mix((uint64_t)im[g].n);
+        mix(((uint64_t)im[g].W << 32) | (uint64_t)im[g].H);
+        mix(((uint64_t)im[g].depth << 32) | (uint64_t)im[g].T);
+    }
+    const int occ_p = i64 ? c->occ_persistent64 : c->occ_persistent32;
+    const bool persistent = c->batch_mode == 1 && c->plan.valid && c->plan.sig == sig && occ_p > 0;
+    uint64_t cap_rec = 0, cap_vox = 0, cap_tiles = 0;
+    if (persistent) {
+        cap_rec = std::max<uint64_t>(c->plan.cap_rec, (uint64_t)n_units);
+        cap_vox = std::max<uint64_t>(c->plan.cap_vox, v0_len);
+        cap_tiles = (cap_rec + kSelTile - 1) / kSelTile + 1;
+        for (int k = 0; k < 2; ++k) {
+            RK(ensure(c, c->rec[k], cap_rec * sizeof(Region)));
+            RK(ensure(c, c->preg[k], cap_rec * sizeof(PassRegion)));
+            RK(ensure(c, c->cnt[k], cap_rec * 4 * sizeof(uint32_t)));
+            RK(ensure(c, c->vox[k], std::max<uint64_t>(cap_vox, 1) * sizeof(Voter)));
+        }
+        RK(ensure(c, c->cursors, cap_rec * sizeof(unsigned long long)));
+        RK(ensure_keep(c, c->leaves, (c->job_leaves + c->plan.cap_leaves + 1) * sizeof(DevLeaf),
+                       c->job_leaves * sizeof(DevLeaf)));
+        if (cap_tiles * 4 > c->sel_flags.bytes) RK(ensure(c, c->sel_flags, cap_tiles * 4, true));
+        RK(ensure(c, c->sel_data, cap_tiles * 2 * 3 * sizeof(uint64_t)));
+    }
     RK(ensure(c, c->rec[0], n_units * sizeof(Region)));
     RK(ensure(c, c->cnt[0], n_units * 4 * sizeof(uint32_t)));
     RK(ensure(c, c->vox[0], std::max<uint64_t>(v0_len, 1) * sizeof(Voter)));
@@ -268,7 +297,61 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
     DeviceStatus* d_status = (DeviceStatus*)c->status.p;
     ScanState* d_scan = (ScanState*)c->scan_states.p;
 
-    {
+    uint64_t leaf_total = wave_leaf_base;
+    uint32_t err = 0;
+    bool fixed_up = false;
+    if (persistent) {
+        PersistentArgs f{};
+        f.base.units = (const Unit*)c->units.p;
+        f.base.cursor = (unsigned long long*)c->cursors.p;
+        f.base.leaves = (DevLeaf*)c->leaves.p;
+        f.base.stats = (uint64_t*)c->stats.p;
+        f.base.leaf_total = (uint64_t*)c->leaf_total.p;
+        f.base.scan = d_scan + 0;
+        f.base.tile_flags = (uint32_t*)c->sel_flags.p;
+        f.base.tile_data = (uint64_t*)c->sel_data.p;
+        f.base.status = d_status;
+        f.base.cap_children = cap_rec;
+        f.base.cap_voters = cap_vox;
+        f.base.cap_leaves = c->leaves.bytes / sizeof(DevLeaf);
+        f.base.cap_tiles = cap_tiles;
+        f.base.num_sms = c->num_sms;
+        for (int k = 0; k < 2; ++k) {
+            f.rec[k] = (Region*)c->rec[k].p;
+            f.preg[k] = (PassRegion*)c->preg[k].p;
+            f.cnt[k] = (uint32_t*)c->cnt[k].p;
+            f.vox[k] = (Voter*)c->vox[k].p;
+        }
+        f.infos = d_infos;
+        f.pts = (const int16_t*)c->pts.p;
+        f.total_pts = total;
+        f.img_start = (const uint64_t*)c->img_start.p;
+        f.img_unit = (const uint32_t*)c->img_unit.p;
+        f.img_err = (uint32_t*)c->img_err.p;
+        f.n_images = count;
+        f.Dmax = Dmax;
+        {
+            ProfScope ps(c, 2);
+            if (launch_persistent(f, i64, c->num_sms * occ_p, st) != 0) return HHT_E_CUDA;
+        }
+        c->prof.launches += 1;
+        CK(cudaMemcpyAsync(&leaf_total, c->leaf_total.p, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(c->h_infos.data(), d_infos, (Dmax + 1) * sizeof(LevelInfo), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        fixed_up = true;
+        c->persistent_runs += 1;
+        c->prof.persistent_launches += 1;
+        // algorithmic bytes of the level passes inside the launch (as if launched one by one)
+        for (int s = 1; s < Dmax; ++s) {
+            const uint64_t nin = c->h_infos[s - 1].n_voters, nout = c->h_infos[s].n_voters;
+            if (nin == 0) continue;
+            c->prof.pass_launches += 1;
+            c->prof.voters_read += nin;
+            c->prof.voters_written += nout;
+            c->prof.pass_bytes += 8 * (nin + nout);
+        }
+    }
+    if (!persistent) {
         ProfScope ps(c, 0);
         if (launch_stage((const int16_t*)c->pts.p, total, (const Unit*)c->units.p, count,
                          (const uint64_t*)c->img_start.p, (const uint32_t*)c->img_unit.p, (Voter*)c->vox[0].p,
@@ -278,10 +361,9 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
         if (total > 0) c->prof.launches += 1;
     }
 
-    // ---- level loop
-    uint64_t leaf_total = wave_leaf_base;
-    uint32_t err = 0;
-    for (int s = 1; s <= Dmax; ++s) {
+    // ---- level loop (sizes recorded as the plan of the persistent form)
+    uint64_t plan_rec = (uint64_t)n_units, plan_vox = v0_len;
+    for (int s = 1; s <= Dmax && !persistent; ++s) {
         const int pi = (s - 1) & 1, ci = s & 1;
         const uint64_t P = c->h_infos[s - 1].n_regions;
         if (P == 0) break;
@@ -342,6 +424,8 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
                     (unsigned long long)c->h_infos[s].n_leaves, c->held / 1e9);
         if (err) break;
         leaf_total += c->h_infos[s].n_leaves;
+        plan_rec = std::max<uint64_t>(plan_rec, c->h_infos[s].n_regions);
+        plan_vox = std::max<uint64_t>(plan_vox, c->h_infos[s].n_voters);
         if (s == Dmax) break;
 
         const uint64_t nin = c->h_infos[s - 1].n_voters;
@@ -376,9 +460,25 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
     CK(cudaMemcpyAsync(&hs, d_status, sizeof hs, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     err |= hs.err;
+    if (persistent && (err & kErrOverflow)) {
+        // the plan's capacities were too small for this data: level by level instead
+        c->plan.valid = false;
+        c->persistent_fallbacks += 1;
+        c->prof.persistent_fallbacks += 1;
+        return kPersistentRetry;
+    }
     if (err & kErrTimeout) return HHT_E_TIMEOUT;
     if (err & kErrOverflow) return HHT_E_NOMEM;
     if (err & kErrInvariant) return HHT_E_CUDA;
+    if (!persistent) {
+        // capacities for the persistent form of the same job, with a margin
+        c->plan.sig = sig;
+        c->plan.cap_rec = plan_rec + plan_rec / 8 + 64;
+        c->plan.cap_vox = plan_vox + plan_vox / 8 + 64;
+        const uint64_t wl = leaf_total - wave_leaf_base;
+        c->plan.cap_leaves = wl + wl / 8 + 64;
+        c->plan.valid = true;
+    }
 
     // Leaves need no sort: a step emits the leaves of the units whose depth it
     // reaches, in record order, and records stay in depth-first order (children
@@ -387,7 +487,7 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
     // depth-first traversal, and blocks follow (depth, unit).  Only the unit
     // field is rewritten to the half.
     const uint64_t wave_leaves = leaf_total - wave_leaf_base;
-    if (wave_leaves > 0) {
+    if (wave_leaves > 0 && !fixed_up) {
         ProfScope ps(c, 3);
         if (launch_unit_to_half((DevLeaf*)c->leaves.p + wave_leaf_base, wave_leaves, st) != 0) return HHT_E_CUDA;
         c->prof.launches += 1;
@@ -481,6 +581,10 @@ int run_waves(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int 
                     budget / 1e9);
         const uint64_t leaves_before = c->job_leaves;
         int rc = run_wave(c, im + first, last - first, outs + first, job_first + first);
+        if (rc == kPersistentRetry) {
+            c->job_leaves = leaves_before;
+            rc = run_wave(c, im + first, last - first, outs + first, job_first + first);
+        }
         if (rc == HHT_E_NOMEM && last - first > 1) {
             // remember that this much did not fit, split the wave and retry each half
             c->wave_cap = acc / 2 > 0 ? acc / 2 : 1;
@@ -534,6 +638,9 @@ int hht_create(hht_ctx** out, int device, void* cuda_stream, uint64_t mem_budget
     c->occ_pass32 = occupancy_pass(false);
     c->occ_pass64 = occupancy_pass(true);
     for (int k = 0; k < kPassShapeCount; ++k) c->occ_shape[k] = occupancy_pass(false, k);
+    c->occ_persistent32 = occupancy_persistent(false);
+    c->occ_persistent64 = occupancy_persistent(true);
+    if (const char* e = getenv("HHT_BATCH_MODE")) c->batch_mode = atoi(e) == 1 ? 1 : 0;
     if (const char* e = getenv("HHT_PASS_SHAPE")) {
         const int k = atoi(e);
         if (k >= 0 && k < kPassShapeCount) c->pass_shape = k;
@@ -607,6 +714,13 @@ int hht_fetch_leaves(hht_ctx* c, int32_t index, hht_leaf* leaves, uint64_t capac
     CK(cudaMemcpyAsync(leaves, (const char*)c->leaves.p + c->job_off[index] * sizeof(DevLeaf), n * sizeof(hht_leaf),
                        cudaMemcpyDefault, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    return HHT_OK;
+}
+
+int hht_set_batch_mode(hht_ctx* c, int32_t mode) {
+    if (!c || (mode != HHT_BATCH_LEVELS && mode != HHT_BATCH_PERSISTENT)) return HHT_E_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->batch_mode = mode;
     return HHT_OK;
 }
 

@@ -37,6 +37,15 @@ struct hht_ctx {
     int num_sms = 0;
     int occ_select = 1, occ_pass32 = 1, occ_pass64 = 1;
     int pass_shape = 0;                                   // pass-kernel tile shape (autotuned)
+    int batch_mode = 0;                                   // 0: level by level; 1: persistent when planned
+    int occ_persistent32 = 0, occ_persistent64 = 0;
+    // sizes seen by the last level-by-level run of a wave, for the persistent form
+    struct Plan {
+        uint64_t sig = 0;
+        uint64_t cap_rec = 0, cap_vox = 0, cap_leaves = 0;
+        bool valid = false;
+    } plan;
+    uint64_t persistent_runs = 0, persistent_fallbacks = 0;
     int occ_shape[hht::kPassShapeCount] = {1, 1, 1, 1, 1, 1};  // resident blocks per SM of each shape
 
     // job buffers

@@ -142,7 +142,26 @@ struct LevelArgs {
     int32_t num_sms;
 };
 
+// Arguments of the persistent (one cooperative launch) form of a batch.
+struct PersistentArgs {
+    LevelArgs base;  // fields common to every level (units, stats, status, scan, cursor, leaves, capacities)
+    Region* rec[2];
+    PassRegion* preg[2];
+    uint32_t* cnt[2];
+    Voter* vox[2];
+    LevelInfo* infos;  // [Dmax + 1]
+    const int16_t* pts;
+    uint64_t total_pts;
+    const uint64_t* img_start;
+    const uint32_t* img_unit;
+    uint32_t* img_err;
+    int32_t n_images;
+    int32_t Dmax;
+};
+
 // Kernel launchers (hht_kernels.cu).  All are asynchronous on `stream`.
+int launch_persistent(const PersistentArgs& f, bool int64_path, int grid, void* stream);
+int occupancy_persistent(bool int64_path);
 // Level 0 of the images [0, n_images) of `pts` (image g owns points
 // [img_start[g], img_start[g+1]) and the units img_unit[g], img_unit[g] + 1).
 int launch_stage(const int16_t* pts, uint64_t total_points, const Unit* units, int n_images,

@@ -14,6 +14,7 @@
 //           counts) into the level-s stream, and grandchild votes are counted
 //           for the next selection.  The copy is skipped where the next level
 //           is the unit's last one, so the largest list is never written.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -59,12 +60,12 @@ __device__ __forceinline__ bool run_head(uint32_t key) {
 
 // ============================================================================ stage
 template <typename I>
-__global__ void __launch_bounds__(256) stage_kernel(const int16_t* __restrict__ pts, uint64_t total,
-                                                    const Unit* __restrict__ units, int n_images,
-                                                    const uint64_t* __restrict__ img_start,
-                                                    const uint32_t* __restrict__ img_unit, Voter* __restrict__ v0,
-                                                    uint32_t* __restrict__ root_cnt, uint64_t* __restrict__ stats,
-                                                    uint32_t* __restrict__ img_err, DeviceStatus* status) {
+__device__ __forceinline__ void stage_body(const int16_t* __restrict__ pts, uint64_t total,
+                                           const Unit* __restrict__ units, int n_images,
+                                           const uint64_t* __restrict__ img_start,
+                                           const uint32_t* __restrict__ img_unit, Voter* __restrict__ v0,
+                                           uint32_t* __restrict__ root_cnt, uint64_t* __restrict__ stats,
+                                           uint32_t* __restrict__ img_err, DeviceStatus* status) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t kb = (uint64_t)blockIdx.x * blockDim.x; kb < total; kb += stride) {
         const uint64_t k = kb + threadIdx.x;
@@ -141,6 +142,16 @@ __global__ void __launch_bounds__(256) stage_kernel(const int16_t* __restrict__ 
     }
 }
 
+template <typename I>
+__global__ void __launch_bounds__(256) stage_kernel(const int16_t* __restrict__ pts, uint64_t total,
+                                                    const Unit* __restrict__ units, int n_images,
+                                                    const uint64_t* __restrict__ img_start,
+                                                    const uint32_t* __restrict__ img_unit, Voter* __restrict__ v0,
+                                                    uint32_t* __restrict__ root_cnt, uint64_t* __restrict__ stats,
+                                                    uint32_t* __restrict__ img_err, DeviceStatus* status) {
+    stage_body<I>(pts, total, units, n_images, img_start, img_unit, v0, root_cnt, stats, img_err, status);
+}
+
 // ============================================================================ select
 namespace {
 constexpr int kSelTPB = 256;
@@ -148,7 +159,22 @@ constexpr int kSelPPT = 4;
 constexpr int kSelTile = kSelTPB * kSelPPT;
 }  // namespace
 
-__global__ void __launch_bounds__(kSelTPB) select_kernel(LevelArgs a) {
+// Level totals once every block is done: leaf count, capacity checks.
+__device__ __forceinline__ void select_totals(const LevelArgs& a) {
+    volatile LevelInfo* info = a.info;
+    volatile uint64_t* lt = a.leaf_total;
+    const uint64_t q0 = info->n_voters;
+    const uint64_t nl = info->n_leaves;
+    const uint64_t total_leaves = *lt + nl;
+    if (info->n_regions > a.cap_children || q0 > a.cap_voters || total_leaves > a.cap_leaves)
+        atomicOr(&a.status->err, kErrOverflow);
+    *lt = total_leaves;
+    __threadfence();
+}
+
+// standalone: the last block to finish writes the totals; otherwise the
+// caller does after a grid-wide barrier.
+__device__ __forceinline__ void select_body(const LevelArgs& a, bool standalone) {
     __shared__ uint32_t s_slot;
     __shared__ uint32_t s_wrec[8], s_wleaf[8], s_wvox[8];
     __shared__ uint64_t s_prefix[3];
@@ -325,17 +351,10 @@ __global__ void __launch_bounds__(kSelTPB) select_kernel(LevelArgs a) {
         if (s_nleaf) atomicAdd((unsigned long long*)&a.info->n_leaves, s_nleaf);
         if (s_nvox) atomicAdd((unsigned long long*)&a.info->n_voters, s_nvox);
     }
-    if (scan_finish(a.scan)) {
-        volatile LevelInfo* info = a.info;
-        const uint64_t q0 = info->n_voters;
-        const uint64_t nl = info->n_leaves;
-        const uint64_t total_leaves = leaf_base + nl;
-        if (info->n_regions > a.cap_children || q0 > a.cap_voters || total_leaves > a.cap_leaves)
-            atomicOr(&a.status->err, kErrOverflow);
-        *a.leaf_total = total_leaves;
-        __threadfence();
-    }
+    if (standalone && scan_finish(a.scan)) select_totals(a);
 }
+
+__global__ void __launch_bounds__(kSelTPB) select_kernel(LevelArgs a) { select_body(a, true); }
 
 // ============================================================================ pass
 namespace {
@@ -462,8 +481,8 @@ __device__ __forceinline__ Classified<I> classify(const ParentGeo<I>& g, uint32_
 // Tile shape (autotuned): STEPS warp steps of 32 voters per chunk (one
 // cursor reservation per child and chunk), TPB threads per block, at least
 // MINB resident blocks per SM (register budget).
-template <typename I, int STEPS, int TPB, int MINB>
-__global__ void __launch_bounds__(TPB, MINB) pass_kernel(LevelArgs a) {
+template <typename I, int STEPS, int TPB>
+__device__ __forceinline__ void pass_body(const LevelArgs& a) {
     constexpr int kChunkSteps = STEPS;
     constexpr int kPassTPB = TPB;
     const int lane = threadIdx.x & 31;
@@ -664,10 +683,60 @@ __global__ void __launch_bounds__(TPB, MINB) pass_kernel(LevelArgs a) {
     settle();
 }
 
+template <typename I, int STEPS, int TPB, int MINB>
+__global__ void __launch_bounds__(TPB, MINB) pass_kernel(LevelArgs a) {
+    pass_body<I, STEPS, TPB>(a);
+}
+
 // ============================================================================ output fix-up
-__global__ void unit_to_half_kernel(DevLeaf* __restrict__ l, uint64_t n) {
+__device__ __forceinline__ void unit_to_half_body(DevLeaf* __restrict__ l, uint64_t n) {
     for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (uint64_t)gridDim.x * blockDim.x)
         l[k].unit &= 1u;
+}
+
+__global__ void unit_to_half_kernel(DevLeaf* __restrict__ l, uint64_t n) { unit_to_half_body(l, n); }
+
+// ============================================================================ persistent form
+// The whole level loop of a batch in one cooperative launch: level 0, then
+// for every level the selection and the pass, separated by grid-wide
+// barriers, then the output fix-up.  Buffers have fixed capacities (from an
+// earlier run of the same job); a capacity overflow is flagged, every later
+// phase is skipped and the host runs the job level by level instead.
+template <typename I>
+__global__ void __launch_bounds__(256, 3) persistent_kernel(PersistentArgs f) {
+    namespace cg = cooperative_groups;
+    cg::grid_group grid = cg::this_grid();
+    stage_body<I>(f.pts, f.total_pts, f.base.units, f.n_images, f.img_start, f.img_unit, f.vox[0], f.cnt[0],
+                  f.base.stats, f.img_err, f.base.status);
+    grid.sync();
+    for (int s = 1; s <= f.Dmax; ++s) {
+        const int pi = (s - 1) & 1, ci = s & 1;
+        LevelArgs a = f.base;
+        a.parents = f.rec[pi];
+        a.pregions = f.preg[pi];
+        a.parent_cnt = f.cnt[pi];
+        a.children = f.rec[ci];
+        a.child_cnt = f.cnt[ci];
+        a.vin = f.vox[pi];
+        a.vout = f.vox[ci];
+        a.info_prev = f.infos + (s - 1);
+        a.info = f.infos + s;
+        a.level = s;
+        select_body(a, false);
+        grid.sync();
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            select_totals(a);
+            // the scan state for the next selection
+            a.scan->tile_counter = 0;
+            a.scan->done_counter = 0;
+            a.scan->epoch = a.scan->epoch + 1u;
+            __threadfence();
+        }
+        grid.sync();
+        if (s < f.Dmax) pass_body<I, 4, 256>(a);
+        grid.sync();
+    }
+    unit_to_half_body(f.base.leaves, *reinterpret_cast<volatile uint64_t*>(f.base.leaf_total));
 }
 
 int launch_unit_to_half(void* leaves, uint64_t n, void* stream) {
@@ -739,6 +808,23 @@ const void* pass_fn(bool int64_path, int shape) {
     }
 }
 }  // namespace
+
+int occupancy_persistent(bool int64_path) {
+    int per_sm = 0;
+    if (int64_path)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel<int64_t>, 256, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel<int32_t>, 256, 0);
+    return per_sm;
+}
+
+int launch_persistent(const PersistentArgs& f, bool int64_path, int grid, void* stream) {
+    void* args[] = {(void*)&f};
+    const void* fn = int64_path ? (const void*)persistent_kernel<int64_t> : (const void*)persistent_kernel<int32_t>;
+    const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(256), args, 0, (cudaStream_t)stream);
+    if (e != cudaSuccess) cudaGetLastError();
+    return e == cudaSuccess ? 0 : -1;
+}
 
 int pass_threads(bool int64_path, int shape) {
     return int64_path ? 256 : kPassShapes[(shape >= 0 && shape < kPassShapeCount) ? shape : 0].tpb;

@@ -31,7 +31,8 @@ HHT_E_UNKNOWN_TICKET = -8
 # every function the C header declares
 EXPORTS = ("hht_create", "hht_destroy", "hht_detect", "hht_detect_batch", "hht_fetch_leaves", "hht_submit",
            "hht_poll", "hht_progress", "hht_profile_enable", "hht_profile_read", "hht_strerror", "hht_version",
-           "hht_detect_noalloc", "hht_autotune", "hht_set_tuning")
+           "hht_detect_noalloc", "hht_autotune", "hht_set_tuning", "hht_set_batch_mode")
+BATCH_LEVELS, BATCH_PERSISTENT = 0, 1
 TUNE_SHAPES = 6
 
 
@@ -51,7 +52,8 @@ class _Profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_uint64), ("pass_launches", ctypes.c_uint64),
                 ("select_launches", ctypes.c_uint64), ("voters_read", ctypes.c_uint64),
                 ("voters_written", ctypes.c_uint64), ("pass_bytes", ctypes.c_uint64), ("pass_ms", ctypes.c_double),
-                ("select_ms", ctypes.c_double), ("stage_ms", ctypes.c_double), ("sort_ms", ctypes.c_double)]
+                ("select_ms", ctypes.c_double), ("stage_ms", ctypes.c_double), ("sort_ms", ctypes.c_double),
+                ("persistent_launches", ctypes.c_uint64), ("persistent_fallbacks", ctypes.c_uint64)]
 
 
 class _Image(ctypes.Structure):
@@ -94,6 +96,8 @@ def load(path: str = LIB_PATH):
     lib.hht_profile_read.restype = ctypes.c_int
     lib.hht_autotune.argtypes = [vp, ctypes.POINTER(_Image), i32, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)]
     lib.hht_autotune.restype = ctypes.c_int
+    lib.hht_set_batch_mode.argtypes = [vp, i32]
+    lib.hht_set_batch_mode.restype = ctypes.c_int
     lib.hht_set_tuning.argtypes = [vp, i32]
     lib.hht_set_tuning.restype = ctypes.c_int
     lib.hht_strerror.argtypes = [ctypes.c_int]
@@ -261,6 +265,13 @@ class Context:
         if rc != HHT_OK and raise_on_error:
             raise HhtError(rc, "hht_detect_batch")
         return res
+
+    def set_batch_mode(self, mode: int) -> None:
+        """BATCH_LEVELS (one launch per level) or BATCH_PERSISTENT (one
+        cooperative launch per batch once the batch has been run once)."""
+        rc = load().hht_set_batch_mode(self._h, int(mode))
+        if rc != HHT_OK:
+            raise HhtError(rc, "hht_set_batch_mode")
 
     # ------------------------------------------------------------ autotuning
     def set_tuning(self, shape: int) -> None:

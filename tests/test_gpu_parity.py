@@ -292,3 +292,39 @@ def test_autotune_picks_a_shape_and_caches_it(hht, tmp_path):
     for im, r in zip(imgs, got):
         _props(r, im.T, im.depth)
     c.close()
+
+
+def test_persistent_form_matches_and_falls_back(hht):
+    """Batch mode PERSISTENT: the first run of a job goes level by level and
+    records its sizes; the same job then runs as one cooperative launch; a job
+    with the same signature but more voters overflows the recorded room and is
+    rerun level by level.  Every result equals the oracle's."""
+    c = hht.Context(device=0)
+    c.set_batch_mode(hht.BATCH_PERSISTENT)
+    imgs = [synth.plain_128(index=k) for k in range(3)] + [synth.batch_image(0), synth.plain_1024()]
+    batch = [(im.points, im.W, im.H, im.depth, im.T) for im in imgs]
+    want = [oracle.detect(im.points, im.W, im.H, im.depth, im.T) for im in imgs]
+    c.profile(True)
+    for _ in range(3):
+        got = c.detect_batch(batch)
+        for r, w in zip(got, want):
+            _same(r, w)
+    p = c.profile_read()
+    assert p["persistent_launches"] == 2 and p["persistent_fallbacks"] == 0
+    # same signature (n, W, H, depth, T), more voters: n identical points are
+    # one line (n * 2^l voters at level l); a fan of lines through one point
+    # crosses about 1.25 * 2^l cells each, beyond the plan's margin
+    n = imgs[0].n
+    line = np.stack([np.arange(n) % 128, np.full(n, 64)], axis=1).astype(np.int16)
+    sparse = np.zeros((n, 2), np.int16)
+    c2 = hht.Context(device=0)
+    c2.set_batch_mode(hht.BATCH_PERSISTENT)
+    c2.profile(True)
+    r1 = c2.detect_batch([(sparse, 128, 128, 7, 3)])[0]
+    r2 = c2.detect_batch([(line, 128, 128, 7, 3)])[0]
+    _same(r1, oracle.detect(sparse, 128, 128, 7, 3))
+    _same(r2, oracle.detect(line, 128, 128, 7, 3))
+    p2 = c2.profile_read()
+    assert p2["persistent_launches"] == 1 and p2["persistent_fallbacks"] == 1
+    c.close()
+    c2.close()
