@@ -181,6 +181,46 @@ constexpr int kPassTile = 256 * 8;  // voters per pass block below which fewer b
         if (r_ != HHT_OK) return r_; \
     } while (0)
 
+// The persistent launch, through a CUDA graph captured once per argument set
+// (replayed while the buffers and sizes are unchanged).  Capture is not
+// possible on the legacy default stream or inside another capture; then the
+// kernel is launched directly.
+int launch_persistent_graph(hht_ctx* c, const PersistentArgs& f, bool i64, int grid) {
+    cudaStream_t st = c->stream;
+    const unsigned char* fb = reinterpret_cast<const unsigned char*>(&f);
+    std::vector<unsigned char> key(fb, fb + sizeof f);
+    key.push_back(i64 ? 1 : 0);
+    if (c->graph_exec && c->graph_grid == grid && key == c->graph_args) {
+        CK(cudaGraphLaunch(c->graph_exec, st));
+        return HHT_OK;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const bool can_capture = st != nullptr && !c->graph_capture_failed &&
+                             cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
+    if (can_capture) {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        bool ok = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            const int lr = launch_persistent(f, i64, grid, st);
+            ok = cudaStreamEndCapture(st, &g) == cudaSuccess && lr == 0 && g != nullptr;
+        }
+        if (ok) ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+        if (ok) {
+            if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+            c->graph_exec = ge;
+            c->graph_args = key;
+            c->graph_grid = grid;
+            CK(cudaGraphLaunch(c->graph_exec, st));
+            return HHT_OK;
+        }
+        cudaGetLastError();
+        c->graph_capture_failed = true;  // launch directly from now on
+    }
+    return launch_persistent(f, i64, grid, st) == 0 ? HHT_OK : HHT_E_CUDA;
+}
+
 // Run one wave of images through the level loop; fills outs[k] for k in
 // [0, count).  Returns HHT_OK or a job-level error (per-image errors are in
 // outs[k].status).
@@ -332,7 +372,7 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
         f.Dmax = Dmax;
         {
             ProfScope ps(c, 2);
-            if (launch_persistent(f, i64, c->num_sms * occ_p, st) != 0) return HHT_E_CUDA;
+            RK(launch_persistent_graph(c, f, i64, c->num_sms * occ_p));
         }
         c->prof.launches += 1;
         CK(cudaMemcpyAsync(&leaf_total, c->leaf_total.p, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
@@ -668,6 +708,7 @@ void hht_destroy(hht_ctx* c) {
     hht::serve_destroy(c->serve);
     resolve_profile(c);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     DevBuf* all[] = {&c->pts,       &c->img_start,  &c->img_unit, &c->units,        &c->stats,     &c->infos,      &c->status,
                      &c->leaf_total, &c->img_err,   &c->scan_states,  &c->rec[0],    &c->rec[1],     &c->preg[0],
                      &c->preg[1],   &c->cnt[0],     &c->cnt[1],       &c->vox[0],    &c->vox[1],     &c->leaves,

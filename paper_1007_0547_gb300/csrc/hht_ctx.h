@@ -46,6 +46,11 @@ struct hht_ctx {
         bool valid = false;
     } plan;
     uint64_t persistent_runs = 0, persistent_fallbacks = 0;
+    // CUDA graph of the persistent launch, replayed while its arguments are unchanged
+    cudaGraphExec_t graph_exec = nullptr;
+    std::vector<unsigned char> graph_args;
+    int graph_grid = 0;
+    bool graph_capture_failed = false;
     int occ_shape[hht::kPassShapeCount] = {1, 1, 1, 1, 1, 1};  // resident blocks per SM of each shape
 
     // job buffers

@@ -328,3 +328,22 @@ def test_persistent_form_matches_and_falls_back(hht):
     assert p2["persistent_launches"] == 1 and p2["persistent_fallbacks"] == 1
     c.close()
     c2.close()
+
+
+def test_persistent_form_replays_a_cuda_graph_on_a_stream(hht):
+    """On a non-default stream the persistent launch is captured into a CUDA
+    graph once and replayed; results stay equal to the oracle's."""
+    import torch
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        c = hht.Context(device=0, stream=s)
+        c.set_batch_mode(hht.BATCH_PERSISTENT)
+        imgs = [synth.plain_128(index=k) for k in range(2)] + [synth.batch_image(1)]
+        batch = [(torch.from_numpy(im.points).cuda(), im.W, im.H, im.depth, im.T) for im in imgs]
+        want = [oracle.detect(im.points, im.W, im.H, im.depth, im.T) for im in imgs]
+        for _ in range(4):
+            got = c.detect_batch(batch)
+            s.synchronize()
+            for r, w in zip(got, want):
+                _same(r, w)
+        c.close()
