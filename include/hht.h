@@ -151,6 +151,18 @@ int hht_detect_batch(hht_ctx *ctx, const hht_image *images, int32_t count, hht_r
 int hht_fetch_leaves(hht_ctx *ctx, int32_t index, hht_leaf *leaves, uint64_t capacity);
 
 /*
+ * Copy all leaves of the last job (every image of the last hht_detect_batch)
+ * with one copy: `leaves` receives *total entries (host or device memory,
+ * `capacity` entries), and image k's leaves are leaves[offsets[k] ..
+ * offsets[k] + counts[k]) (offsets and counts: one entry per image of the
+ * job, may be NULL).  Images that failed have count 0.  With capacity < total
+ * nothing is copied and HHT_E_CAPACITY is returned with *total set.
+ * Errors: HHT_E_ARG, HHT_E_CAPACITY, HHT_E_CUDA.
+ */
+int hht_fetch_all_leaves(hht_ctx *ctx, hht_leaf *leaves, uint64_t capacity, uint64_t *offsets, uint64_t *counts,
+                         uint64_t *total);
+
+/*
  * Serving interface.  hht_submit() queues one request and returns at once;
  * the image is copied (host points) or referenced (device points; they must
  * stay valid until the request is done).  Requests are admitted to the GPU as

@@ -758,6 +758,24 @@ int hht_fetch_leaves(hht_ctx* c, int32_t index, hht_leaf* leaves, uint64_t capac
     return HHT_OK;
 }
 
+int hht_fetch_all_leaves(hht_ctx* c, hht_leaf* leaves, uint64_t capacity, uint64_t* offsets, uint64_t* counts,
+                         uint64_t* total) {
+    if (!c || !total) return HHT_E_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    *total = c->job_leaves;
+    if (capacity < c->job_leaves) return HHT_E_CAPACITY;
+    if (c->job_leaves > 0 && !leaves) return HHT_E_ARG;
+    for (size_t k = 0; k < c->job_n.size(); ++k) {
+        if (offsets) offsets[k] = c->job_off[k];
+        if (counts) counts[k] = c->job_n[k];
+    }
+    if (c->job_leaves == 0) return HHT_OK;
+    cudaSetDevice(c->device);
+    CK(cudaMemcpyAsync(leaves, c->leaves.p, c->job_leaves * sizeof(hht_leaf), cudaMemcpyDefault, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return HHT_OK;
+}
+
 int hht_set_batch_mode(hht_ctx* c, int32_t mode) {
     if (!c || (mode != HHT_BATCH_LEVELS && mode != HHT_BATCH_PERSISTENT)) return HHT_E_ARG;
     std::lock_guard<std::mutex> lk(c->mu);

@@ -485,6 +485,7 @@ template <typename I, int STEPS, int TPB>
 __device__ __forceinline__ void pass_body(const LevelArgs& a) {
     constexpr int kChunkSteps = STEPS;
     constexpr int kPassTPB = TPB;
+    static_assert(32 * STEPS <= 255, "a chunk's per-quadrant counts are summed in byte fields");
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
     const uint64_t nin = a.info_prev->n_voters;
@@ -564,28 +565,42 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
             steps += kChunkSteps;
             if (steps >= 255 - kChunkSteps) settle();  // byte counters nearly full
             // reserve each kept child's slots for the whole chunk (one atomic
-            // per child), then write in step and lane order
+            // per child): per-lane counts per quadrant as byte fields, one warp
+            // scan for all four quadrants, then every lane writes its kept
+            // voters of a quadrant to consecutive slots
+            uint32_t k4[kChunkSteps];
+            uint32_t cnt = 0;
+#pragma unroll
+            for (int k = 0; k < kChunkSteps; ++k) {
+                k4[k] = ((kw[k] >> quad_bit(0)) & 1u) | (((kw[k] >> quad_bit(1)) & 1u) << 1) |
+                        (((kw[k] >> quad_bit(2)) & 1u) << 2) | (((kw[k] >> quad_bit(3)) & 1u) << 3);
+                cnt += spread4(k4[k]);
+            }
+            uint32_t inc = cnt;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t o = __shfl_up_sync(0xffffffffu, inc, off);
+                if (lane >= off) inc += o;
+            }
+            const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
             unsigned long long base[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                uint32_t tot = 0;
-#pragma unroll
-                for (int k = 0; k < kChunkSteps; ++k) tot += __popc(__ballot_sync(0xffffffffu, (kw[k] >> quad_bit(q)) & 1u));
+                const uint32_t tq = (tot >> (8 * q)) & 0xffu;
                 base[q] = 0;
-                if (tot && lane == 0) base[q] = atomicAdd(&a.cursor[ci[q]], (unsigned long long)tot);
+                if (tq && lane == 0) base[q] = atomicAdd(&a.cursor[ci[q]], (unsigned long long)tq);
             }
+            const uint32_t excl = inc - cnt;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                unsigned long long p = __shfl_sync(0xffffffffu, base[q], 0);
+                if (!((tot >> (8 * q)) & 0xffu)) continue;
+                uint64_t p = __shfl_sync(0xffffffffu, base[q], 0) + ((excl >> (8 * q)) & 0xffu);
 #pragma unroll
                 for (int k = 0; k < kChunkSteps; ++k) {
-                    const bool keep = (kw[k] >> quad_bit(q)) & 1u;
-                    const uint32_t bq = __ballot_sync(0xffffffffu, keep);
-                    if (keep) {
-                        const uint64_t at = p + __popc(bq & lt);
-                        if (at < a.cap_voters) vout[at] = make_uint2(rec[k].x, ci[q]);
+                    if ((k4[k] >> q) & 1u) {
+                        if (p < a.cap_voters) vout[p] = make_uint2(rec[k].x, ci[q]);
+                        ++p;
                     }
-                    p += __popc(bq);
                 }
             }
             continue;
@@ -787,7 +802,7 @@ int launch_select(const LevelArgs& a, int tpb_unused, int grid, void* stream) {
 struct PassShape {
     int steps, tpb, minb;
 };
-constexpr PassShape kPassShapes[kPassShapeCount] = {{4, 256, 4}, {2, 256, 4}, {8, 256, 3},
+constexpr PassShape kPassShapes[kPassShapeCount] = {{4, 256, 4}, {2, 256, 4}, {2, 512, 2},
                                                     {4, 128, 8}, {4, 256, 3}, {4, 512, 2}};
 
 namespace {

@@ -31,7 +31,7 @@ HHT_E_UNKNOWN_TICKET = -8
 # every function the C header declares
 EXPORTS = ("hht_create", "hht_destroy", "hht_detect", "hht_detect_batch", "hht_fetch_leaves", "hht_submit",
            "hht_poll", "hht_progress", "hht_profile_enable", "hht_profile_read", "hht_strerror", "hht_version",
-           "hht_detect_noalloc", "hht_autotune", "hht_set_tuning", "hht_set_batch_mode")
+           "hht_detect_noalloc", "hht_autotune", "hht_set_tuning", "hht_set_batch_mode", "hht_fetch_all_leaves")
 BATCH_LEVELS, BATCH_PERSISTENT = 0, 1
 TUNE_SHAPES = 6
 
@@ -82,6 +82,8 @@ def load(path: str = LIB_PATH):
     lib.hht_detect.restype = ctypes.c_int
     lib.hht_detect_batch.argtypes = [vp, ctypes.POINTER(_Image), i32, ctypes.POINTER(_Result)]
     lib.hht_detect_batch.restype = ctypes.c_int
+    lib.hht_fetch_all_leaves.argtypes = [vp, vp, u64, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u64)]
+    lib.hht_fetch_all_leaves.restype = ctypes.c_int
     lib.hht_fetch_leaves.argtypes = [vp, i32, vp, u64]
     lib.hht_fetch_leaves.restype = ctypes.c_int
     lib.hht_submit.argtypes = [vp, ctypes.POINTER(_Image), ctypes.POINTER(u64)]
@@ -241,20 +243,25 @@ class Context:
             arr[k].points = p.ptr
             arr[k].n = p.n
             arr[k].W, arr[k].H, arr[k].depth, arr[k].T = (int(v) for v in im[1:5])
-        # no leaves are copied by the batch call itself: every image's leaves
-        # are fetched afterwards into a buffer of exactly the right size
+        # no leaves are copied by the batch call itself: all leaves of the job
+        # are fetched afterwards with one copy, and each image gets a view
         outs = (_Result * len(images))()
         rc = lib.hht_detect_batch(self._h, arr, len(images), outs)
-        bufs = []
         for k in range(len(images)):
             if outs[k].status == HHT_E_CAPACITY:
                 outs[k].status = HHT_OK
-                if rc == HHT_E_CAPACITY:
-                    rc = HHT_OK
-            bufs.append(self._fetch(k, int(outs[k].n_leaves), leaves_on_device) if outs[k].status == HHT_OK
-                        else self._alloc_leaves(0, leaves_on_device)[0])
         if rc == HHT_E_CAPACITY:
             rc = HHT_OK
+        total = ctypes.c_uint64()
+        nimg = len(images)
+        offs = (ctypes.c_uint64 * nimg)()
+        cnts = (ctypes.c_uint64 * nimg)()
+        lib.hht_fetch_all_leaves(self._h, None, 0, offs, cnts, ctypes.byref(total))
+        allbuf, ptr = self._alloc_leaves(int(total.value), leaves_on_device)
+        frc = lib.hht_fetch_all_leaves(self._h, ptr, int(total.value), offs, cnts, ctypes.byref(total))
+        if frc != HHT_OK:
+            raise HhtError(frc, "hht_fetch_all_leaves")
+        bufs = [allbuf[int(offs[k]): int(offs[k]) + int(cnts[k])] for k in range(nimg)]
         res = []
         for k in range(len(images)):
             st = int(outs[k].status)

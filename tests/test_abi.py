@@ -28,7 +28,7 @@ def test_header_declares_the_api():
     assert set(_declared()) == {"hht_create", "hht_destroy", "hht_detect", "hht_detect_batch", "hht_fetch_leaves",
                                 "hht_submit", "hht_poll", "hht_progress", "hht_profile_enable", "hht_profile_read",
                                 "hht_strerror", "hht_version", "hht_detect_noalloc", "hht_autotune",
-                                "hht_set_tuning", "hht_set_batch_mode"}
+                                "hht_set_tuning", "hht_set_batch_mode", "hht_fetch_all_leaves"}
 
 
 def test_library_exports_every_declared_symbol(lib):
@@ -55,6 +55,7 @@ def test_host_only_calls(lib):
     assert lib.hht_fetch_leaves(None, 0, None, 0) == hht.HHT_E_ARG
     assert lib.hht_set_tuning(None, 0) == hht.HHT_E_ARG
     assert lib.hht_set_batch_mode(None, 1) == hht.HHT_E_ARG
+    assert lib.hht_fetch_all_leaves(None, None, 0, None, None, None) == hht.HHT_E_ARG
     assert lib.hht_autotune(None, None, 0, None, None) == hht.HHT_E_ARG
 
 
