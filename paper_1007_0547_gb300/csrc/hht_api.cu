@@ -864,7 +864,10 @@ const char* hht_strerror(int code) {
     }
 }
 
-const char* hht_version(void) { return "hht 0.1 (sm_103a, level-synchronous stage/select/pass)"; }
+const char* hht_version(void) {
+    return "hht 0.2 (sm_103a, level-synchronous stage/select/pass; pass tile shapes 4x256/3 2x256/4 3x256/4 4x128/6 "
+           "4x256/4 4x512/2)";
+}
 
 }  // extern "C"
 

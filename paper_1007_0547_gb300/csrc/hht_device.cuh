@@ -109,10 +109,13 @@ __device__ __forceinline__ uint32_t region_code3(uint32_t M) {
 // the cell whose SW vertex is p lands on the cell's NE vertex bit p + 6*sz:
 // the NE corner bit is M itself, NW is M << 5*sz, SW is M << 6*sz and SE is
 // M << sz.  A line votes for the cell when its code is neither 0000 nor 1111.
+// Every column of M is a prefix (the vertices below the line are the lowest
+// t of the column), so the code is 1111 exactly when both upper corners are
+// set and 0000 exactly when both lower corners are clear.
 template <int sz>
 __device__ __forceinline__ uint32_t code_votes(uint32_t M) {
     const uint32_t ne = M, nw = M * (1u << (5 * sz)), sw = M * (1u << (6 * sz)), se = M * (1u << sz);
-    return (ne | nw | sw | se) & ~(ne & nw & sw & se);
+    return (sw | se) & ~(nw & ne);
 }
 
 // Children (2 x 2 steps) of quadrant q = NE, NW, SW, SE have SW vertices
@@ -131,12 +134,20 @@ __device__ __forceinline__ uint32_t spread_quads(uint32_t q4) {
 // (one multiply; the four children's cells are disjoint, so nothing carries).
 __device__ __forceinline__ uint32_t grand_cells(uint32_t kids) { return (kids >> 6) * 0x63u; }
 
-// Low t bits set (0 <= t <= 31).
+// Bits pos .. pos + t - 1 set (0 <= pos, t and pos + t <= 32).
+template <int pos>
 __device__ __forceinline__ uint32_t prefix_bits(int t) {
     uint32_t r;
-    asm("bmsk.clamp.b32 %0, 0, %1;" : "=r"(r) : "r"(t));
+    asm("bmsk.clamp.b32 %0, %1, %2;" : "=r"(r) : "n"(pos), "r"(t));
     return r;
 }
+
+// The children's vote bits (quad_bit positions) of `kw` as byte counters:
+// ((kw >> 12) * 0x1041) moves bits 12, 14, 22, 24 to bits 0, 8, 16, 24 and
+// every other product lands off those bits without a carry into them.
+// Quadrant q counts in byte quad_byte(q).
+__device__ __forceinline__ uint32_t quad_counts(uint32_t kw) { return ((kw >> 12) * 0x1041u) & 0x01010101u; }
+__host__ __device__ __forceinline__ constexpr int quad_byte(int q) { return q == 0 ? 3 : q == 1 ? 1 : q == 2 ? 0 : 2; }
 
 // Grandchild cells (1 x 1 steps of the 5 x 5 grid, bits alpha*5 + beta with
 // alpha, beta < 4) that lie inside the children whose bit is set in `kids`.

@@ -89,7 +89,8 @@ struct LevelInfo {
     uint64_t n_regions;      // passed regions of this level (records)
     uint64_t n_voters;       // length of this level's voter stream
     uint64_t n_leaves;       // leaves emitted at this level
-    uint64_t pad[12];
+    unsigned long long pass_next;  // voters of this level's stream claimed by the pass reading it (starts at 0)
+    uint64_t pad[11];
 };
 
 // State of one single-pass (decoupled look-back) scan: tile ids are claimed in

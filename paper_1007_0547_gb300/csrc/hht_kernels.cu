@@ -455,20 +455,20 @@ __device__ __forceinline__ Classified<I> classify(const ParentGeo<I>& g, uint32_
     const I x = I(xy & 0xffffu), y = I(xy >> 16);
     const I u0 = g.W0 - x * g.A + (x + y) * g.Kc;
     const I d = x * g.dmul;
-    uint32_t M = 0;
+    int t[5];
 #pragma unroll
     for (int alpha = 0; alpha < 5; ++alpha) {
         const I w = u0 - I(alpha) * d;
-        int t;
         if constexpr (sizeof(I) == 4) {
-            t = __vimin_s32_relu((int)(w >> g.k), 5);
+            t[alpha] = __vimin_s32_relu((int)(w >> g.k), 5);
         } else {
             I tt = w >> g.k;
             tt = tt < I(0) ? I(0) : (tt > I(5) ? I(5) : tt);
-            t = (int)tt;
+            t[alpha] = (int)tt;
         }
-        M += prefix_bits(t) * (1u << (5 * alpha));
     }
+    const uint32_t M = prefix_bits<0>(t[0]) | prefix_bits<5>(t[1]) | prefix_bits<10>(t[2]) |
+                       prefix_bits<15>(t[3]) | prefix_bits<20>(t[4]);
     const uint32_t v2 = code_votes<2>(M);  // children: vote bits at quad_bit(q)
     const uint32_t v1 = code_votes<1>(M);  // grandchildren: vote bits at kGrandBase + 5*alpha + beta
     Classified<I> c;
@@ -477,6 +477,12 @@ __device__ __forceinline__ Classified<I> classify(const ParentGeo<I>& g, uint32_
     return c;
 }
 }  // namespace
+
+// Pass-kernel work distribution: grabs of about 1/kGrabShare of a warp's
+// even share of the stream, within [kMinGrab, kMaxGrab] records.
+constexpr uint32_t kGrabShare = 4;
+constexpr int kMinGrab = 1024;
+constexpr int kMaxGrab = 4096;
 
 // Tile shape (autotuned): STEPS warp steps of 32 voters per chunk (one
 // cursor reservation per child and chunk), TPB threads per block, at least
@@ -490,12 +496,30 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
     const uint32_t lt = (1u << lane) - 1u;
     const uint64_t nin = a.info_prev->n_voters;
     if (job_aborted(a.status)) return;
-    const uint64_t nwarps = (uint64_t)gridDim.x * (kPassTPB / 32);
-    const uint64_t wid = (uint64_t)blockIdx.x * (kPassTPB / 32) + (threadIdx.x >> 5);
-    const uint64_t per = (((nin + nwarps - 1) / nwarps) + 31) & ~uint64_t(31);
-    const uint64_t beg = wid * per;
-    const uint64_t end = beg + per < nin ? beg + per : nin;
-    if (beg >= end) return;
+    // Work distribution: the stream is cut into grabs of G consecutive
+    // records, G = a quarter of a warp's even share rounded to whole chunks
+    // and kept within [kMinGrab, kMaxGrab].  Warp w takes grab w first and
+    // then claims the next free grab from the level's counter (one atomic,
+    // issued a grab ahead of its use).  All warps thus sweep the stream
+    // together, which keeps the child segments being written (laid out in
+    // parent order) in a narrow window of L2, and warps that meet many short
+    // parents do not hold up the launch.
+    constexpr int kChunk = 32 * kChunkSteps;
+    static_assert(kMinGrab >= kChunk, "a grab holds whole chunks");
+    const uint32_t nwarps = gridDim.x * (kPassTPB / 32);
+    const uint32_t wid = blockIdx.x * (kPassTPB / 32) + (threadIdx.x >> 5);
+    uint32_t G;
+    {
+        const int lg = 32 - __clz(kGrabShare * nwarps - 1);  // kGrabShare * nwarps <= 2^lg
+        const uint64_t g = nin >> lg;
+        G = g < (uint64_t)kMinGrab ? (uint32_t)kMinGrab : (g > (uint64_t)kMaxGrab ? (uint32_t)kMaxGrab : (uint32_t)g);
+        G = G / kChunk * kChunk;
+    }
+    uint64_t c = (uint64_t)wid * G;  // start of this warp's first grab
+    if (c >= nin) return;
+    unsigned long long* const claim_ctr = &a.info_prev->pass_next;
+    uint64_t claim_at = 0;  // lane 0: start of the warp's claimed next grab
+    if (lane == 0) claim_at = (uint64_t)nwarps * G + atomicAdd(claim_ctr, (unsigned long long)G);
     const uint2* __restrict__ vin = reinterpret_cast<const uint2*>(a.vin);
     uint2* __restrict__ vout = reinterpret_cast<uint2*>(a.vout);
 
@@ -522,22 +546,30 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
         for (int q = 0; q < 4; ++q) ci[q] = child_index(cg.pr, q);
     };
 
+    // chunks are loaded one ahead through a lane pointer with constant
+    // offsets; `rem` counts the records of the loaded chunk's grab from the
+    // chunk on (at most G)
+    const uint2* pin = vin + c + lane;
+    int rem = (int)(c + G < nin ? G : nin - c);
     uint2 nxt[kChunkSteps];
 #pragma unroll
-    for (int k = 0; k < kChunkSteps; ++k) {
-        const uint64_t i = beg + 32 * k + lane;
-        nxt[k] = i < end ? vin[i] : make_uint2(0u, kNoRegion);
-    }
-    for (uint64_t c0 = beg; c0 < end; c0 += 32 * kChunkSteps) {
+    for (int k = 0; k < kChunkSteps; ++k) nxt[k] = 32 * k + lane < rem ? pin[32 * k] : make_uint2(0u, kNoRegion);
+    while (rem > 0) {
         uint2 rec[kChunkSteps];
 #pragma unroll
-        for (int k = 0; k < kChunkSteps; ++k) {
-            rec[k] = nxt[k];
-            const uint64_t i = c0 + 32 * (kChunkSteps + k) + lane;
-            nxt[k] = i < end ? vin[i] : make_uint2(0u, kNoRegion);
+        for (int k = 0; k < kChunkSteps; ++k) rec[k] = nxt[k];
+        const int nvalid = rem < kChunk ? rem : kChunk;
+        // the chunk after this one: the rest of this grab, else the claimed grab
+        rem -= kChunk;
+        pin += kChunk;
+        if (rem <= 0) {
+            c = __shfl_sync(0xffffffffu, claim_at, 0);
+            rem = c < nin ? (int)(c + G < nin ? G : nin - c) : 0;
+            pin = vin + c + lane;
+            if (lane == 0 && rem > 0) claim_at = (uint64_t)nwarps * G + atomicAdd(claim_ctr, (unsigned long long)G);
         }
-        const uint64_t left = end - c0;
-        const int nvalid = (int)(left < 32 * kChunkSteps ? left : 32 * kChunkSteps);
+#pragma unroll
+        for (int k = 0; k < kChunkSteps; ++k) nxt[k] = 32 * k + lane < rem ? pin[32 * k] : make_uint2(0u, kNoRegion);
         const uint32_t r_first = __shfl_sync(0xffffffffu, rec[0].y, 0);
         const int lk = (nvalid - 1) >> 5, ll = (nvalid - 1) & 31;
         uint32_t r_last = rec[0].y;
@@ -553,6 +585,7 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
                 start_run(r_first);
             }
             uint32_t kw[kChunkSteps];
+            uint32_t cnt = 0;
 #pragma unroll
             for (int k = 0; k < kChunkSteps; ++k) {
                 kw[k] = 0u;
@@ -561,21 +594,12 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
                     kw[k] = c.kw;
                     add_rows(rows, c.gv);
                 }
+                cnt += quad_counts(kw[k]);
             }
-            steps += kChunkSteps;
-            if (steps >= 255 - kChunkSteps) settle();  // byte counters nearly full
             // reserve each kept child's slots for the whole chunk (one atomic
             // per child): per-lane counts per quadrant as byte fields, one warp
             // scan for all four quadrants, then every lane writes its kept
             // voters of a quadrant to consecutive slots
-            uint32_t k4[kChunkSteps];
-            uint32_t cnt = 0;
-#pragma unroll
-            for (int k = 0; k < kChunkSteps; ++k) {
-                k4[k] = ((kw[k] >> quad_bit(0)) & 1u) | (((kw[k] >> quad_bit(1)) & 1u) << 1) |
-                        (((kw[k] >> quad_bit(2)) & 1u) << 2) | (((kw[k] >> quad_bit(3)) & 1u) << 3);
-                cnt += spread4(k4[k]);
-            }
             uint32_t inc = cnt;
 #pragma unroll
             for (int off = 1; off < 32; off <<= 1) {
@@ -586,20 +610,40 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
             unsigned long long base[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const uint32_t tq = (tot >> (8 * q)) & 0xffu;
+                const uint32_t tq = (tot >> (8 * quad_byte(q))) & 0xffu;
                 base[q] = 0;
                 if (tq && lane == 0) base[q] = atomicAdd(&a.cursor[ci[q]], (unsigned long long)tq);
             }
+            steps += kChunkSteps;
+            if (steps >= 255 - kChunkSteps) settle();  // byte counters nearly full
             const uint32_t excl = inc - cnt;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                if (!((tot >> (8 * q)) & 0xffu)) continue;
-                uint64_t p = __shfl_sync(0xffffffffu, base[q], 0) + ((excl >> (8 * q)) & 0xffu);
+                const int sh = 8 * quad_byte(q);
+                const uint32_t tq = (tot >> sh) & 0xffu;
+                if (!tq) continue;
+                const uint64_t b = __shfl_sync(0xffffffffu, base[q], 0);
+                const uint32_t off = (excl >> sh) & 0xffu;
+                const uint32_t bit = 1u << quad_bit(q);
+                if (b + tq <= a.cap_voters) {
+                    uint2* dst = vout + b + off;
+                    uint32_t j = 0;
 #pragma unroll
-                for (int k = 0; k < kChunkSteps; ++k) {
-                    if ((k4[k] >> q) & 1u) {
-                        if (p < a.cap_voters) vout[p] = make_uint2(rec[k].x, ci[q]);
-                        ++p;
+                    for (int k = 0; k < kChunkSteps; ++k) {
+                        if (kw[k] & bit) {
+                            dst[j] = make_uint2(rec[k].x, ci[q]);
+                            ++j;
+                        }
+                    }
+                } else {
+                    // the stream overflows its capacity (the host reruns with more room)
+                    uint64_t p = b + off;
+#pragma unroll
+                    for (int k = 0; k < kChunkSteps; ++k) {
+                        if (kw[k] & bit) {
+                            if (p < a.cap_voters) vout[p] = make_uint2(rec[k].x, ci[q]);
+                            ++p;
+                        }
                     }
                 }
             }
@@ -802,8 +846,8 @@ int launch_select(const LevelArgs& a, int tpb_unused, int grid, void* stream) {
 struct PassShape {
     int steps, tpb, minb;
 };
-constexpr PassShape kPassShapes[kPassShapeCount] = {{4, 256, 4}, {2, 256, 4}, {2, 512, 2},
-                                                    {4, 128, 8}, {4, 256, 3}, {4, 512, 2}};
+constexpr PassShape kPassShapes[kPassShapeCount] = {{4, 256, 3}, {2, 256, 4}, {3, 256, 4},
+                                                    {4, 128, 6}, {4, 256, 4}, {4, 512, 2}};
 
 namespace {
 template <int S>
@@ -812,7 +856,7 @@ const void* pass_fn32() {
     return (const void*)pass_kernel<int32_t, p.steps, p.tpb, p.minb>;
 }
 const void* pass_fn(bool int64_path, int shape) {
-    if (int64_path) return (const void*)pass_kernel<int64_t, 4, 256, 4>;
+    if (int64_path) return (const void*)pass_kernel<int64_t, 4, 256, 3>;
     switch (shape) {
         case 1: return pass_fn32<1>();
         case 2: return pass_fn32<2>();

@@ -296,7 +296,7 @@ class Context:
         import torch
         cache = cache or os.environ.get("HHT_TUNE_CACHE")
         n_total = sum(_Points(im[0]).n for im in images)
-        key = (f"{torch.cuda.get_device_name(self.device)}|images={len(images)}|"
+        key = (f"{torch.cuda.get_device_name(self.device)}|{load().hht_version().decode()}|images={len(images)}|"
                f"points~2^{int(math.log2(max(1, n_total)))}|depth<={max(int(im[3]) for im in images)}")
         table = {}
         if cache and os.path.exists(cache):
