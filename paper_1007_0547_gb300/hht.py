@@ -205,6 +205,23 @@ class Context:
         buf = np.empty((max(cap, 1), 4), dtype=np.int32)
         return buf, buf.ctypes.data
 
+    @staticmethod
+    def _out_buffer(out):
+        """A caller's leaf buffer: int32 [cap, 4] (numpy array or torch tensor,
+        host or device, contiguous) -> (buffer, address, capacity)."""
+        try:
+            import torch
+            if isinstance(out, torch.Tensor):
+                if out.dtype != torch.int32 or out.dim() != 2 or out.shape[1] != 4 or not out.is_contiguous():
+                    raise ValueError("leaves_out must be a contiguous int32 tensor of shape [capacity, 4]")
+                return out, out.data_ptr(), int(out.shape[0])
+        except ImportError:  # pragma: no cover
+            pass
+        if not (isinstance(out, np.ndarray) and out.dtype == np.int32 and out.ndim == 2 and out.shape[1] == 4
+                and out.flags.c_contiguous):
+            raise ValueError("leaves_out must be a C-contiguous int32 array of shape [capacity, 4]")
+        return out, out.ctypes.data, int(out.shape[0])
+
     def _fetch(self, index: int, n: int, on_device: bool):
         """Leaves of image `index` of the last job (no recomputation)."""
         buf, ptr = self._alloc_leaves(n, on_device)
@@ -214,16 +231,25 @@ class Context:
         return buf
 
     def detect(self, points, W: int, H: int, depth: int, T: int, leaves_on_device: bool = True,
-               leaf_capacity: Optional[int] = None, raise_on_error: bool = True) -> Result:
+               leaf_capacity: Optional[int] = None, raise_on_error: bool = True, leaves_out=None) -> Result:
+        """Detect one image.  The leaves land in a new buffer (on the device
+        unless leaves_on_device is False) or, with `leaves_out` (an int32
+        [capacity, 4] host or device buffer, e.g. pinned host memory reused
+        across calls), in that buffer: the result's leaves are then a view of it."""
         lib = load()
         p = _Points(points)
-        cap = int(leaf_capacity or self._cap_hint)
-        buf, ptr = self._alloc_leaves(cap, leaves_on_device)
+        if leaves_out is not None:
+            buf, ptr, cap = self._out_buffer(leaves_out)
+        else:
+            cap = int(leaf_capacity or self._cap_hint)
+            buf, ptr = self._alloc_leaves(cap, leaves_on_device)
         r = _Result()
         r.leaves = ptr
         r.leaf_capacity = cap
         rc = lib.hht_detect(self._h, p.ptr, p.n, int(W), int(H), int(depth), int(T), ctypes.byref(r))
         if rc == HHT_E_CAPACITY:
+            if leaves_out is not None:
+                raise ValueError(f"leaves_out holds {cap} leaves, the image has {int(r.n_leaves)}")
             # the leaves are kept by the context: copy them into a buffer of the right size
             self._cap_hint = max(self._cap_hint, int(r.n_leaves))
             buf = self._fetch(0, int(r.n_leaves), leaves_on_device)
@@ -234,8 +260,12 @@ class Context:
         return Result(buf[:k], _stats_of(r), int(r.depth), int(r.L), rc)
 
     def detect_batch(self, images: Sequence[Tuple], leaves_on_device: bool = True,
-                     raise_on_error: bool = True) -> List[Result]:
-        """images: sequence of (points, W, H, depth, T)."""
+                     raise_on_error: bool = True, leaves_out=None) -> List[Result]:
+        """images: sequence of (points, W, H, depth, T).  The leaves of all
+        images land in one new buffer (on the device unless leaves_on_device
+        is False) or in `leaves_out` (an int32 [capacity, 4] host or device
+        buffer, e.g. pinned host memory reused across calls); each result's
+        leaves are a view of that buffer."""
         lib = load()
         pts = [_Points(im[0]) for im in images]
         arr = (_Image * len(images))()
@@ -257,7 +287,12 @@ class Context:
         offs = (ctypes.c_uint64 * nimg)()
         cnts = (ctypes.c_uint64 * nimg)()
         lib.hht_fetch_all_leaves(self._h, None, 0, offs, cnts, ctypes.byref(total))
-        allbuf, ptr = self._alloc_leaves(int(total.value), leaves_on_device)
+        if leaves_out is not None:
+            allbuf, ptr, cap = self._out_buffer(leaves_out)
+            if cap < int(total.value):
+                raise ValueError(f"leaves_out holds {cap} leaves, the batch has {int(total.value)}")
+        else:
+            allbuf, ptr = self._alloc_leaves(int(total.value), leaves_on_device)
         frc = lib.hht_fetch_all_leaves(self._h, ptr, int(total.value), offs, cnts, ctypes.byref(total))
         if frc != HHT_OK:
             raise HhtError(frc, "hht_fetch_all_leaves")

@@ -75,3 +75,17 @@ def test_package_fails_loudly_without_library(tmp_path):
             hht.load(str(tmp_path / "missing.so"))
     finally:
         hht._lib = saved
+
+
+def test_caller_leaf_buffer_is_checked_before_any_call():
+    import numpy as np
+    import torch
+    from paper_1007_0547_gb300 import hht
+    buf, ptr, cap = hht.Context._out_buffer(np.zeros((7, 4), np.int32))
+    assert cap == 7 and ptr == buf.ctypes.data
+    t = torch.zeros((5, 4), dtype=torch.int32)
+    assert hht.Context._out_buffer(t)[2] == 5
+    for bad in (np.zeros((7, 4), np.int64), np.zeros((7, 3), np.int32), np.zeros((4, 7), np.int32).T,
+                torch.zeros((5, 4), dtype=torch.int64), torch.zeros(20, dtype=torch.int32)):
+        with pytest.raises(ValueError):
+            hht.Context._out_buffer(bad)

@@ -158,6 +158,35 @@ def test_host_and_device_inputs_and_outputs(ctx):
     _same(ctx.detect(dev, img.W, img.H, img.depth, img.T, leaves_on_device=False), want)
 
 
+def test_caller_leaf_buffers_pinned_and_device(ctx):
+    import torch
+    imgs = [synth.plain_128(index=k) for k in range(3)] + [synth.random_small(777, max_side=300, max_n=2000,
+                                                                              max_depth=8, max_T=10)]
+    want = [oracle.detect(im.points, im.W, im.H, im.depth, im.T) for im in imgs]
+    total = sum(len(w.leaves) for w in want)
+    batch = [(torch.from_numpy(im.points).pin_memory(), im.W, im.H, im.depth, im.T) for im in imgs]
+    for out in (torch.full((total + 5, 4), -1, dtype=torch.int32).pin_memory(),
+                torch.full((total, 4), -1, dtype=torch.int32, device="cuda"),
+                np.full((total + 1, 4), -1, np.int32)):
+        res = ctx.detect_batch(batch, leaves_out=out)
+        for r, w in zip(res, want):
+            _same(r, w)
+        host = out.cpu().numpy() if isinstance(out, torch.Tensor) else out
+        # the buffer holds every image's leaves (each result is a view at its
+        # image's offset) and nothing past them
+        got_rows = np.sort(host[:total].astype(np.uint32).view(np.dtype((np.void, 16))).ravel())
+        want_rows = np.sort(np.ascontiguousarray(np.concatenate([w.leaves for w in want])).view(
+            np.dtype((np.void, 16))).ravel())
+        assert np.array_equal(got_rows, want_rows)
+        assert (host[total:] == -1).all()
+        one = ctx.detect(*batch[0], leaves_out=out)
+        _same(one, want[0])
+    with pytest.raises(ValueError):
+        ctx.detect_batch(batch, leaves_out=np.zeros((total - 1, 4), np.int32))
+    with pytest.raises(ValueError):
+        ctx.detect(*batch[0], leaves_out=np.zeros((1, 4), np.int32))
+
+
 def test_capacity_two_call_protocol(ctx, hht):
     import ctypes
     img = synth.plain_128()
