@@ -30,7 +30,7 @@ enum Quad : int { NE = 0, NW = 1, SW = 2, SE = 3 };
 // One (image, half) of a job.  Units advance one level per step of the level
 // loop; a unit that joined at step t0 is at level (step - t0), so requests can
 // join a running loop (continuous batching) without changing the kernels.
-struct Unit {
+struct alignas(16) Unit {
     int32_t lL;        // log2 of the frame side L
     int32_t D;         // depth (leaf level)
     int32_t T;         // threshold: a region passes when votes >= T
@@ -48,14 +48,14 @@ static_assert(sizeof(Unit) == 64, "unit record is 64 bytes");
 
 // Voter record: the (half-swapped) point and the index of the region whose
 // voter list it belongs to.  Two records form one 16-byte vector load.
-struct Voter {
+struct alignas(8) Voter {
     int16_t x, y;
     uint32_t region;
 };
 static_assert(sizeof(Voter) == 8, "voter record is 8 bytes");
 
 // A region that passed (level-0 regions always do).
-struct Region {
+struct alignas(16) Region {
     uint32_t unit;
     uint32_t a, b;     // cell indices at the region's level
     uint32_t count;    // votes = length of its voter list
@@ -65,7 +65,7 @@ static_assert(sizeof(Region) == 16, "region record is 16 bytes");
 // Everything the pass kernel needs about a parent region, in one 16-byte
 // record written by the selection of the next level: the parent's cell, its
 // geometry and where its passed children are.
-struct PassRegion {
+struct alignas(16) PassRegion {
     uint32_t a, b;        // parent cell indices at its level
     uint32_t child_base;  // record index of its first passed child at the next level
     uint32_t packed;      // see pack_region()
@@ -80,7 +80,7 @@ __host__ __device__ inline uint32_t pack_region(uint32_t pass, uint32_t write, u
 }
 
 // Leaf as produced on the device (before sorting): unit, cell, votes.
-struct DevLeaf {
+struct alignas(16) DevLeaf {
     uint32_t unit, i, j, votes;
 };
 

@@ -311,12 +311,16 @@ __device__ __forceinline__ void select_body(const LevelArgs& a, bool standalone)
             const uint64_t p = base + j;
             if (p >= np) continue;
             const Region R = a.parents[p];
-            PassRegion pr;
-            pr.a = R.a;
-            pr.b = R.b;
-            pr.child_base = (uint32_t)rec;
-            pr.packed = geo[j] | (leafy[j] ? 0u : pass[j]) | (wmask[j] << 4);
-            a.pregions[p] = pr;
+            if (!leafy[j]) {
+                // the pass record (a parent whose children are leaves has no
+                // voters in the stream the pass reads, so it needs none)
+                PassRegion pr;
+                pr.a = R.a;
+                pr.b = R.b;
+                pr.child_base = (uint32_t)rec;
+                pr.packed = geo[j] | pass[j] | (wmask[j] << 4);
+                a.pregions[p] = pr;
+            }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 if (!(pass[j] & (1u << q))) continue;
@@ -336,8 +340,9 @@ __device__ __forceinline__ void select_body(const LevelArgs& a, bool standalone)
                         c.unit = R.unit; c.a = ca; c.b = cb; c.count = cnt[j][q];
                         a.children[rec] = c;
                         reinterpret_cast<uint4*>(a.child_cnt)[rec] = make_uint4(0, 0, 0, 0);
-                        // the child's voters fill [vox, vox + count) of the next stream
-                        a.cursor[rec] = vox;
+                        // the child's voters fill [vox, vox + count) of the next
+                        // stream (only a child whose list is written has a cursor)
+                        if (wmask[j] & (1u << q)) a.cursor[rec] = vox;
                     }
                     if (wmask[j] & (1u << q)) vox += cnt[j][q];
                     ++rec;
