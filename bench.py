@@ -374,7 +374,8 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e2e_s = float(t.item())
         e2e = {"value": tests_all * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_s / args.steps}
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_s / args.steps,
+               "ms_steps": [round(1e3 * t, 2) for t in ts]}
 
     if rank != 0:
         if world > 1:
@@ -428,8 +429,7 @@ def main():
                 "algorithmic_bytes_per_launch": per_launch,
                 "launches": prof["pass_launches"], "pass_ms_per_step": prof["pass_ms"] / args.steps,
                 "select_ms_per_step": prof["select_ms"] / args.steps,
-                "stage_ms_per_step": prof["stage_ms"] / args.steps,
-                "sort_ms_per_step": prof["sort_ms"] / args.steps}
+                "stage_ms_per_step": prof["stage_ms"] / args.steps}
 
     cpu = None
     if not args.no_cpu_baseline and world == 1:

@@ -194,7 +194,6 @@ typedef struct {
     double pass_ms;             /* summed device time of the pass launches */
     double select_ms;
     double stage_ms;
-    double sort_ms;             /* leaf output fix-up */
     uint64_t persistent_launches;   /* batches run as one persistent launch (its time counts as pass_ms) */
     uint64_t persistent_fallbacks;  /* persistent launches that ran out of room and were rerun level by level */
 } hht_profile_counters;

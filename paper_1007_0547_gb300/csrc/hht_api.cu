@@ -148,8 +148,7 @@ void resolve_profile(hht_ctx* c) {
         switch (p.kind) {
             case 0: c->prof.stage_ms += ms; break;
             case 1: c->prof.select_ms += ms; break;
-            case 2: c->prof.pass_ms += ms; break;
-            default: c->prof.sort_ms += ms; break;
+            default: c->prof.pass_ms += ms; break;
         }
         c->ev_pool.push_back(p.a);
         c->ev_pool.push_back(p.b);
@@ -339,7 +338,6 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
 
     uint64_t leaf_total = wave_leaf_base;
     uint32_t err = 0;
-    bool fixed_up = false;
     if (persistent) {
         PersistentArgs f{};
         f.base.units = (const Unit*)c->units.p;
@@ -378,7 +376,6 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
         CK(cudaMemcpyAsync(&leaf_total, c->leaf_total.p, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
         CK(cudaMemcpyAsync(c->h_infos.data(), d_infos, (Dmax + 1) * sizeof(LevelInfo), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        fixed_up = true;
         c->persistent_runs += 1;
         c->prof.persistent_launches += 1;
         // algorithmic bytes of the level passes inside the launch (as if launched one by one)
@@ -524,14 +521,8 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
     // reaches, in record order, and records stay in depth-first order (children
     // in quadrant order NE, NW, SW, SE under their parent, parents in order), so
     // every unit's leaves form one block in the order of the paper's
-    // depth-first traversal, and blocks follow (depth, unit).  Only the unit
-    // field is rewritten to the half.
-    const uint64_t wave_leaves = leaf_total - wave_leaf_base;
-    if (wave_leaves > 0 && !fixed_up) {
-        ProfScope ps(c, 3);
-        if (launch_unit_to_half((DevLeaf*)c->leaves.p + wave_leaf_base, wave_leaves, st) != 0) return HHT_E_CUDA;
-        c->prof.launches += 1;
-    }
+    // depth-first traversal, and blocks follow (depth, unit).  The selection
+    // writes each leaf's half directly, so the leaves are final as written.
     std::vector<uint64_t> img_leaves(count, 0), img_off(count, 0);
     for (int g = 0; g < count; ++g)
         for (int h = 0; h < 2; ++h)
@@ -865,7 +856,7 @@ const char* hht_strerror(int code) {
 }
 
 const char* hht_version(void) {
-    return "hht 0.2 (sm_103a, level-synchronous stage/select/pass; pass tile shapes 4x256/3 2x256/4 3x256/4 4x128/6 "
+    return "hht 0.3 (sm_103a, level-synchronous stage/select/pass; pass tile shapes 4x256/3 2x256/4 3x256/4 4x128/6 "
            "4x256/4 4x512/2)";
 }
 

@@ -77,7 +77,7 @@ struct hht_ctx {
     std::vector<cudaEvent_t> ev_pool;
     struct Pending {
         cudaEvent_t a, b;
-        int kind;  // 0 stage, 1 select, 2 pass, 3 output fix-up
+        int kind;  // 0 stage, 1 select, 2 pass
     };
     std::vector<Pending> pending;
 };

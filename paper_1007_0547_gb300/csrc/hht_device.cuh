@@ -148,6 +148,10 @@ __device__ __forceinline__ uint32_t prefix_bits(int t) {
 // Quadrant q counts in byte quad_byte(q).
 __device__ __forceinline__ uint32_t quad_counts(uint32_t kw) { return ((kw >> 12) * 0x1041u) & 0x01010101u; }
 __host__ __device__ __forceinline__ constexpr int quad_byte(int q) { return q == 0 ? 3 : q == 1 ? 1 : q == 2 ? 0 : 2; }
+// quad_byte for a quadrant known only at run time (a nibble table, no local array).
+__host__ __device__ __forceinline__ constexpr uint32_t quad_byte_rt(uint32_t q) { return (0x2013u >> (4 * q)) & 0xfu; }
+static_assert(quad_byte_rt(0) == 3 && quad_byte_rt(1) == 1 && quad_byte_rt(2) == 0 && quad_byte_rt(3) == 2,
+              "run-time quadrant byte table");
 
 // Grandchild cells (1 x 1 steps of the 5 x 5 grid, bits alpha*5 + beta with
 // alpha, beta < 4) that lie inside the children whose bit is set in `kids`.
@@ -158,6 +162,22 @@ __device__ __forceinline__ uint32_t grandchild_mask(uint32_t kids) {
     m |= (kids & (1u << SW)) ? 0x00063u : 0u;  // alpha, beta in {0, 1}
     m |= (kids & (1u << SE)) ? 0x18C00u : 0u;  // alpha in {2, 3}, beta in {0, 1}
     return m;
+}
+
+// An 8-byte store made only when `pred` is non-zero, as one predicated
+// instruction (a plain `if` around a store may become a branch).
+__device__ __forceinline__ void st_pred_v2(void* p, uint32_t pred, uint32_t x, uint32_t y) {
+    asm volatile("{ .reg .pred q; setp.ne.u32 q, %0, 0; @q st.global.v2.u32 [%1], {%2, %3}; }"
+                 :: "r"(pred), "l"(p), "r"(x), "r"(y));
+}
+
+// An 8-byte read-only load made only when `pred` is non-zero; otherwise the
+// result is `dflt`.  One predicated instruction, no branch.
+__device__ __forceinline__ uint2 ld_pred_v2(const void* p, uint32_t pred, uint2 dflt) {
+    uint32_t x = dflt.x, y = dflt.y;
+    asm("{ .reg .pred q; setp.ne.u32 q, %2, 0; @q ld.global.nc.v2.u32 {%0, %1}, [%3]; }"
+        : "+r"(x), "+r"(y) : "r"(pred), "l"(p));
+    return make_uint2(x, y);
 }
 
 // Spread 4 bits into the low bit of 4 bytes (bit b -> byte b).

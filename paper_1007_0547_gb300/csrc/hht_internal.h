@@ -79,9 +79,9 @@ __host__ __device__ inline uint32_t pack_region(uint32_t pass, uint32_t write, u
     return pass | (write << 4) | (sS << 8) | (lL << 13) | (D << 18);
 }
 
-// Leaf as produced on the device (before sorting): unit, cell, votes.
+// Leaf as produced on the device (the layout of hht_leaf): half, cell, votes.
 struct alignas(16) DevLeaf {
-    uint32_t unit, i, j, votes;
+    uint32_t half, i, j, votes;
 };
 
 // Per-level totals written by the selection kernel's last block.
@@ -177,7 +177,6 @@ int occupancy_select();
 int occupancy_pass(bool int64_path, int shape = 0);
 
 // Rewrite each leaf's unit (2 * image + half) to its half.
-int launch_unit_to_half(void* leaves, uint64_t n, void* stream);
 
 
 }  // namespace hht

@@ -330,7 +330,8 @@ __device__ __forceinline__ void select_body(const LevelArgs& a, bool standalone)
                 if (leafy[j]) {
                     if (leaf < a.cap_leaves) {
                         DevLeaf lf;
-                        lf.unit = R.unit; lf.i = ca; lf.j = cb; lf.votes = cnt[j][q];
+                        lf.half = R.unit & 1u;  // units are numbered 2 * image (or request slot) + half
+                        lf.i = ca; lf.j = cb; lf.votes = cnt[j][q];
                         a.leaves[leaf] = lf;
                     }
                     ++leaf;
@@ -593,12 +594,10 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
             uint32_t cnt = 0;
 #pragma unroll
             for (int k = 0; k < kChunkSteps; ++k) {
-                kw[k] = 0u;
-                if (rec[k].y != kNoRegion) {
-                    const Classified<I> c = classify(cg, rec[k].x);
-                    kw[k] = c.kw;
-                    add_rows(rows, c.gv);
-                }
+                const uint32_t live = rec[k].y != kNoRegion ? 0xffffffffu : 0u;
+                const Classified<I> c = classify(cg, rec[k].x);
+                kw[k] = c.kw & live;
+                add_rows(rows, c.gv & live);
                 cnt += quad_counts(kw[k]);
             }
             // reserve each kept child's slots for the whole chunk (one atomic
@@ -612,37 +611,46 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
                 if (lane >= off) inc += o;
             }
             const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
-            unsigned long long base[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const uint32_t tq = (tot >> (8 * quad_byte(q))) & 0xffu;
-                base[q] = 0;
-                if (tq && lane == 0) base[q] = atomicAdd(&a.cursor[ci[q]], (unsigned long long)tq);
+            // lanes 0..3 reserve the slots of quadrant `lane` in parallel
+            unsigned long long mybase = 0;
+            bool over = false;
+            if (lane < 4) {
+                const uint32_t tq = (tot >> (8 * quad_byte_rt(lane))) & 0xffu;
+                const uint32_t cq = lane == 0 ? ci[0] : lane == 1 ? ci[1] : lane == 2 ? ci[2] : ci[3];
+                if (tq) {
+                    mybase = atomicAdd(&a.cursor[cq], (unsigned long long)tq);
+                    over = mybase + tq > a.cap_voters;
+                }
             }
+            const bool any_over = __any_sync(0xffffffffu, over);
             steps += kChunkSteps;
             if (steps >= 255 - kChunkSteps) settle();  // byte counters nearly full
             const uint32_t excl = inc - cnt;
+            if (!any_over) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int sh = 8 * quad_byte(q);
-                const uint32_t tq = (tot >> sh) & 0xffu;
-                if (!tq) continue;
-                const uint64_t b = __shfl_sync(0xffffffffu, base[q], 0);
-                const uint32_t off = (excl >> sh) & 0xffu;
-                const uint32_t bit = 1u << quad_bit(q);
-                if (b + tq <= a.cap_voters) {
-                    uint2* dst = vout + b + off;
+                for (int q = 0; q < 4; ++q) {
+                    const int sh = 8 * quad_byte(q);
+                    const uint32_t tq = (tot >> sh) & 0xffu;
+                    if (!tq) continue;
+                    uint2* dst = vout + __shfl_sync(0xffffffffu, mybase, q) + ((excl >> sh) & 0xffu);
+                    const uint32_t bit = 1u << quad_bit(q);
                     uint32_t j = 0;
 #pragma unroll
                     for (int k = 0; k < kChunkSteps; ++k) {
-                        if (kw[k] & bit) {
-                            dst[j] = make_uint2(rec[k].x, ci[q]);
-                            ++j;
-                        }
+                        const uint32_t keep = (kw[k] & bit) ? 1u : 0u;
+                        st_pred_v2(dst + j, keep, rec[k].x, ci[q]);
+                        j += keep;
                     }
-                } else {
-                    // the stream overflows its capacity (the host reruns with more room)
-                    uint64_t p = b + off;
+                }
+            } else {
+                // the stream overflows its capacity (the host reruns with more room)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int sh = 8 * quad_byte(q);
+                    const uint32_t tq = (tot >> sh) & 0xffu;
+                    if (!tq) continue;
+                    uint64_t p = __shfl_sync(0xffffffffu, mybase, q) + ((excl >> sh) & 0xffu);
+                    const uint32_t bit = 1u << quad_bit(q);
 #pragma unroll
                     for (int k = 0; k < kChunkSteps; ++k) {
                         if (kw[k] & bit) {
@@ -687,10 +695,8 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
                     unsigned long long p = 0;
                     if (lane == 0) p = atomicAdd(&a.cursor[ci[q]], (unsigned long long)__popc(bq));
                     p = __shfl_sync(0xffffffffu, p, 0);
-                    if (keep) {
-                        const uint64_t at = p + __popc(bq & lt);
-                        if (at < a.cap_voters) vout[at] = make_uint2(rk.x, ci[q]);
-                    }
+                    const uint64_t at = p + __popc(bq & lt);
+                    st_pred_v2(vout + at, keep && at < a.cap_voters, rk.x, ci[q]);
                 }
                 continue;
             }
@@ -715,10 +721,8 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
                 unsigned long long p = 0;
                 if (keep && lane == leader) p = atomicAdd(&a.cursor[child_index(g.pr, q)], (unsigned long long)__popc(gm));
                 p = __shfl_sync(0xffffffffu, p, leader);
-                if (keep) {
-                    const uint64_t at = p + __popc(gm & lt);
-                    if (at < a.cap_voters) vout[at] = make_uint2(rk.x, child_index(g.pr, q));
-                }
+                const uint64_t at = p + __popc(gm & lt);
+                st_pred_v2(vout + at, keep && at < a.cap_voters, rk.x, child_index(g.pr, q));
             }
             // count every parent but the last lane's on its own; the last one
             // continues as the current run
@@ -752,18 +756,11 @@ __global__ void __launch_bounds__(TPB, MINB) pass_kernel(LevelArgs a) {
     pass_body<I, STEPS, TPB>(a);
 }
 
-// ============================================================================ output fix-up
-__device__ __forceinline__ void unit_to_half_body(DevLeaf* __restrict__ l, uint64_t n) {
-    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (uint64_t)gridDim.x * blockDim.x)
-        l[k].unit &= 1u;
-}
-
-__global__ void unit_to_half_kernel(DevLeaf* __restrict__ l, uint64_t n) { unit_to_half_body(l, n); }
 
 // ============================================================================ persistent form
 // The whole level loop of a batch in one cooperative launch: level 0, then
 // for every level the selection and the pass, separated by grid-wide
-// barriers, then the output fix-up.  Buffers have fixed capacities (from an
+// barriers.  Buffers have fixed capacities (from an
 // earlier run of the same job); a capacity overflow is flagged, every later
 // phase is skipped and the host runs the job level by level instead.
 template <typename I>
@@ -800,15 +797,8 @@ __global__ void __launch_bounds__(256, 3) persistent_kernel(PersistentArgs f) {
         if (s < f.Dmax) pass_body<I, 4, 256>(a);
         grid.sync();
     }
-    unit_to_half_body(f.base.leaves, *reinterpret_cast<volatile uint64_t*>(f.base.leaf_total));
 }
 
-int launch_unit_to_half(void* leaves, uint64_t n, void* stream) {
-    if (n == 0) return 0;
-    const uint64_t want = (n + 255) / 256;
-    unit_to_half_kernel<<<(int)(want < 2048 ? want : 2048), 256, 0, (cudaStream_t)stream>>>((DevLeaf*)leaves, n);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
-}
 
 // ============================================================================ launchers
 namespace {

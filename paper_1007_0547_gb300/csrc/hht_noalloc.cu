@@ -279,7 +279,6 @@ extern "C" int hht_detect_noalloc(const hht_point* points, int64_t n, int32_t W,
     if (nl != leaf_total) return out->status = HHT_E_CUDA;
     if (nl > leaf_capacity || (nl > 0 && !leaves)) return out->status = HHT_E_CAPACITY;
     if (nl > 0) {
-        if (launch_unit_to_half(d_leaves, nl, st) != 0) return HHT_E_CUDA;
         NA_CK(cudaMemcpyAsync(leaves, d_leaves, nl * sizeof(hht_leaf), cudaMemcpyDefault, st));
         NA_CK(cudaStreamSynchronize(st));
     }

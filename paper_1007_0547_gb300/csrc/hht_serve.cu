@@ -227,7 +227,6 @@ int engine_complete(hht_ctx* c, ServeState* S, uint64_t step_leaves) {
     }
     if (fin.empty()) return HHT_OK;
     if (step_leaves > 0) {
-        if (launch_unit_to_half(S->leaves.p, step_leaves, st) != 0) return HHT_E_CUDA;
         S->h_leaves.resize(step_leaves);
         SV_CK(cudaMemcpyAsync(S->h_leaves.data(), S->leaves.p, step_leaves * sizeof(hht_leaf), cudaMemcpyDeviceToHost, st));
     }

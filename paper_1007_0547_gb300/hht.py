@@ -52,7 +52,7 @@ class _Profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_uint64), ("pass_launches", ctypes.c_uint64),
                 ("select_launches", ctypes.c_uint64), ("voters_read", ctypes.c_uint64),
                 ("voters_written", ctypes.c_uint64), ("pass_bytes", ctypes.c_uint64), ("pass_ms", ctypes.c_double),
-                ("select_ms", ctypes.c_double), ("stage_ms", ctypes.c_double), ("sort_ms", ctypes.c_double),
+                ("select_ms", ctypes.c_double), ("stage_ms", ctypes.c_double),
                 ("persistent_launches", ctypes.c_uint64), ("persistent_fallbacks", ctypes.c_uint64)]
 
 
@@ -64,11 +64,13 @@ class _Image(ctypes.Structure):
 _lib = None
 
 
-def load(path: str = LIB_PATH):
-    """Load libhht.so; raises if it has not been built."""
+def load(path: Optional[str] = None):
+    """Load libhht.so (the in-tree build, or the file $HHT_LIB names); raises
+    if it is missing."""
     global _lib
     if _lib is not None:
         return _lib
+    path = path or os.environ.get("HHT_LIB") or LIB_PATH
     if not os.path.exists(path):
         raise ImportError(f"{path} is missing: build it with `python -m paper_1007_0547_gb300.build` "
                           "(needs nvcc); there is no CPU fallback")
@@ -139,6 +141,15 @@ class Result:
         return np.asarray(lv).astype(np.uint32).reshape(-1, 4)
 
 
+# numpy view of an array of _Result (fields at the ctypes offsets)
+_RESULT_DTYPE = np.dtype({
+    "names": [f for f, _ in _Result._fields_],
+    "formats": [np.uint64, np.uint64, np.uint64, np.int32, np.int32, np.int32, np.int32,
+                (np.uint64, (2 * (MAX_DEPTH + 1) * 4,))],
+    "offsets": [getattr(_Result, f).offset for f, _ in _Result._fields_],
+    "itemsize": ctypes.sizeof(_Result)})
+
+
 def _stats_of(r: _Result) -> np.ndarray:
     st = np.frombuffer(r.stats, dtype=np.uint64).reshape(2, MAX_DEPTH + 1, 4)
     return st[:, : r.depth + 1].copy()
@@ -152,7 +163,9 @@ class _Points:
         try:
             import torch
             if isinstance(points, torch.Tensor):
-                t = points.to(torch.int16).contiguous().reshape(-1, 2)
+                t = points
+                if t.dtype != torch.int16 or t.dim() != 2 or t.shape[1] != 2 or not t.is_contiguous():
+                    t = t.to(torch.int16).contiguous().reshape(-1, 2)
                 self.keep = t
                 self.ptr = t.data_ptr() if t.numel() else None
                 self.n = t.shape[0]
@@ -296,14 +309,22 @@ class Context:
         frc = lib.hht_fetch_all_leaves(self._h, ptr, int(total.value), offs, cnts, ctypes.byref(total))
         if frc != HHT_OK:
             raise HhtError(frc, "hht_fetch_all_leaves")
-        bufs = [allbuf[int(offs[k]): int(offs[k]) + int(cnts[k])] for k in range(nimg)]
+        # per-image views and statistics from one numpy view of the result array
+        o = np.frombuffer(offs, dtype=np.uint64).astype(np.int64)
+        rows = np.frombuffer(outs, dtype=_RESULT_DTYPE)
+        n_leaves = rows["n_leaves"].astype(np.int64)
+        status = rows["status"].astype(np.int64)
+        depth = rows["depth"].astype(np.int64)
+        Ls = rows["L"].astype(np.int64)
+        stats = rows["stats"].reshape(nimg, 2, MAX_DEPTH + 1, 4)
         res = []
-        for k in range(len(images)):
-            st = int(outs[k].status)
+        for k in range(nimg):
+            st = int(status[k])
             if st != HHT_OK and raise_on_error:
                 raise HhtError(st, f"hht_detect_batch[{k}]")
-            nk = int(outs[k].n_leaves) if st == HHT_OK else 0
-            res.append(Result(bufs[k][:nk], _stats_of(outs[k]), int(outs[k].depth), int(outs[k].L), st))
+            nk = int(n_leaves[k]) if st == HHT_OK else 0
+            dk = int(depth[k])
+            res.append(Result(allbuf[int(o[k]): int(o[k]) + nk], stats[k, :, : dk + 1].copy(), dk, int(Ls[k]), st))
         if rc != HHT_OK and raise_on_error:
             raise HhtError(rc, "hht_detect_batch")
         return res

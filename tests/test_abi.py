@@ -89,3 +89,32 @@ def test_caller_leaf_buffer_is_checked_before_any_call():
                 torch.zeros((5, 4), dtype=torch.int64), torch.zeros(20, dtype=torch.int32)):
         with pytest.raises(ValueError):
             hht.Context._out_buffer(bad)
+
+
+def test_binding_structs_match_the_header_as_compiled(tmp_path):
+    """Sizes and field offsets of the ctypes mirrors equal those a C compiler
+    gives the public header's structs."""
+    import shutil
+    import subprocess
+    from paper_1007_0547_gb300 import hht
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    mirrors = {"hht_result": hht._Result, "hht_image": hht._Image, "hht_profile_counters": hht._Profile}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hht.h"', 'int main(void) {']
+    for cname, py in mirrors.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in py._fields_:
+            lines.append(f'printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ['return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(root, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {(w[0], w[1]): int(w[2]) for w in (l.split() for l in out) if len(w) == 3}
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for field, _ in py._fields_:
+            assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
