@@ -584,8 +584,10 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
             if (k == lk) r_last = rec[k].y;
         r_last = __shfl_sync(0xffffffffu, r_last, ll);
 
-        if (r_first == r_last) {
-            // ---- the whole chunk belongs to one parent (the stream is grouped by parent)
+        if (r_first == r_last && r_first != kNoRegion) {
+            // ---- the whole chunk belongs to one parent (the stream is grouped by
+            // parent; a chunk that starts and ends with dead records goes step by
+            // step, where only live lanes look up their parent)
             if (r_first != cur) {
                 settle();
                 start_run(r_first);

@@ -292,6 +292,33 @@ def test_range_error_in_a_batch_leaves_other_images_intact(ctx, hht):
 
 
 @pytest.mark.parametrize("shape", range(6))
+def test_chunks_that_start_and_end_with_dead_records(hht, shape):
+    """Points outside their image leave dead records in the level-0 stream.
+    Laid out so that whole 128-record chunks are dead and one chunk starts and
+    ends with dead records around live ones (both halves, 1024 records each,
+    so chunk borders fall on multiples of 128): the image fails with a range
+    error and the image after it in the batch is exact."""
+    rng = np.random.default_rng(4242)
+    n = 1024
+    dead = np.zeros(n, bool)
+    for lo, hi in ((0, 260), (384, 390), (505, 512), (896, 1024)):
+        dead[lo:hi] = True
+    assert dead[384] and dead[511] and not dead[390:505].any()
+    pts = rng.integers(0, 128, size=(n, 2)).astype(np.int16)
+    pts[dead] = (300, 5)
+    good = synth.plain_128(index=0)
+    c = hht.Context(device=0)
+    try:
+        c.set_tuning(shape)
+        res = c.detect_batch([(pts, 128, 128, 7, 20), (good.points, 128, 128, 7, 20)], raise_on_error=False)
+        assert res[0].status == hht.HHT_E_RANGE
+        assert res[1].status == hht.HHT_OK
+        _same(res[1], oracle.detect(good.points, 128, 128, 7, 20))
+    finally:
+        c.close()
+
+
+@pytest.mark.parametrize("shape", range(6))
 def test_every_tile_shape_gives_the_same_result(hht, shape):
     """The autotuner may pick any compiled tile shape of the level kernel;
     every shape must give the oracle's result."""
