@@ -131,7 +131,7 @@ int hht_detect(hht_ctx *ctx, const hht_point *points, int64_t n, int32_t W, int3
 /*
  * Detect lines in `count` independent images in one batched pass: all images
  * and both halves of each advance level by level through the same kernel
- * launches (captured as one CUDA graph per level schedule).  outs[k] receives
+ * launches (see hht_set_batch_mode for the one-launch form).  outs[k] receives
  * image k's result exactly as hht_detect would produce it.  Returns HHT_OK
  * when every image succeeded, else the first failing image's code (each
  * outs[k].status holds that image's own code).
@@ -260,6 +260,23 @@ int hht_set_tuning(hht_ctx *ctx, int32_t shape);
 #define HHT_BATCH_LEVELS 0
 #define HHT_BATCH_PERSISTENT 1
 int hht_set_batch_mode(hht_ctx *ctx, int32_t mode);
+
+/*
+ * Host-side fault injection, for tests of the failure path (no paper
+ * counterpart).  HHT_FAULT_WITHHOLD_SCAN_TILE: in the next detection job
+ * (hht_detect or hht_detect_batch) of this context, tile `arg` of every
+ * selection launch's look-back scan (tiles of 1024 parent regions, in claim
+ * order) publishes nothing.  The tiles after it then wait on a flag that
+ * nothing sets; each wait gives up after its bounded spin (about a second or
+ * two), the job returns HHT_E_TIMEOUT, and the context stays usable for the
+ * next call.  A selection with at most `arg` + 1 tiles is unaffected.
+ * HHT_FAULT_NONE clears a pending injection.  No GPU fault, trap or endless
+ * wait is involved.  Errors: HHT_E_ARG (NULL context, unknown kind, arg
+ * outside [0, 2^32 - 1)).
+ */
+#define HHT_FAULT_NONE 0
+#define HHT_FAULT_WITHHOLD_SCAN_TILE 1
+int hht_inject_fault(hht_ctx *ctx, int32_t kind, int64_t arg);
 
 /* Short description of an HHT_* code (static string). */
 const char *hht_strerror(int code);

@@ -180,6 +180,30 @@ constexpr int kPassTile = 256 * 8;  // voters per pass block below which fewer b
         if (r_ != HHT_OK) return r_; \
     } while (0)
 
+// Copy `bytes` of leaves from device memory to a caller's buffer on the
+// context's stream.  A large copy into pinned host memory is written by the
+// SMs through the buffer's device mapping: on a GB300 they reach host memory
+// over NVLink-C2C at a steadier rate than a copy engine gave (whose device ->
+// host copies of a few GB ran at about 200 GB/s on some calls and at a tenth
+// of that on others).  $HHT_COPY_ENGINE=1 keeps every copy on the copy
+// engines.  Anything else (device memory, pageable host memory, unaligned or
+// small copies) goes through cudaMemcpyAsync.
+int copy_out(hht_ctx* c, void* dst, const void* src, size_t bytes) {
+    constexpr size_t kKernelMin = 1u << 20;
+    if (bytes >= kKernelMin && !c->copy_engine_only && ((uintptr_t)dst % 16) == 0 && ((uintptr_t)src % 16) == 0 &&
+        bytes % 16 == 0) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, dst) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer) {
+            if (launch_copy16(src, at.devicePointer, bytes / 16, c->num_sms * 4, c->stream) != 0) return HHT_E_CUDA;
+            c->prof.launches += 1;
+            return HHT_OK;
+        }
+        cudaGetLastError();
+    }
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream));
+    return HHT_OK;
+}
+
 // The persistent launch, through a CUDA graph captured once per argument set
 // (replayed while the buffers and sizes are unchanged).  Capture is not
 // possible on the legacy default stream or inside another capture; then the
@@ -354,6 +378,7 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
         f.base.cap_leaves = c->leaves.bytes / sizeof(DevLeaf);
         f.base.cap_tiles = cap_tiles;
         f.base.num_sms = c->num_sms;
+        f.base.withhold_tile_plus1 = c->inject_tile >= 0 ? (uint32_t)(c->inject_tile + 1) : 0u;
         for (int k = 0; k < 2; ++k) {
             f.rec[k] = (Region*)c->rec[k].p;
             f.preg[k] = (PassRegion*)c->preg[k].p;
@@ -439,6 +464,7 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
         a.tile_flags = (uint32_t*)c->sel_flags.p;
         a.tile_data = (uint64_t*)c->sel_data.p;
         a.cap_tiles = sel_tiles;
+        a.withhold_tile_plus1 = c->inject_tile >= 0 ? (uint32_t)(c->inject_tile + 1) : 0u;
         const int sel_grid = (int)std::min<uint64_t>(sel_tiles, (uint64_t)c->num_sms * c->occ_select);
         // select's capacity test on the voter stream is re-done below with the exact size
         a.cap_voters = UINT64_MAX;
@@ -567,8 +593,7 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
         } else {
             r.status = HHT_OK;
             if (nl > 0) {
-                CK(cudaMemcpyAsync(r.leaves, (const char*)c->leaves.p + off * sizeof(DevLeaf), nl * sizeof(hht_leaf),
-                                   cudaMemcpyDefault, st));
+                RK(copy_out(c, r.leaves, (const char*)c->leaves.p + off * sizeof(DevLeaf), nl * sizeof(hht_leaf)));
             }
         }
     }
@@ -640,7 +665,9 @@ int run_job(hht_ctx* c, const hht_image* im, int count, hht_result* outs) {
     c->job_off.assign(count, 0);
     c->job_n.assign(count, 0);
     c->job_leaves = 0;
-    return run_waves(c, im, count, outs, 0);
+    const int rc = run_waves(c, im, count, outs, 0);
+    c->inject_tile = -1;  // an injected fault lasts one job
+    return rc;
 }
 
 }  // namespace
@@ -672,6 +699,7 @@ int hht_create(hht_ctx** out, int device, void* cuda_stream, uint64_t mem_budget
     c->occ_persistent32 = occupancy_persistent(false);
     c->occ_persistent64 = occupancy_persistent(true);
     if (const char* e = getenv("HHT_BATCH_MODE")) c->batch_mode = atoi(e) == 1 ? 1 : 0;
+    c->copy_engine_only = getenv("HHT_COPY_ENGINE") && getenv("HHT_COPY_ENGINE")[0] == '1';
     if (const char* e = getenv("HHT_PASS_SHAPE")) {
         const int k = atoi(e);
         if (k >= 0 && k < kPassShapeCount) c->pass_shape = k;
@@ -743,8 +771,7 @@ int hht_fetch_leaves(hht_ctx* c, int32_t index, hht_leaf* leaves, uint64_t capac
     if (!leaves) return HHT_E_ARG;
     if (capacity < n) return HHT_E_CAPACITY;
     cudaSetDevice(c->device);
-    CK(cudaMemcpyAsync(leaves, (const char*)c->leaves.p + c->job_off[index] * sizeof(DevLeaf), n * sizeof(hht_leaf),
-                       cudaMemcpyDefault, c->stream));
+    RK(copy_out(c, leaves, (const char*)c->leaves.p + c->job_off[index] * sizeof(DevLeaf), n * sizeof(hht_leaf)));
     CK(cudaStreamSynchronize(c->stream));
     return HHT_OK;
 }
@@ -762,7 +789,7 @@ int hht_fetch_all_leaves(hht_ctx* c, hht_leaf* leaves, uint64_t capacity, uint64
     }
     if (c->job_leaves == 0) return HHT_OK;
     cudaSetDevice(c->device);
-    CK(cudaMemcpyAsync(leaves, c->leaves.p, c->job_leaves * sizeof(hht_leaf), cudaMemcpyDefault, c->stream));
+    RK(copy_out(c, leaves, c->leaves.p, c->job_leaves * sizeof(hht_leaf)));
     CK(cudaStreamSynchronize(c->stream));
     return HHT_OK;
 }
@@ -819,6 +846,22 @@ int hht_autotune(hht_ctx* c, const hht_image* images, int32_t count, int32_t* be
     if (rc != HHT_OK) return rc;
     *best = best_shape;
     return HHT_OK;
+}
+
+int hht_inject_fault(hht_ctx* c, int32_t kind, int64_t arg) {
+    if (!c) return HHT_E_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    switch (kind) {
+        case HHT_FAULT_NONE:
+            c->inject_tile = -1;
+            return HHT_OK;
+        case HHT_FAULT_WITHHOLD_SCAN_TILE:
+            if (arg < 0 || arg >= (int64_t)UINT32_MAX) return HHT_E_ARG;
+            c->inject_tile = arg;
+            return HHT_OK;
+        default:
+            return HHT_E_ARG;
+    }
 }
 
 int hht_profile_enable(hht_ctx* c, int on) {

@@ -30,6 +30,7 @@ struct hht_ctx {
     using DevBuf = hht::DevBuf;
     int device = 0;
     bool debug = false;          // HHT_DEBUG=1: wave and allocation trace on stderr
+    bool copy_engine_only = false;  // HHT_COPY_ENGINE=1: leaves to host memory by cudaMemcpyAsync only
     uint64_t wave_cap = 0;       // largest wave estimate known to fit (0 = none failed yet)
     cudaStream_t stream = nullptr;
     uint64_t budget = 0;
@@ -52,6 +53,7 @@ struct hht_ctx {
     int graph_grid = 0;
     bool graph_capture_failed = false;
     int occ_shape[hht::kPassShapeCount] = {1, 1, 1, 1, 1, 1};  // resident blocks per SM of each shape
+    int64_t inject_tile = -1;  // hht_inject_fault: selection tile withheld in the next job (-1 = none)
 
     // job buffers
     DevBuf pts, img_start, img_unit, units, stats, infos, status, leaf_total, img_err, scan_states;

@@ -206,9 +206,12 @@ __device__ __forceinline__ void publish_aggregate(uint32_t* flags, uint64_t* dat
     st_release_u32(&flags[t], (epoch << 2) | (t == 0 ? 2u : 1u));
 }
 
+// `publish` is false only for a tile withheld by host-side fault injection
+// (hht_inject_fault): it then publishes nothing, and the tiles after it wait
+// until their bounded wait expires.
 template <int C>
 __device__ void resolve_prefix(uint32_t* flags, uint64_t* data, uint32_t t, uint32_t epoch, const uint64_t (&agg)[C],
-                               uint64_t (&prefix)[C], DeviceStatus* status) {
+                               uint64_t (&prefix)[C], DeviceStatus* status, bool publish = true) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int c = 0; c < C; ++c) prefix[c] = 0;
@@ -250,7 +253,7 @@ __device__ void resolve_prefix(uint32_t* flags, uint64_t* data, uint32_t t, uint
         top -= 32;
     }
     if (timed_out && lane == 0) atomicOr(&status->err, kErrTimeout);
-    if (lane == 0) {
+    if (lane == 0 && publish) {
 #pragma unroll
         for (int c = 0; c < C; ++c) st_relaxed_u64(&data[(size_t)t * 2 * C + C + c], prefix[c] + agg[c]);
         st_release_u32(&flags[t], (epoch << 2) | 2u);
@@ -260,10 +263,11 @@ __device__ void resolve_prefix(uint32_t* flags, uint64_t* data, uint32_t t, uint
 // Both halves back to back (for kernels with nothing to overlap).
 template <int C>
 __device__ __forceinline__ void tile_lookback(uint32_t* flags, uint64_t* data, uint32_t t, uint32_t epoch,
-                                              const uint64_t (&agg)[C], uint64_t (&prefix)[C], DeviceStatus* status) {
-    if ((threadIdx.x & 31) == 0) publish_aggregate<C>(flags, data, t, epoch, agg);
+                                              const uint64_t (&agg)[C], uint64_t (&prefix)[C], DeviceStatus* status,
+                                              bool publish = true) {
+    if ((threadIdx.x & 31) == 0 && publish) publish_aggregate<C>(flags, data, t, epoch, agg);
     __syncwarp();
-    resolve_prefix<C>(flags, data, t, epoch, agg, prefix, status);
+    resolve_prefix<C>(flags, data, t, epoch, agg, prefix, status, publish);
 }
 
 // End-of-launch protocol for a scan: the last block to finish resets the tile

@@ -141,6 +141,7 @@ struct LevelArgs {
     uint64_t cap_children, cap_voters, cap_leaves, cap_tiles;
     int32_t level;             // step of the level loop
     int32_t num_sms;
+    uint32_t withhold_tile_plus1;  // fault injection: 1 + the selection tile that publishes nothing (0 = none)
 };
 
 // Arguments of the persistent (one cooperative launch) form of a batch.
@@ -169,6 +170,9 @@ int launch_stage(const int16_t* pts, uint64_t total_points, const Unit* units, i
                  const uint64_t* img_start, const uint32_t* img_unit, Voter* vstream, uint32_t* cnt,
                  uint64_t* stats, uint32_t* img_err, DeviceStatus* status, bool int64_path, void* stream);
 int launch_select(const LevelArgs& a, int threads_per_block, int grid, void* stream);
+// Copy n16 16-byte words from device memory to `dst` (device memory, or the
+// device mapping of pinned host memory).
+int launch_copy16(const void* src, void* dst, uint64_t n16, int grid, void* stream);
 // Pass-kernel tile shapes for the autotuner; shape 0 is the default.
 constexpr int kPassShapeCount = 6;
 int launch_pass(const LevelArgs& a, bool int64_path, int grid, void* stream, int shape = 0);

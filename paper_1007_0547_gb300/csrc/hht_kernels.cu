@@ -292,7 +292,7 @@ __device__ __forceinline__ void select_body(const LevelArgs& a, bool standalone)
             __syncwarp();
             if (lane < 8) { s_wrec[lane] = ir - wr; s_wleaf[lane] = il - wl; s_wvox[lane] = iv - wv; }
             uint64_t pre[3];
-            tile_lookback<3>(a.tile_flags, a.tile_data, t, epoch, agg, pre, a.status);
+            tile_lookback<3>(a.tile_flags, a.tile_data, t, epoch, agg, pre, a.status, t + 1u != a.withhold_tile_plus1);
             if (lane == 0) {
                 s_prefix[0] = pre[0];
                 s_prefix[1] = pre[1];
@@ -371,21 +371,26 @@ __device__ __forceinline__ uint32_t child_index(const PassRegion& pr, int q) {
     return pr.child_base + __popc(pr.packed & 0xfu & ((1u << q) - 1u));
 }
 
-// Add grandchild counts of one parent to the level-(s+1) counters of its
+// Add the grandchild counts of one parent to the level-(s+1) counters of its
 // passed children.  c16[2*alpha + (beta & 1)] holds the counts of cells
-// (alpha, beta) and (alpha, beta + 2) in its low and high 16 bits.
-__device__ __forceinline__ void add_counts(uint32_t* __restrict__ cnt, const PassRegion& pr, const uint32_t (&c16)[8]) {
+// (alpha, beta) and (alpha, beta + 2) in its low and high 16 bits, the same
+// values in every lane.  The lanes add them in parallel: lane l < 16 adds the
+// count of grandchild cell (alpha, beta) = (l >> 2, l & 3) of the parent whose
+// passed children start at record child_base (pass mask in the low bits of
+// `packed`), so one atomic instruction covers all sixteen cells.  Every lane
+// must call this.
+__device__ __forceinline__ void add_counts_lanes(uint32_t* __restrict__ cnt, uint32_t child_base, uint32_t packed,
+                                                 const uint32_t (&c16)[8]) {
+    const int lane = threadIdx.x & 31;
+    const int al = (lane >> 2) & 3, be = lane & 3;
+    const int sel = 2 * al + (be & 1);
+    uint32_t w = c16[0];
 #pragma unroll
-    for (int al = 0; al < 4; ++al) {
-#pragma unroll
-        for (int be = 0; be < 4; ++be) {
-            const uint32_t word = c16[2 * al + (be & 1)];
-            const uint32_t c = (be >> 1) ? (word >> 16) : (word & 0xffffu);
-            if (!c) continue;
-            const int q = quad_of(al >> 1, be >> 1), g = quad_of(al & 1, be & 1);
-            atomicAdd(&cnt[4 * (size_t)child_index(pr, q) + g], c);
-        }
-    }
+    for (int k = 1; k < 8; ++k) w = sel == k ? c16[k] : w;
+    const uint32_t c = (be & 2) ? (w >> 16) : (w & 0xffffu);
+    const int q = quad_of(al >> 1, be >> 1), g = quad_of(al & 1, be & 1);
+    const uint32_t ci = child_base + __popc(packed & 0xfu & ((1u << q) - 1u));
+    if (lane < 16 && c) atomicAdd(&cnt[4 * (size_t)ci + g], c);
 }
 
 // Per-lane byte counters rows[alpha] (byte beta) -> 16-bit pairs summed over
@@ -540,7 +545,7 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
         if (cur != kNoRegion) {
             uint32_t c16[8];
             reduce_rows(rows, 0xffffffffu, c16);
-            if (lane == 0) add_counts(a.child_cnt, cg.pr, c16);
+            add_counts_lanes(a.child_cnt, cg.pr.child_base, cg.pr.packed, c16);
         }
         rows[0] = rows[1] = rows[2] = rows[3] = 0u;
         steps = 0;
@@ -733,14 +738,17 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
             const bool mine = valid && r == rl;
             uint32_t rest = __ballot_sync(0xffffffffu, valid && !mine);
             while (rest) {
+                // one parent group at a time; every lane takes part (lanes
+                // outside the group add zero) so the counts land in all lanes
                 const int leader = __ffs(rest) - 1;
                 const uint32_t rg = __shfl_sync(0xffffffffu, r, leader);
                 const uint32_t gmask = __ballot_sync(0xffffffffu, valid && r == rg);
-                if (gmask & (1u << lane)) {
-                    uint32_t c16[8];
-                    reduce_rows(own, gmask, c16);
-                    if (lane == leader) add_counts(a.child_cnt, g.pr, c16);
-                }
+                const uint32_t in = (gmask >> lane) & 1u ? 0xffffffffu : 0u;
+                const uint32_t part[4] = {own[0] & in, own[1] & in, own[2] & in, own[3] & in};
+                uint32_t c16[8];
+                reduce_rows(part, 0xffffffffu, c16);
+                add_counts_lanes(a.child_cnt, __shfl_sync(0xffffffffu, g.pr.child_base, leader),
+                                 __shfl_sync(0xffffffffu, g.pr.packed, leader), c16);
                 rest &= ~gmask;
             }
             start_run(rl);
@@ -766,7 +774,7 @@ __global__ void __launch_bounds__(TPB, MINB) pass_kernel(LevelArgs a) {
 // earlier run of the same job); a capacity overflow is flagged, every later
 // phase is skipped and the host runs the job level by level instead.
 template <typename I>
-__global__ void __launch_bounds__(256, 3) persistent_kernel(PersistentArgs f) {
+__global__ void __launch_bounds__(256, 4) persistent_kernel(PersistentArgs f) {
     namespace cg = cooperative_groups;
     cg::grid_group grid = cg::this_grid();
     stage_body<I>(f.pts, f.total_pts, f.base.units, f.n_images, f.img_start, f.img_unit, f.vox[0], f.cnt[0],
@@ -836,6 +844,30 @@ int launch_stage(const int16_t* pts, uint64_t total_points, const Unit* units, i
 int launch_select(const LevelArgs& a, int tpb_unused, int grid, void* stream) {
     (void)tpb_unused;
     select_kernel<<<grid, kSelTPB, 0, (cudaStream_t)stream>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// ============================================================================ copy out
+// Leaves to a caller's pinned host buffer, written by the SMs through its
+// device mapping (over the CPU-GPU link) instead of by a copy engine.  16-byte
+// words, four per thread and iteration, grid-stride.
+__global__ void __launch_bounds__(256) copy16_kernel(const uint4* __restrict__ src, uint4* __restrict__ dst,
+                                                     uint64_t n16) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; k + 3 * stride < n16; k += 4 * stride) {
+        const uint4 a = src[k], b = src[k + stride], c = src[k + 2 * stride], d = src[k + 3 * stride];
+        dst[k] = a;
+        dst[k + stride] = b;
+        dst[k + 2 * stride] = c;
+        dst[k + 3 * stride] = d;
+    }
+    for (; k < n16; k += stride) dst[k] = src[k];
+}
+
+int launch_copy16(const void* src, void* dst, uint64_t n16, int grid, void* stream) {
+    if (n16 == 0) return 0;
+    copy16_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>((const uint4*)src, (uint4*)dst, n16);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

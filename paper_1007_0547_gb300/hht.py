@@ -31,8 +31,10 @@ HHT_E_UNKNOWN_TICKET = -8
 # every function the C header declares
 EXPORTS = ("hht_create", "hht_destroy", "hht_detect", "hht_detect_batch", "hht_fetch_leaves", "hht_submit",
            "hht_poll", "hht_progress", "hht_profile_enable", "hht_profile_read", "hht_strerror", "hht_version",
-           "hht_detect_noalloc", "hht_autotune", "hht_set_tuning", "hht_set_batch_mode", "hht_fetch_all_leaves")
+           "hht_detect_noalloc", "hht_autotune", "hht_set_tuning", "hht_set_batch_mode", "hht_fetch_all_leaves",
+           "hht_inject_fault")
 BATCH_LEVELS, BATCH_PERSISTENT = 0, 1
+FAULT_NONE, FAULT_WITHHOLD_SCAN_TILE = 0, 1
 TUNE_SHAPES = 6
 
 
@@ -104,6 +106,8 @@ def load(path: Optional[str] = None):
     lib.hht_set_batch_mode.restype = ctypes.c_int
     lib.hht_set_tuning.argtypes = [vp, i32]
     lib.hht_set_tuning.restype = ctypes.c_int
+    lib.hht_inject_fault.argtypes = [vp, i32, i64]
+    lib.hht_inject_fault.restype = ctypes.c_int
     lib.hht_strerror.argtypes = [ctypes.c_int]
     lib.hht_strerror.restype = ctypes.c_char_p
     lib.hht_version.argtypes = []
@@ -385,6 +389,15 @@ class Context:
         return int(best.value), times
 
     # ------------------------------------------------------------ kernel timing
+    def inject_fault(self, kind: int, arg: int = 0) -> None:
+        """Host-side fault injection for tests (hht_inject_fault): with
+        FAULT_WITHHOLD_SCAN_TILE, tile `arg` of the next job's look-back
+        scans publishes nothing, so that job fails with HHT_E_TIMEOUT once the
+        bounded waits behind it expire."""
+        rc = load().hht_inject_fault(self._h, int(kind), int(arg))
+        if rc != HHT_OK:
+            raise HhtError(rc, "hht_inject_fault")
+
     def profile(self, on: bool = True) -> None:
         rc = load().hht_profile_enable(self._h, 1 if on else 0)
         if rc != HHT_OK:

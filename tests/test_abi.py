@@ -28,7 +28,8 @@ def test_header_declares_the_api():
     assert set(_declared()) == {"hht_create", "hht_destroy", "hht_detect", "hht_detect_batch", "hht_fetch_leaves",
                                 "hht_submit", "hht_poll", "hht_progress", "hht_profile_enable", "hht_profile_read",
                                 "hht_strerror", "hht_version", "hht_detect_noalloc", "hht_autotune",
-                                "hht_set_tuning", "hht_set_batch_mode", "hht_fetch_all_leaves"}
+                                "hht_set_tuning", "hht_set_batch_mode", "hht_fetch_all_leaves",
+                                "hht_inject_fault"}
 
 
 def test_library_exports_every_declared_symbol(lib):
@@ -57,6 +58,7 @@ def test_host_only_calls(lib):
     assert lib.hht_set_batch_mode(None, 1) == hht.HHT_E_ARG
     assert lib.hht_fetch_all_leaves(None, None, 0, None, None, None) == hht.HHT_E_ARG
     assert lib.hht_autotune(None, None, 0, None, None) == hht.HHT_E_ARG
+    assert lib.hht_inject_fault(None, hht.FAULT_WITHHOLD_SCAN_TILE, 0) == hht.HHT_E_ARG
 
 
 def test_result_struct_layout_matches_header(lib):

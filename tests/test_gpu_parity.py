@@ -187,6 +187,41 @@ def test_caller_leaf_buffers_pinned_and_device(ctx):
         ctx.detect(*batch[0], leaves_out=np.zeros((1, 4), np.int32))
 
 
+def test_large_leaf_copies_into_pinned_host_memory(ctx, hht):
+    # more than 1 MB of leaves: into pinned host memory they are written by a
+    # copy kernel through the buffer's device mapping, into device or pageable
+    # memory by cudaMemcpyAsync; every route must give the same bytes
+    import ctypes
+    import torch
+    imgs = [synth.plain_1024(index=2), synth.plain_1024(index=3)]
+    dev = [(torch.from_numpy(im.points).cuda(), im.W, im.H, im.depth, im.T) for im in imgs]
+    ref = [ctx.detect(*x) for x in dev]
+    lv = [r.leaves_numpy().copy() for r in ref]
+    assert lv[0].nbytes > (1 << 20)
+    pinned = torch.full((len(lv[0]) + len(lv[1]) + 3, 4), -1, dtype=torch.int32).pin_memory()
+    one = ctx.detect(*dev[0], leaves_out=pinned)
+    assert np.array_equal(one.leaves_numpy(), lv[0])
+    assert (pinned[len(lv[0]):] == -1).all()
+    pinned.fill_(-1)
+    both = ctx.detect_batch(dev, leaves_out=pinned)
+    for r, want in zip(both, lv):
+        assert np.array_equal(r.leaves_numpy(), want)
+    assert (pinned[len(lv[0]) + len(lv[1]):] == -1).all()
+    pageable = np.full((len(lv[1]), 4), -1, np.int32)
+    assert np.array_equal(ctx.detect(*dev[1], leaves_out=pageable).leaves_numpy(), lv[1])
+    # second call of the two-call protocol into pinned memory
+    r = hht._Result()
+    r.leaves = None
+    r.leaf_capacity = 0
+    lib = hht.load()
+    rc = lib.hht_detect(ctx._h, dev[0][0].data_ptr(), imgs[0].n, imgs[0].W, imgs[0].H, imgs[0].depth, imgs[0].T,
+                        ctypes.byref(r))
+    assert rc == hht.HHT_E_CAPACITY and r.n_leaves == len(lv[0])
+    pinned.fill_(-1)
+    assert lib.hht_fetch_leaves(ctx._h, 0, pinned.data_ptr(), len(pinned)) == hht.HHT_OK
+    assert np.array_equal(pinned[: len(lv[0])].numpy().astype(np.uint32), lv[0])
+
+
 def test_capacity_two_call_protocol(ctx, hht):
     import ctypes
     img = synth.plain_128()
