@@ -249,6 +249,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-persistent", action="store_true")
+    ap.add_argument("--no-fht", action="store_true", help="skip the prior-art FHT circle-test comparison")
     ap.add_argument("--serve", action="store_true", help="open-loop serving benchmark instead of the batch line")
     ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--serve-load", type=float, default=0.8, help="offered rate as a fraction of the saturated rate")
@@ -418,6 +419,30 @@ def main():
         persistent = {"ms_per_step": pm, "images_per_s": len(dev_images) / (pm / 1e3),
                       "tests_per_s": tests_per_step / (pm / 1e3)}
 
+    # ---------------------------------------------------------------- prior-art FHT circle test, same images
+    fht = None
+    if not args.no_fht:
+        votes_exact = sum(int(r.stats[:, :, 2].sum()) for r in res)
+        ctx.set_predicate(hht.PREDICATE_FHT)
+        fres = step()  # allocations
+        torch.cuda.synchronize()
+        f_ms = []
+        for _ in range(max(2, args.steps // 2)):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fres = step()
+            e1.record(stream)
+            e1.synchronize()
+            f_ms.append(e0.elapsed_time(e1))
+        ctx.set_predicate(hht.PREDICATE_EXACT)
+        fm = sum(f_ms) / len(f_ms)
+        votes_fht = sum(int(r.stats[:, :, 2].sum()) for r in fres)
+        fht = {"what": "circumscribed-circle test of the prior-art FHT (exact integer form), same images and thresholds",
+               "ms_per_step": fm, "tests_per_s": sum(r.total_tests() for r in fres) / (fm / 1e3),
+               "votes": votes_fht, "votes_exact": votes_exact, "C_v": votes_fht / max(1, votes_exact),
+               "C_t": fm / (total_ms / args.steps), "leaves": int(sum(r.n_leaves for r in fres))}
+
     # ---------------------------------------------------------------- roofline of the pass kernel
     peak, peak_kind = read_peaks()
     achieved = (prof["pass_bytes"] / 1e9) / (prof["pass_ms"] / 1e3) if prof["pass_ms"] > 0 else 0.0
@@ -451,6 +476,7 @@ def main():
                        "what": "one step (whole batch)"},
         "per_image_sequence": per_image,
         "persistent_form": persistent,
+        "fht_form": fht,
         "e2e": e2e,
         "roofline": roofline,
         "cpu_baseline": cpu,

@@ -262,6 +262,27 @@ int hht_set_tuning(hht_ctx *ctx, int32_t shape);
 int hht_set_batch_mode(hht_ctx *ctx, int32_t mode);
 
 /*
+ * Membership test of hht_detect and hht_detect_batch on this context.
+ * HHT_PREDICATE_EXACT (default): the paper's 4-bit corner code (Section 2).
+ * HHT_PREDICATE_FHT: the circumscribed-circle test of the Fast Hough
+ * Transform that the paper compares against (Sections 1 and 3; Table 1): a
+ * line votes for a region when its distance from the region's centre is at
+ * most the radius of the circle through the region's four corners.
+ * Distances are taken in cell units, where every region is a square, and the
+ * test G(centre)^2 <= 2 s^2 (x^2 + 4L^2) (s = region side in cells, G as in
+ * the exact test) is decided exactly on integers.  Every line that crosses a
+ * region also passes its circle, so FHT votes are a superset of the exact
+ * ones (the paper's false votes).  The FHT form runs the same level loop, is
+ * built for images with log2(L) + depth <= 27 (larger ones: HHT_E_ARG before
+ * any device work) and is not used by the serving interface or the
+ * persistent batch form (those always use the exact test).
+ * Errors: HHT_E_ARG (NULL context, unknown predicate).
+ */
+#define HHT_PREDICATE_EXACT 0
+#define HHT_PREDICATE_FHT 1
+int hht_set_predicate(hht_ctx *ctx, int32_t predicate);
+
+/*
  * Host-side fault injection, for tests of the failure path (no paper
  * counterpart).  HHT_FAULT_WITHHOLD_SCAN_TILE: in the next detection job
  * (hht_detect or hht_detect_batch) of this context, tile `arg` of every

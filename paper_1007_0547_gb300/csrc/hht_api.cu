@@ -165,6 +165,12 @@ int check_image(const hht_image& im) {
     return HHT_OK;
 }
 
+// The circle test is built on int32 corner arithmetic: log2 L + depth <= 27.
+int check_predicate(const hht_ctx* c, const hht_image& im) {
+    if (c->predicate != HHT_PREDICATE_FHT) return HHT_OK;
+    return hht::ceil_log2_i(std::max(im.W, im.H)) + im.depth <= 27 ? HHT_OK : HHT_E_ARG;
+}
+
 constexpr int kSelTile = 1024;   // parents per select tile
 constexpr int kPersistentRetry = 1;  // run_wave: persistent capacities too small, run again level by level
 constexpr int kPassTile = 256 * 8;  // voters per pass block below which fewer blocks are launched
@@ -321,8 +327,10 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
         mix(((uint64_t)im[g].W << 32) | (uint64_t)im[g].H);
         mix(((uint64_t)im[g].depth << 32) | (uint64_t)im[g].T);
     }
+    const bool fht = c->predicate == HHT_PREDICATE_FHT;
+    if (fht && i64) return HHT_E_ARG;  // checked by the entry points before any device work
     const int occ_p = i64 ? c->occ_persistent64 : c->occ_persistent32;
-    const bool persistent = c->batch_mode == 1 && c->plan.valid && c->plan.sig == sig && occ_p > 0;
+    const bool persistent = !fht && c->batch_mode == 1 && c->plan.valid && c->plan.sig == sig && occ_p > 0;
     uint64_t cap_rec = 0, cap_vox = 0, cap_tiles = 0;
     if (persistent) {
         cap_rec = std::max<uint64_t>(c->plan.cap_rec, (uint64_t)n_units);
@@ -418,7 +426,7 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
         if (launch_stage((const int16_t*)c->pts.p, total, (const Unit*)c->units.p, count,
                          (const uint64_t*)c->img_start.p, (const uint32_t*)c->img_unit.p, (Voter*)c->vox[0].p,
                          (uint32_t*)c->cnt[0].p, (uint64_t*)c->stats.p, (uint32_t*)c->img_err.p, d_status, i64,
-                         st) != 0)
+                         st, fht) != 0)
             return HHT_E_CUDA;
         if (total > 0) c->prof.launches += 1;
     }
@@ -498,15 +506,15 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
         a.vin = (const Voter*)c->vox[pi].p;
         a.vout = (Voter*)c->vox[ci].p;
         a.cap_voters = nout;
-        const int shape = i64 ? 0 : c->pass_shape;
-        const int occ = i64 ? c->occ_pass64 : c->occ_shape[shape];
+        const int shape = (i64 || fht) ? 0 : c->pass_shape;
+        const int occ = fht ? c->occ_pass_fht : (i64 ? c->occ_pass64 : c->occ_shape[shape]);
         // enough warp slices to fill the device, no more than the stream needs
-        const uint64_t tile = 8ull * (uint64_t)pass_threads(i64, shape);
+        const uint64_t tile = 8ull * (uint64_t)(fht ? 256 : pass_threads(i64, shape));
         const uint64_t want_blocks = (nin + tile - 1) / tile;
         const int pass_grid = (int)std::min<uint64_t>(want_blocks, (uint64_t)c->num_sms * occ);
         {
             ProfScope ps(c, 2);
-            if (launch_pass(a, i64, std::max(pass_grid, 1), st, shape) != 0) return HHT_E_CUDA;
+            if (launch_pass(a, i64, std::max(pass_grid, 1), st, shape, fht) != 0) return HHT_E_CUDA;
         }
         c->prof.launches += 1;
         c->prof.pass_launches += 1;
@@ -604,12 +612,14 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
 
 // Upper estimate of a wave member's peak device bytes (two voter streams of
 // the two deepest written levels, both halves, dense regime).
-uint64_t estimate_bytes(const hht_image& im) {
+uint64_t estimate_bytes(const hht_image& im, bool fht) {
     const double n = (double)im.n;
     const int D = im.depth;
     if (D < 3) return (uint64_t)(64.0 * n + 4096);
     const double dense = 1.25 * n * (std::ldexp(1.0, D - 2) + std::ldexp(1.0, D - 3));
-    return (uint64_t)(2.0 * 8.0 * dense * 1.2 + 64.0 * n + 4096);
+    // the circle test's wider voter lists (the paper reports 2-8 times the votes)
+    const double widen = fht ? 4.0 : 1.0;
+    return (uint64_t)(2.0 * 8.0 * dense * 1.2 * widen + 64.0 * n + 4096);
 }
 
 int run_waves(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int job_first) {
@@ -627,7 +637,7 @@ int run_waves(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int 
         int last = first;
         uint64_t acc = 0;
         while (last < count) {
-            const uint64_t e = estimate_bytes(im[last]);
+            const uint64_t e = estimate_bytes(im[last], c->predicate == HHT_PREDICATE_FHT);
             if (last > first && acc + e > budget) break;
             acc += e;
             ++last;
@@ -696,6 +706,7 @@ int hht_create(hht_ctx** out, int device, void* cuda_stream, uint64_t mem_budget
     c->occ_pass32 = occupancy_pass(false);
     c->occ_pass64 = occupancy_pass(true);
     for (int k = 0; k < kPassShapeCount; ++k) c->occ_shape[k] = occupancy_pass(false, k);
+    c->occ_pass_fht = occupancy_pass_fht();
     c->occ_persistent32 = occupancy_persistent(false);
     c->occ_persistent64 = occupancy_persistent(true);
     if (const char* e = getenv("HHT_BATCH_MODE")) c->batch_mode = atoi(e) == 1 ? 1 : 0;
@@ -743,6 +754,8 @@ int hht_detect(hht_ctx* c, const hht_point* points, int64_t n, int32_t W, int32_
     int rc = check_image(im);
     if (rc != HHT_OK) return rc;
     std::lock_guard<std::mutex> lk(c->mu);
+    rc = check_predicate(c, im);
+    if (rc != HHT_OK) return rc;
     cudaSetDevice(c->device);
     rc = run_job(c, &im, 1, out);
     if (rc != HHT_OK) return rc;
@@ -758,6 +771,10 @@ int hht_detect_batch(hht_ctx* c, const hht_image* images, int32_t count, hht_res
         if (rc != HHT_OK) return rc;
     }
     std::lock_guard<std::mutex> lk(c->mu);
+    for (int g = 0; g < count; ++g) {
+        const int rc = check_predicate(c, images[g]);
+        if (rc != HHT_OK) return rc;
+    }
     cudaSetDevice(c->device);
     return run_job(c, images, count, outs);
 }
@@ -817,6 +834,9 @@ int hht_autotune(hht_ctx* c, const hht_image* images, int32_t count, int32_t* be
     std::lock_guard<std::mutex> lk(c->mu);
     cudaSetDevice(c->device);
     std::vector<hht_result> outs((size_t)count);
+    // the tile shapes are those of the exact test's level kernel
+    const int saved_predicate = c->predicate;
+    c->predicate = HHT_PREDICATE_EXACT;
     const bool was_profiling = c->profile;
     const hht_profile_counters saved = c->prof;
     double best_ms = 1e300;
@@ -843,8 +863,17 @@ int hht_autotune(hht_ctx* c, const hht_image* images, int32_t count, int32_t* be
     c->pass_shape = best_shape;
     c->profile = was_profiling;
     c->prof = saved;
+    c->predicate = saved_predicate;
     if (rc != HHT_OK) return rc;
     *best = best_shape;
+    return HHT_OK;
+}
+
+int hht_set_predicate(hht_ctx* c, int32_t predicate) {
+    if (!c || (predicate != HHT_PREDICATE_EXACT && predicate != HHT_PREDICATE_FHT)) return HHT_E_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (predicate != c->predicate) c->plan.valid = false;  // the persistent form's size plan was for the other test
+    c->predicate = predicate;
     return HHT_OK;
 }
 

@@ -54,6 +54,8 @@ struct hht_ctx {
     bool graph_capture_failed = false;
     int occ_shape[hht::kPassShapeCount] = {1, 1, 1, 1, 1, 1};  // resident blocks per SM of each shape
     int64_t inject_tile = -1;  // hht_inject_fault: selection tile withheld in the next job (-1 = none)
+    int predicate = 0;         // HHT_PREDICATE_EXACT or HHT_PREDICATE_FHT (hht_detect / hht_detect_batch)
+    int occ_pass_fht = 1;
 
     // job buffers
     DevBuf pts, img_start, img_unit, units, stats, infos, status, leaf_total, img_err, scan_states;

@@ -168,14 +168,18 @@ int occupancy_persistent(bool int64_path);
 // [img_start[g], img_start[g+1]) and the units img_unit[g], img_unit[g] + 1).
 int launch_stage(const int16_t* pts, uint64_t total_points, const Unit* units, int n_images,
                  const uint64_t* img_start, const uint32_t* img_unit, Voter* vstream, uint32_t* cnt,
-                 uint64_t* stats, uint32_t* img_err, DeviceStatus* status, bool int64_path, void* stream);
+                 uint64_t* stats, uint32_t* img_err, DeviceStatus* status, bool int64_path, void* stream,
+                 bool fht = false);
 int launch_select(const LevelArgs& a, int threads_per_block, int grid, void* stream);
 // Copy n16 16-byte words from device memory to `dst` (device memory, or the
 // device mapping of pinned host memory).
 int launch_copy16(const void* src, void* dst, uint64_t n16, int grid, void* stream);
 // Pass-kernel tile shapes for the autotuner; shape 0 is the default.
 constexpr int kPassShapeCount = 6;
-int launch_pass(const LevelArgs& a, bool int64_path, int grid, void* stream, int shape = 0);
+// fht: the prior-art circumscribed-circle test instead of the 4-bit code
+// (int32 corner arithmetic and tile shape 0 only).
+int launch_pass(const LevelArgs& a, bool int64_path, int grid, void* stream, int shape = 0, bool fht = false);
+int occupancy_pass_fht();
 int pass_threads(bool int64_path, int shape = 0);
 int occupancy_select();
 int occupancy_pass(bool int64_path, int shape = 0);

@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "hht_device.cuh"
 #include "hht_internal.h"
@@ -59,7 +60,25 @@ __device__ __forceinline__ bool run_head(uint32_t key) {
 }  // namespace
 
 // ============================================================================ stage
-template <typename I>
+// FHT circle test of the four level-1 quadrants (side K/2) of the level-0
+// region: with 2G at a child's centre = -2LK + 4LK*n - K*x + 2K*x*e - 2K*y
+// (e, n: east and north halves), the child gets the vote when
+// (2G)^2 <= 2 K^2 (x^2 + 4L^2).  Bit q = quadrant q.
+__device__ __forceinline__ uint32_t fht_root_children(int32_t x, int32_t y, int lL, int D) {
+    const int64_t L = int64_t(1) << lL, K = int64_t(1) << D;
+    const int64_t X = (int64_t)x * x + 4 * L * L;
+    const int64_t r = X << (2 * D + 1);
+    uint32_t bits = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int64_t e = (q == NE || q == SE) ? 1 : 0, n = (q == NE || q == NW) ? 1 : 0;
+        const int64_t g2 = -2 * L * K + 4 * L * K * n - K * x + 2 * K * x * e - 2 * K * y;
+        bits |= (g2 * g2 <= r ? 1u : 0u) << q;
+    }
+    return bits;
+}
+
+template <typename I, bool FHT = false>
 __device__ __forceinline__ void stage_body(const int16_t* __restrict__ pts, uint64_t total,
                                            const Unit* __restrict__ units, int n_images,
                                            const uint64_t* __restrict__ img_start,
@@ -117,7 +136,7 @@ __device__ __forceinline__ void stage_body(const int16_t* __restrict__ pts, uint
                 const uint32_t code = region_code3(M);
                 const bool votes_root = code != 0u && code != 15u;
                 if (!votes_root) atomicOr(&status->err, kErrInvariant);
-                vals[0] = spread4(child_votes3(M));
+                vals[0] = spread4(FHT ? fht_root_children(x, y, lL, D) : child_votes3(M));
                 vals[1] = votes_root ? 1u : 0u;
                 if (D >= 2) {
                     Voter vr;
@@ -142,14 +161,14 @@ __device__ __forceinline__ void stage_body(const int16_t* __restrict__ pts, uint
     }
 }
 
-template <typename I>
+template <typename I, bool FHT = false>
 __global__ void __launch_bounds__(256) stage_kernel(const int16_t* __restrict__ pts, uint64_t total,
                                                     const Unit* __restrict__ units, int n_images,
                                                     const uint64_t* __restrict__ img_start,
                                                     const uint32_t* __restrict__ img_unit, Voter* __restrict__ v0,
                                                     uint32_t* __restrict__ root_cnt, uint64_t* __restrict__ stats,
                                                     uint32_t* __restrict__ img_err, DeviceStatus* status) {
-    stage_body<I>(pts, total, units, n_images, img_start, img_unit, v0, root_cnt, stats, img_err, status);
+    stage_body<I, FHT>(pts, total, units, n_images, img_start, img_unit, v0, root_cnt, stats, img_err, status);
 }
 
 // ============================================================================ select
@@ -487,6 +506,76 @@ __device__ __forceinline__ Classified<I> classify(const ParentGeo<I>& g, uint32_
     c.gv = v1 & grand_cells(v2 & g.pspread);
     return c;
 }
+
+// ---- the prior-art FHT circle test (Sections 1-3: the paper's comparison)
+// A line votes for a region when its distance from the region's centre is at
+// most the radius of the circle through the region's corners, distances in
+// cell units (regions are squares).  In those units the line is G(i, j) = 0
+// with |grad G| = 2 sqrt(x^2 + 4L^2), and a region of side s has radius
+// s / sqrt(2), so the test is G(centre)^2 <= 2 s^2 (x^2 + 4L^2), decided
+// exactly on integers.  Centres of the parent's 4 x 4 grandchildren (side
+// S/4) are half-integer vertices, so 2 G is used:
+//   2G(alpha, beta) = C0 + x*Cx - 2K*y + alpha * (x*S) + beta * 2LS,
+//   C0 = 8L*bS + L*S - 4LK, Cx = 4*aS + S/2 - 2K,
+// and a grandchild votes when (2G)^2 <= S^2 (x^2 + 4L^2) / 2.  A child's
+// centre is the midpoint of the centres of its SW and NE grandchildren, so
+// with h = the sum of those two 2G values it votes when
+// h^2 <= 8 S^2 (x^2 + 4L^2).  A grandchild's circle lies inside its child's
+// (centre offset and radius both half the child's radius), so, as for the
+// exact test, every grandchild voter is a voter of its child.  int32 holds
+// every 2G when lL + D <= 27 (|2G| <= 8LK at points of the parameter space);
+// the squares and bounds are int64.
+struct ParentGeoF {
+    PassRegion pr;
+    int32_t C0, Cx, dB, yK;  // yK = 2K
+    int64_t L4;              // 4L^2
+    int sS;
+    uint32_t pspread, wspread;
+    __device__ __forceinline__ void load(const PassRegion* p, uint32_t r) {
+        pr = p[r];
+        sS = (pr.packed >> 8) & 31;
+        const int lL = (pr.packed >> 13) & 31, D = (pr.packed >> 18) & 31;
+        const int64_t S = int64_t(1) << sS, K = int64_t(1) << D, L = int64_t(1) << lL;
+        C0 = (int32_t)(8 * L * (int64_t)pr.b * S + L * S - 4 * L * K);
+        Cx = (int32_t)(4 * (int64_t)pr.a * S + S / 2 - 2 * K);
+        dB = (int32_t)(2 * L * S);
+        yK = (int32_t)(2 * K);
+        L4 = 4 * L * L;
+        pspread = spread_quads(pr.packed & 0xfu);
+        wspread = spread_quads((pr.packed >> 4) & 0xfu);
+    }
+};
+
+template <typename I>
+__device__ __forceinline__ Classified<I> classify(const ParentGeoF& g, uint32_t xy) {
+    const int32_t x = (int32_t)(xy & 0xffffu), y = (int32_t)(xy >> 16);
+    const int32_t h00 = g.C0 + x * g.Cx - g.yK * y;
+    const int32_t hx = x << g.sS;
+    const int64_t X = (int64_t)x * x + g.L4;
+    const int64_t rg = X << (2 * g.sS - 1);  // grandchildren: (2G)^2 <= S^2 X / 2
+    const int64_t rc = X << (2 * g.sS + 3);  // children: h^2 <= 8 S^2 X
+    int32_t h[4][4];
+    uint32_t v1 = 0;
+#pragma unroll
+    for (int al = 0; al < 4; ++al) {
+#pragma unroll
+        for (int be = 0; be < 4; ++be) {
+            h[al][be] = h00 + al * hx + be * g.dB;
+            v1 |= ((int64_t)h[al][be] * h[al][be] <= rg ? 1u : 0u) << (kGrandBase + 5 * al + be);
+        }
+    }
+    uint32_t v2 = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int e = (q == NE || q == SE) ? 1 : 0, n = (q == NE || q == NW) ? 1 : 0;
+        const int64_t sum = (int64_t)h[2 * e][2 * n] + h[2 * e + 1][2 * n + 1];
+        v2 |= (sum * sum <= rc ? 1u : 0u) << quad_bit(q);
+    }
+    Classified<I> c;
+    c.kw = v2 & g.wspread;
+    c.gv = v1 & grand_cells(v2 & g.pspread);
+    return c;
+}
 }  // namespace
 
 // Pass-kernel work distribution: grabs of about 1/kGrabShare of a warp's
@@ -498,8 +587,9 @@ constexpr int kMaxGrab = 4096;
 // Tile shape (autotuned): STEPS warp steps of 32 voters per chunk (one
 // cursor reservation per child and chunk), TPB threads per block, at least
 // MINB resident blocks per SM (register budget).
-template <typename I, int STEPS, int TPB>
+template <typename I, int STEPS, int TPB, bool FHT = false>
 __device__ __forceinline__ void pass_body(const LevelArgs& a) {
+    using Geo = typename std::conditional<FHT, ParentGeoF, ParentGeo<I>>::type;
     constexpr int kChunkSteps = STEPS;
     constexpr int kPassTPB = TPB;
     static_assert(32 * STEPS <= 255, "a chunk's per-quadrant counts are summed in byte fields");
@@ -536,7 +626,7 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
 
     // the run being counted: warp-uniform parent and per-lane byte counters
     uint32_t cur = kNoRegion;
-    ParentGeo<I> cg;
+    Geo cg;
     uint32_t ci[4] = {0u, 0u, 0u, 0u};  // child record index per quadrant of cur
     uint32_t rows[4] = {0u, 0u, 0u, 0u};
     uint32_t steps = 0;
@@ -602,7 +692,7 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
 #pragma unroll
             for (int k = 0; k < kChunkSteps; ++k) {
                 const uint32_t live = rec[k].y != kNoRegion ? 0xffffffffu : 0u;
-                const Classified<I> c = classify(cg, rec[k].x);
+                const Classified<I> c = classify<I>(cg, rec[k].x);
                 kw[k] = c.kw & live;
                 add_rows(rows, c.gv & live);
                 cnt += quad_counts(kw[k]);
@@ -689,7 +779,7 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
                 // still the current run
                 uint32_t kw = 0u;
                 if (valid) {
-                    const Classified<I> c = classify(cg, rk.x);
+                    const Classified<I> c = classify<I>(cg, rk.x);
                     kw = c.kw;
                     add_rows(rows, c.gv);
                 }
@@ -709,11 +799,11 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
             }
             // settle the current run; every lane classifies with its own parent
             settle();
-            ParentGeo<I> g = cg;
+            Geo g = cg;
             if (valid && r != cur) g.load(a.pregions, r);
             uint32_t kw = 0u, gv = 0u;
             if (valid) {
-                const Classified<I> c = classify(g, rk.x);
+                const Classified<I> c = classify<I>(g, rk.x);
                 kw = c.kw;
                 gv = c.gv;
             }
@@ -761,9 +851,9 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
     settle();
 }
 
-template <typename I, int STEPS, int TPB, int MINB>
+template <typename I, int STEPS, int TPB, int MINB, bool FHT = false>
 __global__ void __launch_bounds__(TPB, MINB) pass_kernel(LevelArgs a) {
-    pass_body<I, STEPS, TPB>(a);
+    pass_body<I, STEPS, TPB, FHT>(a);
 }
 
 
@@ -827,12 +917,17 @@ int occupancy_select() {
 
 int launch_stage(const int16_t* pts, uint64_t total_points, const Unit* units, int n_images,
                  const uint64_t* img_start, const uint32_t* img_unit, Voter* v0, uint32_t* root_cnt,
-                 uint64_t* stats, uint32_t* img_err, DeviceStatus* status, bool int64_path, void* stream) {
+                 uint64_t* stats, uint32_t* img_err, DeviceStatus* status, bool int64_path, void* stream,
+                 bool fht) {
     if (total_points == 0) return 0;
     cudaStream_t st = (cudaStream_t)stream;
     const uint64_t want = (total_points + 255) / 256;
     const int grid = (int)(want < 4096 ? want : 4096);
-    if (int64_path)
+    if (fht) {
+        if (int64_path) return -1;  // the circle test is built for int32 corner arithmetic only
+        stage_kernel<int32_t, true><<<grid, 256, 0, st>>>(pts, total_points, units, n_images, img_start, img_unit,
+                                                          v0, root_cnt, stats, img_err, status);
+    } else if (int64_path)
         stage_kernel<int64_t><<<grid, 256, 0, st>>>(pts, total_points, units, n_images, img_start, img_unit, v0,
                                                      root_cnt, stats, img_err, status);
     else
@@ -884,7 +979,8 @@ const void* pass_fn32() {
     constexpr PassShape p = kPassShapes[S];
     return (const void*)pass_kernel<int32_t, p.steps, p.tpb, p.minb>;
 }
-const void* pass_fn(bool int64_path, int shape) {
+const void* pass_fn(bool int64_path, int shape, bool fht = false) {
+    if (fht) return (const void*)pass_kernel<int32_t, 4, 256, 3, true>;
     if (int64_path) return (const void*)pass_kernel<int64_t, 4, 256, 3>;
     switch (shape) {
         case 1: return pass_fn32<1>();
@@ -925,11 +1021,19 @@ int occupancy_pass(bool int64_path, int shape) {
     return per_sm < 1 ? 1 : per_sm;
 }
 
-int launch_pass(const LevelArgs& a, bool int64_path, int grid, void* stream, int shape) {
+int launch_pass(const LevelArgs& a, bool int64_path, int grid, void* stream, int shape, bool fht) {
+    if (fht && int64_path) return -1;
     void* args[] = {(void*)&a};
-    const cudaError_t e = cudaLaunchKernel(pass_fn(int64_path, shape), dim3(grid), dim3(pass_threads(int64_path, shape)),
-                                           args, 0, (cudaStream_t)stream);
+    const int tpb = fht ? 256 : pass_threads(int64_path, shape);
+    const cudaError_t e = cudaLaunchKernel(pass_fn(int64_path, shape, fht), dim3(grid), dim3(tpb), args, 0,
+                                           (cudaStream_t)stream);
     return e == cudaSuccess ? 0 : -1;
+}
+
+int occupancy_pass_fht() {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pass_fn(false, 0, true), 256, 0);
+    return per_sm < 1 ? 1 : per_sm;
 }
 
 }  // namespace hht

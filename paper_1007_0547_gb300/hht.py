@@ -32,9 +32,10 @@ HHT_E_UNKNOWN_TICKET = -8
 EXPORTS = ("hht_create", "hht_destroy", "hht_detect", "hht_detect_batch", "hht_fetch_leaves", "hht_submit",
            "hht_poll", "hht_progress", "hht_profile_enable", "hht_profile_read", "hht_strerror", "hht_version",
            "hht_detect_noalloc", "hht_autotune", "hht_set_tuning", "hht_set_batch_mode", "hht_fetch_all_leaves",
-           "hht_inject_fault")
+           "hht_inject_fault", "hht_set_predicate")
 BATCH_LEVELS, BATCH_PERSISTENT = 0, 1
 FAULT_NONE, FAULT_WITHHOLD_SCAN_TILE = 0, 1
+PREDICATE_EXACT, PREDICATE_FHT = 0, 1
 TUNE_SHAPES = 6
 
 
@@ -108,6 +109,8 @@ def load(path: Optional[str] = None):
     lib.hht_set_tuning.restype = ctypes.c_int
     lib.hht_inject_fault.argtypes = [vp, i32, i64]
     lib.hht_inject_fault.restype = ctypes.c_int
+    lib.hht_set_predicate.argtypes = [vp, i32]
+    lib.hht_set_predicate.restype = ctypes.c_int
     lib.hht_strerror.argtypes = [ctypes.c_int]
     lib.hht_strerror.restype = ctypes.c_char_p
     lib.hht_version.argtypes = []
@@ -389,6 +392,13 @@ class Context:
         return int(best.value), times
 
     # ------------------------------------------------------------ kernel timing
+    def set_predicate(self, predicate: int) -> None:
+        """PREDICATE_EXACT (the paper's 4-bit code) or PREDICATE_FHT (the
+        prior-art circumscribed-circle test) for detect and detect_batch."""
+        rc = load().hht_set_predicate(self._h, int(predicate))
+        if rc != HHT_OK:
+            raise HhtError(rc, "hht_set_predicate")
+
     def inject_fault(self, kind: int, arg: int = 0) -> None:
         """Host-side fault injection for tests (hht_inject_fault): with
         FAULT_WITHHOLD_SCAN_TILE, tile `arg` of the next job's look-back

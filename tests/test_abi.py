@@ -29,7 +29,7 @@ def test_header_declares_the_api():
                                 "hht_submit", "hht_poll", "hht_progress", "hht_profile_enable", "hht_profile_read",
                                 "hht_strerror", "hht_version", "hht_detect_noalloc", "hht_autotune",
                                 "hht_set_tuning", "hht_set_batch_mode", "hht_fetch_all_leaves",
-                                "hht_inject_fault"}
+                                "hht_inject_fault", "hht_set_predicate"}
 
 
 def test_library_exports_every_declared_symbol(lib):
@@ -59,6 +59,7 @@ def test_host_only_calls(lib):
     assert lib.hht_fetch_all_leaves(None, None, 0, None, None, None) == hht.HHT_E_ARG
     assert lib.hht_autotune(None, None, 0, None, None) == hht.HHT_E_ARG
     assert lib.hht_inject_fault(None, hht.FAULT_WITHHOLD_SCAN_TILE, 0) == hht.HHT_E_ARG
+    assert lib.hht_set_predicate(None, hht.PREDICATE_FHT) == hht.HHT_E_ARG
 
 
 def test_result_struct_layout_matches_header(lib):
