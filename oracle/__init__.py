@@ -12,6 +12,9 @@ from .oracle import (  # noqa: F401
     scaled_F,
     fht_votes,
     frame_side,
+    sobel,
+    edges,
+    detect_split,
     OracleResult,
     STAT_TESTED,
     STAT_PASSED,

@@ -277,3 +277,57 @@ int64_t oracle_count_region(const int16_t *xy, int64_t n, int32_t W, int32_t H, 
     }
     return cnt;
 }
+
+/*
+ * Front end (Section 3): Sobel's gradient operator on a grey-level image and
+ * the split of the edge points into ALPHA and BETA.
+ *
+ * gx and gy are Sobel's 3 x 3 responses at (x, y) (x to the right, y down):
+ *   gx = [p(x+1, y-1) + 2 p(x+1, y) + p(x+1, y+1)] - [p(x-1, y-1) + 2 p(x-1, y) + p(x-1, y+1)]
+ *   gy = [p(x-1, y+1) + 2 p(x, y+1) + p(x+1, y+1)] - [p(x-1, y-1) + 2 p(x, y-1) + p(x+1, y-1)]
+ * for interior pixels (1 <= x <= W-2, 1 <= y <= H-2); border pixels have no
+ * full neighbourhood and are never edge points.
+ *
+ * Readings where the paper is silent:
+ *   - a pixel is an edge point when gx^2 + gy^2 >= threshold^2 (the gradient
+ *     magnitude reaches `threshold`, compared exactly in integers);
+ *   - the line through an edge point runs across its gradient, so its slope
+ *     is -gx / gy; the point belongs to ALPHA (|slope| <= 1) when
+ *     |gx| <= |gy| and to BETA otherwise.
+ * Points are emitted in row-major order (y, then x).
+ */
+void oracle_sobel(const uint8_t *img, int32_t W, int32_t H, int32_t x, int32_t y, int32_t *gx, int32_t *gy)
+{
+    (void)H; /* the caller passes an interior pixel */
+#define P(dx, dy) ((int32_t)img[(int64_t)(y + (dy)) * W + (x + (dx))])
+    *gx = (P(1, -1) + 2 * P(1, 0) + P(1, 1)) - (P(-1, -1) + 2 * P(-1, 0) + P(-1, 1));
+    *gy = (P(-1, 1) + 2 * P(0, 1) + P(1, 1)) - (P(-1, -1) + 2 * P(0, -1) + P(1, -1));
+#undef P
+}
+
+int oracle_edges(const uint8_t *img, int32_t W, int32_t H, int32_t threshold, int16_t *alpha, int64_t alpha_cap,
+                 int64_t *n_alpha, int16_t *beta, int64_t beta_cap, int64_t *n_beta)
+{
+    if (!img || W < 1 || H < 1 || W > 32767 || H > 32767 || threshold < 0 || !n_alpha || !n_beta)
+        return ORACLE_E_ARG;
+    int64_t na = 0, nb = 0;
+    const int64_t t2 = (int64_t)threshold * threshold;
+    for (int32_t y = 1; y + 1 < H; ++y) {
+        for (int32_t x = 1; x + 1 < W; ++x) {
+            int32_t gx, gy;
+            oracle_sobel(img, W, H, x, y, &gx, &gy);
+            if ((int64_t)gx * gx + (int64_t)gy * gy < t2) continue;
+            const int32_t ax = gx < 0 ? -gx : gx, ay = gy < 0 ? -gy : gy;
+            if (ax <= ay) {
+                if (na < alpha_cap) { alpha[2 * na] = (int16_t)x; alpha[2 * na + 1] = (int16_t)y; }
+                ++na;
+            } else {
+                if (nb < beta_cap) { beta[2 * nb] = (int16_t)x; beta[2 * nb + 1] = (int16_t)y; }
+                ++nb;
+            }
+        }
+    }
+    *n_alpha = na;
+    *n_beta = nb;
+    return (na > alpha_cap || nb > beta_cap) ? ORACLE_E_CAPACITY : ORACLE_OK;
+}

@@ -73,6 +73,15 @@ def _load():
             lib.oracle_count_region.argtypes = [i16p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                                 ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64]
             lib.oracle_count_region.restype = ctypes.c_int64
+            u8p = ctypes.POINTER(ctypes.c_uint8)
+            i32p = ctypes.POINTER(ctypes.c_int32)
+            lib.oracle_sobel.argtypes = [u8p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                         i32p, i32p]
+            lib.oracle_sobel.restype = None
+            lib.oracle_edges.argtypes = [u8p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, i16p, ctypes.c_int64,
+                                         ctypes.POINTER(ctypes.c_int64), i16p, ctypes.c_int64,
+                                         ctypes.POINTER(ctypes.c_int64)]
+            lib.oracle_edges.restype = ctypes.c_int
             lib.oracle_frame_side.argtypes = [ctypes.c_int32, ctypes.c_int32]
             lib.oracle_frame_side.restype = ctypes.c_int64
             _lib = lib
@@ -153,3 +162,47 @@ def detect(points: np.ndarray, W: int, H: int, depth: int, T: int, mode: str = "
         if int(nr.value) > region_cap:
             raise RuntimeError("oracle: region dump capacity exceeded")
     return OracleResult(lv, stats, reg, rc)
+
+
+def sobel(image: np.ndarray, x: int, y: int):
+    """(gx, gy) of Sobel's operator at interior pixel (x, y) of a uint8 [H, W] image."""
+    img = np.ascontiguousarray(image, dtype=np.uint8)
+    H, W = img.shape
+    if not (1 <= x <= W - 2 and 1 <= y <= H - 2):
+        raise ValueError("oracle.sobel: not an interior pixel")
+    gx, gy = ctypes.c_int32(), ctypes.c_int32()
+    _load().oracle_sobel(img.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), W, H, x, y, ctypes.byref(gx),
+                         ctypes.byref(gy))
+    return int(gx.value), int(gy.value)
+
+
+def edges(image: np.ndarray, threshold: int):
+    """Sobel edge points of a uint8 [H, W] image split into ALPHA (|gx| <= |gy|)
+    and BETA, each int16 [k, 2] (x, y) in row-major order (Section 3)."""
+    img = np.ascontiguousarray(image, dtype=np.uint8)
+    H, W = img.shape
+    lib = _load()
+    cap = max(1, W * H)
+    a = np.zeros((cap, 2), np.int16)
+    b = np.zeros((cap, 2), np.int16)
+    na, nb = ctypes.c_int64(), ctypes.c_int64()
+    i16p = ctypes.POINTER(ctypes.c_int16)
+    rc = lib.oracle_edges(img.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), W, H, int(threshold),
+                          a.ctypes.data_as(i16p), cap, ctypes.byref(na), b.ctypes.data_as(i16p), cap,
+                          ctypes.byref(nb))
+    if rc != 0:
+        raise ValueError(f"oracle.edges failed with code {rc}")
+    return a[: na.value].copy(), b[: nb.value].copy()
+
+
+def detect_split(alpha: np.ndarray, beta: np.ndarray, W: int, H: int, depth: int, T: int) -> OracleResult:
+    """Section 3 with the front end's split: ALPHA is processed as given (half
+    0) and BETA with x and y swapped (half 1).  That is half 0 of a run on the
+    ALPHA points and half 1 of a run on the BETA points; leaves of ALPHA come
+    first, as the paper processes ALPHA first."""
+    ra = detect(alpha, W, H, depth, T)
+    rb = detect(beta, W, H, depth, T)
+    la = ra.leaves[ra.leaves[:, 0] == 0] if len(ra.leaves) else ra.leaves
+    lb = rb.leaves[rb.leaves[:, 0] == 1] if len(rb.leaves) else rb.leaves
+    stats = np.stack([ra.stats[0], rb.stats[1]])
+    return OracleResult(np.ascontiguousarray(np.concatenate([la, lb]).reshape(-1, 4)), stats, None, 0)

@@ -1,7 +1,8 @@
 """Seeded synthetic edge-point workloads.
 
 This package only draws inputs: binary edge images made of rasterised segments
-plus salt noise, returned as int16 (x, y) point lists.  It holds none of the
+plus salt noise, returned as int16 (x, y) point lists, and grey-level images
+for the front end.  It holds none of the
 Hough-transform arithmetic, so both the CPU oracle and the CUDA path can share
 it without sharing any of the method.
 """
@@ -21,3 +22,4 @@ from .edges import (  # noqa: F401
     ceil_log2,
     CONFIG_SEED_BASE,
 )
+from .gray import GrayImage, gray_256, gray_4096, gray_random  # noqa: F401
