@@ -196,6 +196,10 @@ typedef struct {
     double stage_ms;
     uint64_t persistent_launches;   /* batches run as one persistent launch (its time counts as pass_ms) */
     uint64_t persistent_fallbacks;  /* persistent launches that ran out of room and were rerun level by level */
+    uint64_t edges_launches;        /* front-end (Sobel and split) launches */
+    uint64_t edges_pixels;          /* pixels they read */
+    uint64_t edges_points;          /* edge points they wrote */
+    double edges_ms;                /* their summed device time */
 } hht_profile_counters;
 
 int hht_profile_enable(hht_ctx *ctx, int on);
@@ -260,6 +264,36 @@ int hht_set_tuning(hht_ctx *ctx, int32_t shape);
 #define HHT_BATCH_LEVELS 0
 #define HHT_BATCH_PERSISTENT 1
 int hht_set_batch_mode(hht_ctx *ctx, int32_t mode);
+
+/*
+ * Front end (Section 3): Sobel's gradient operator on a grey-level image and
+ * the split of its edge points into ALPHA (points on lines of absolute slope
+ * <= 1) and BETA (the rest), which the paper does while the gradient is
+ * computed.  `image` holds W * H bytes, row-major (pixel (x, y) at
+ * y * W + x), in host or device memory.  Readings of the paper:
+ *   - Sobel's 3 x 3 responses gx (right column minus left, weights 1, 2, 1)
+ *     and gy (row below minus row above) exist at interior pixels
+ *     (1 <= x <= W-2, 1 <= y <= H-2); border pixels are never edge points;
+ *   - a pixel is an edge point when gx^2 + gy^2 >= threshold^2;
+ *   - the line through an edge point runs across its gradient (slope
+ *     -gx / gy): ALPHA when |gx| <= |gy|, else BETA.
+ * hht_edges() writes the two point lists (row-major order each) into the
+ * caller's buffers (host or device) and their lengths into *n_alpha and
+ * *n_beta; when a buffer is too small it copies nothing and returns
+ * HHT_E_CAPACITY with the lengths set (call again with larger buffers).
+ * hht_detect_image() runs the front end and then the detection of
+ * hht_detect with ALPHA as half 0 and BETA (x and y swapped) as half 1,
+ * instead of every point entering both halves: out->stats[0] and [1] are the
+ * two halves' statistics, and the leaves are ALPHA's followed by BETA's
+ * (hht_fetch_leaves index 0 after HHT_E_CAPACITY).
+ * Errors: HHT_E_ARG (NULL, W or H outside [1, 32767], threshold < 0, depth or
+ * T as for hht_detect), HHT_E_CAPACITY, HHT_E_NOMEM, HHT_E_TIMEOUT, HHT_E_CUDA.
+ */
+int hht_edges(hht_ctx *ctx, const uint8_t *image, int32_t W, int32_t H, int32_t threshold, hht_point *alpha,
+              uint64_t alpha_capacity, uint64_t *n_alpha, hht_point *beta, uint64_t beta_capacity,
+              uint64_t *n_beta);
+int hht_detect_image(hht_ctx *ctx, const uint8_t *image, int32_t W, int32_t H, int32_t threshold, int32_t depth,
+                     int32_t T, hht_result *out);
 
 /*
  * Membership test of hht_detect and hht_detect_batch on this context.

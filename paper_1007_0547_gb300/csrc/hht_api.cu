@@ -148,6 +148,7 @@ void resolve_profile(hht_ctx* c) {
         switch (p.kind) {
             case 0: c->prof.stage_ms += ms; break;
             case 1: c->prof.select_ms += ms; break;
+            case 3: c->prof.edges_ms += ms; break;
             default: c->prof.pass_ms += ms; break;
         }
         c->ev_pool.push_back(p.a);
@@ -194,7 +195,9 @@ constexpr int kPassTile = 256 * 8;  // voters per pass block below which fewer b
 // of that on others).  $HHT_COPY_ENGINE=1 keeps every copy on the copy
 // engines.  Anything else (device memory, pageable host memory, unaligned or
 // small copies) goes through cudaMemcpyAsync.
-int copy_out(hht_ctx* c, void* dst, const void* src, size_t bytes) {
+}  // namespace
+
+int hht::copy_out(hht_ctx* c, void* dst, const void* src, size_t bytes) {
     constexpr size_t kKernelMin = 1u << 20;
     if (bytes >= kKernelMin && !c->copy_engine_only && ((uintptr_t)dst % 16) == 0 && ((uintptr_t)src % 16) == 0 &&
         bytes % 16 == 0) {
@@ -209,6 +212,8 @@ int copy_out(hht_ctx* c, void* dst, const void* src, size_t bytes) {
     CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream));
     return HHT_OK;
 }
+
+namespace {
 
 // The persistent launch, through a CUDA graph captured once per argument set
 // (replayed while the buffers and sizes are unchanged).  Capture is not
@@ -278,10 +283,13 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
             U.half = h;
             U.t0 = 0;
             U.root_rec = (uint32_t)(2 * g + h);
-            U.pad = 0;
+            // front-end split images: ALPHA points enter half 0 only, BETA half 1 only
+            const bool on = !c->job_halves || ((c->job_halves[job_first + g] >> h) & 1u);
+            U.inactive = on ? 0u : 1u;
+            if (!on) U.n = 0;
             U.pad2 = 0;
             U.v0_off = v0_len;
-            if (U.D >= 2) v0_len += (uint64_t)im[g].n;
+            if (U.D >= 2 && on) v0_len += (uint64_t)im[g].n;
         }
         total += (uint64_t)im[g].n;
     }
@@ -330,7 +338,8 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
     const bool fht = c->predicate == HHT_PREDICATE_FHT;
     if (fht && i64) return HHT_E_ARG;  // checked by the entry points before any device work
     const int occ_p = i64 ? c->occ_persistent64 : c->occ_persistent32;
-    const bool persistent = !fht && c->batch_mode == 1 && c->plan.valid && c->plan.sig == sig && occ_p > 0;
+    const bool persistent =
+        !fht && !c->job_halves && c->batch_mode == 1 && c->plan.valid && c->plan.sig == sig && occ_p > 0;
     uint64_t cap_rec = 0, cap_vox = 0, cap_tiles = 0;
     if (persistent) {
         cap_rec = std::max<uint64_t>(c->plan.cap_rec, (uint64_t)n_units);
@@ -671,12 +680,14 @@ int run_waves(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int 
     return rc_all;
 }
 
-int run_job(hht_ctx* c, const hht_image* im, int count, hht_result* outs) {
+int run_job(hht_ctx* c, const hht_image* im, int count, hht_result* outs, const uint8_t* halves = nullptr) {
+    c->job_halves = halves;
     c->job_off.assign(count, 0);
     c->job_n.assign(count, 0);
     c->job_leaves = 0;
     const int rc = run_waves(c, im, count, outs, 0);
     c->inject_tile = -1;  // an injected fault lasts one job
+    c->job_halves = nullptr;
     return rc;
 }
 
@@ -742,7 +753,8 @@ void hht_destroy(hht_ctx* c) {
     DevBuf* all[] = {&c->pts,       &c->img_start,  &c->img_unit, &c->units,        &c->stats,     &c->infos,      &c->status,
                      &c->leaf_total, &c->img_err,   &c->scan_states,  &c->rec[0],    &c->rec[1],     &c->preg[0],
                      &c->preg[1],   &c->cnt[0],     &c->cnt[1],       &c->vox[0],    &c->vox[1],     &c->leaves,
-                     &c->sel_flags, &c->sel_data,   &c->cursors};
+                     &c->sel_flags, &c->sel_data,   &c->cursors,      &c->img_buf,   &c->edge_pts[0],
+                     &c->edge_pts[1], &c->edge_tot};
     for (DevBuf* b : all) release(c, *b);
     delete c;
 }
@@ -937,6 +949,12 @@ const char* hht_version(void) {
 // Internal entry used by the serving loop.
 int hht_internal_run_job(hht_ctx* c, const hht_image* im, int count, hht_result* outs) {
     return run_job(c, im, count, outs);
+}
+
+// Internal entry used by the front end: halves[k] bit h set when half h of
+// image k takes its points (the caller holds the context's lock).
+int hht_internal_run_job_halves(hht_ctx* c, const hht_image* im, int count, hht_result* outs, const uint8_t* halves) {
+    return run_job(c, im, count, outs, halves);
 }
 
 hht::ServeState** hht_internal_serve_slot(hht_ctx* c) { return &c->serve; }

@@ -55,6 +55,9 @@ struct hht_ctx {
     int occ_shape[hht::kPassShapeCount] = {1, 1, 1, 1, 1, 1};  // resident blocks per SM of each shape
     int64_t inject_tile = -1;  // hht_inject_fault: selection tile withheld in the next job (-1 = none)
     int predicate = 0;         // HHT_PREDICATE_EXACT or HHT_PREDICATE_FHT (hht_detect / hht_detect_batch)
+    const uint8_t* job_halves = nullptr;  // during a job: per image, bit h set when half h takes its points
+    // front end (hht_edges, hht_detect_image): staged image, ALPHA and BETA point lists, their counts
+    DevBuf img_buf, edge_pts[2], edge_tot;
     int occ_pass_fht = 1;
 
     // job buffers
@@ -81,7 +84,7 @@ struct hht_ctx {
     std::vector<cudaEvent_t> ev_pool;
     struct Pending {
         cudaEvent_t a, b;
-        int kind;  // 0 stage, 1 select, 2 pass
+        int kind;  // 0 stage, 1 select, 2 pass, 3 front end
     };
     std::vector<Pending> pending;
 };
@@ -89,6 +92,9 @@ struct hht_ctx {
 
 namespace hht {
 int cuda_fail(cudaError_t e);
+// Copy leaves (or any 16-byte-aligned device data) to a caller's buffer on
+// the context's stream (hht_api.cu).
+int copy_out(hht_ctx* c, void* dst, const void* src, size_t bytes);
 // Grow a device buffer to at least `bytes` (contents are not kept; zeroed when asked).
 int ensure(hht_ctx* c, DevBuf& b, size_t bytes, bool zero = false);
 // Grow a device buffer keeping its first `keep` bytes.

@@ -41,7 +41,7 @@ struct alignas(16) Unit {
     int32_t half;      // 0: (x, y); 1: (y, x)
     int32_t t0;        // loop step at which the unit's level 0 is current
     uint32_t root_rec; // record index of the unit's level-0 region at step t0
-    uint32_t pad;
+    uint32_t inactive; // 1: this half takes none of the image's points (front-end split images)
     uint64_t pad2;
 };
 static_assert(sizeof(Unit) == 64, "unit record is 64 bytes");

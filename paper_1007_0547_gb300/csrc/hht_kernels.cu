@@ -109,9 +109,13 @@ __device__ __forceinline__ void stage_body(const int16_t* __restrict__ pts, uint
         }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const uint32_t u = active ? img_unit[img] + (uint32_t)h : 0u;
-            uint32_t key = (active && ok) ? u : kNoRegion;
-            if (active && !ok) {
+            const uint32_t u0 = active ? img_unit[img] + (uint32_t)h : 0u;
+            // a half that takes none of the image's points (its unit has no
+            // level-0 voters) behaves as past the end
+            const bool on = active && units[u0].inactive == 0u;
+            const uint32_t u = on ? u0 : 0u;
+            uint32_t key = (on && ok) ? u : kNoRegion;
+            if (on && !ok) {
                 // a point outside its image fails the image; its level-0 slot
                 // still gets a record, marked as belonging to no region, so
                 // that the stream holds no uninitialised entries
@@ -125,7 +129,7 @@ __device__ __forceinline__ void stage_body(const int16_t* __restrict__ pts, uint
                 }
             }
             uint32_t vals[2] = {0u, 0u};  // [0]: child votes as 4 bytes, [1]: level-0 votes
-            if (active && ok) {
+            if (on && ok) {
                 const Unit& U = units[u];
                 const int32_t x = h ? py : px, y = h ? px : py;
                 const int D = U.D, lL = U.lL;

@@ -32,7 +32,7 @@ HHT_E_UNKNOWN_TICKET = -8
 EXPORTS = ("hht_create", "hht_destroy", "hht_detect", "hht_detect_batch", "hht_fetch_leaves", "hht_submit",
            "hht_poll", "hht_progress", "hht_profile_enable", "hht_profile_read", "hht_strerror", "hht_version",
            "hht_detect_noalloc", "hht_autotune", "hht_set_tuning", "hht_set_batch_mode", "hht_fetch_all_leaves",
-           "hht_inject_fault", "hht_set_predicate")
+           "hht_inject_fault", "hht_set_predicate", "hht_edges", "hht_detect_image")
 BATCH_LEVELS, BATCH_PERSISTENT = 0, 1
 FAULT_NONE, FAULT_WITHHOLD_SCAN_TILE = 0, 1
 PREDICATE_EXACT, PREDICATE_FHT = 0, 1
@@ -56,7 +56,9 @@ class _Profile(ctypes.Structure):
                 ("select_launches", ctypes.c_uint64), ("voters_read", ctypes.c_uint64),
                 ("voters_written", ctypes.c_uint64), ("pass_bytes", ctypes.c_uint64), ("pass_ms", ctypes.c_double),
                 ("select_ms", ctypes.c_double), ("stage_ms", ctypes.c_double),
-                ("persistent_launches", ctypes.c_uint64), ("persistent_fallbacks", ctypes.c_uint64)]
+                ("persistent_launches", ctypes.c_uint64), ("persistent_fallbacks", ctypes.c_uint64),
+                ("edges_launches", ctypes.c_uint64), ("edges_pixels", ctypes.c_uint64),
+                ("edges_points", ctypes.c_uint64), ("edges_ms", ctypes.c_double)]
 
 
 class _Image(ctypes.Structure):
@@ -111,6 +113,10 @@ def load(path: Optional[str] = None):
     lib.hht_inject_fault.restype = ctypes.c_int
     lib.hht_set_predicate.argtypes = [vp, i32]
     lib.hht_set_predicate.restype = ctypes.c_int
+    lib.hht_edges.argtypes = [vp, vp, i32, i32, i32, vp, u64, ctypes.POINTER(u64), vp, u64, ctypes.POINTER(u64)]
+    lib.hht_edges.restype = ctypes.c_int
+    lib.hht_detect_image.argtypes = [vp, vp, i32, i32, i32, i32, i32, ctypes.POINTER(_Result)]
+    lib.hht_detect_image.restype = ctypes.c_int
     lib.hht_strerror.argtypes = [ctypes.c_int]
     lib.hht_strerror.restype = ctypes.c_char_p
     lib.hht_version.argtypes = []
@@ -392,6 +398,65 @@ class Context:
         return int(best.value), times
 
     # ------------------------------------------------------------ kernel timing
+    @staticmethod
+    def _image(image):
+        """A grey-level image (uint8 [H, W], numpy or torch, host or device) ->
+        (keep-alive, address, W, H)."""
+        try:
+            import torch
+            if isinstance(image, torch.Tensor):
+                if image.dtype != torch.uint8 or image.dim() != 2:
+                    raise ValueError("image must be a uint8 tensor of shape [H, W]")
+                t = image.contiguous()
+                return t, t.data_ptr(), int(t.shape[1]), int(t.shape[0])
+        except ImportError:  # pragma: no cover
+            pass
+        a = np.ascontiguousarray(image)
+        if a.dtype != np.uint8 or a.ndim != 2:
+            raise ValueError("image must be a uint8 array of shape [H, W]")
+        return a, a.ctypes.data, int(a.shape[1]), int(a.shape[0])
+
+    def edges(self, image, threshold: int, on_device: bool = True):
+        """Sobel edge points of a grey-level image split into ALPHA and BETA
+        (Section 3): two int16 [k, 2] (x, y) buffers, row-major order each."""
+        import torch
+        lib = load()
+        keep, ptr, W, H = self._image(image)
+        # one call with buffers that hold every interior pixel (the most either list can get)
+        cap = max(1, (W - 2) * (H - 2)) if W >= 3 and H >= 3 else 1
+        dev = f"cuda:{self.device}" if on_device else "cpu"
+        a = torch.empty((cap, 2), dtype=torch.int16, device=dev)
+        b = torch.empty((cap, 2), dtype=torch.int16, device=dev)
+        na, nb = ctypes.c_uint64(), ctypes.c_uint64()
+        rc = lib.hht_edges(self._h, ptr, W, H, int(threshold), a.data_ptr(), cap, ctypes.byref(na),
+                           b.data_ptr(), cap, ctypes.byref(nb))
+        if rc != HHT_OK:
+            raise HhtError(rc, "hht_edges")
+        del keep
+        return a[: int(na.value)], b[: int(nb.value)]
+
+    def detect_image(self, image, threshold: int, depth: int, T: int, leaves_on_device: bool = True,
+                     raise_on_error: bool = True) -> Result:
+        """Front end plus detection: Sobel edges split into ALPHA (half 0) and
+        BETA (half 1, x and y swapped), then the hierarchy on each."""
+        lib = load()
+        keep, ptr, W, H = self._image(image)
+        cap = int(self._cap_hint)
+        buf, lp = self._alloc_leaves(cap, leaves_on_device)
+        r = _Result()
+        r.leaves = lp
+        r.leaf_capacity = cap
+        rc = lib.hht_detect_image(self._h, ptr, W, H, int(threshold), int(depth), int(T), ctypes.byref(r))
+        if rc == HHT_E_CAPACITY:
+            self._cap_hint = max(self._cap_hint, int(r.n_leaves))
+            buf = self._fetch(0, int(r.n_leaves), leaves_on_device)
+            rc = HHT_OK
+        if rc != HHT_OK and raise_on_error:
+            raise HhtError(rc, "hht_detect_image")
+        del keep
+        k = int(r.n_leaves) if rc == HHT_OK else 0
+        return Result(buf[:k], _stats_of(r), int(r.depth), int(r.L), rc)
+
     def set_predicate(self, predicate: int) -> None:
         """PREDICATE_EXACT (the paper's 4-bit code) or PREDICATE_FHT (the
         prior-art circumscribed-circle test) for detect and detect_batch."""

@@ -29,7 +29,7 @@ def test_header_declares_the_api():
                                 "hht_submit", "hht_poll", "hht_progress", "hht_profile_enable", "hht_profile_read",
                                 "hht_strerror", "hht_version", "hht_detect_noalloc", "hht_autotune",
                                 "hht_set_tuning", "hht_set_batch_mode", "hht_fetch_all_leaves",
-                                "hht_inject_fault", "hht_set_predicate"}
+                                "hht_inject_fault", "hht_set_predicate", "hht_edges", "hht_detect_image"}
 
 
 def test_library_exports_every_declared_symbol(lib):
@@ -60,6 +60,9 @@ def test_host_only_calls(lib):
     assert lib.hht_autotune(None, None, 0, None, None) == hht.HHT_E_ARG
     assert lib.hht_inject_fault(None, hht.FAULT_WITHHOLD_SCAN_TILE, 0) == hht.HHT_E_ARG
     assert lib.hht_set_predicate(None, hht.PREDICATE_FHT) == hht.HHT_E_ARG
+    na, nb = ctypes.c_uint64(), ctypes.c_uint64()
+    assert lib.hht_edges(None, None, 8, 8, 10, None, 0, ctypes.byref(na), None, 0, ctypes.byref(nb)) == hht.HHT_E_ARG
+    assert lib.hht_detect_image(None, None, 8, 8, 10, 3, 1, ctypes.byref(r)) == hht.HHT_E_ARG
 
 
 def test_result_struct_layout_matches_header(lib):
