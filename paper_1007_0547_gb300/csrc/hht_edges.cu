@@ -13,10 +13,10 @@
 //
 // One kernel pass: tiles of 8192 consecutive pixels (row-major), claimed in
 // order; a tile stages its pixels and the rows above and below into shared
-// memory (three 8194-byte segments, coalesced word loads), classifies 32
-// pixels per thread with a sliding column window, and a single-pass decoupled
-// look-back scan of the two counts gives every tile its offsets in the two
-// lists; only edge pixels are then visited to write them.
+// memory (three 8194-byte segments, coalesced word loads), each warp walks
+// its 1024 pixels in steps of 32 (one pixel per lane), and a single-pass
+// decoupled look-back scan of the two counts gives every tile its offsets in
+// the two lists; only steps with edge pixels are visited to write them.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -36,9 +36,10 @@ namespace hht {
 namespace {
 
 constexpr int kEdgeTPB = 256;
-constexpr int kEdgePPT = 32;                    // pixels per thread
-constexpr int kEdgeTile = kEdgeTPB * kEdgePPT;  // pixels per tile (row-major, consecutive)
-constexpr int kEdgeSeg = kEdgeTile + 2;         // a row segment with one halo pixel on each side
+constexpr int kEdgeWarps = kEdgeTPB / 32;
+constexpr int kEdgeSteps = 32;                       // warp steps of 32 pixels per warp and tile
+constexpr int kEdgeTile = kEdgeTPB * kEdgeSteps;     // pixels per tile (row-major, consecutive)
+constexpr int kEdgeSeg = kEdgeTile + 2;              // a row segment with one halo pixel on each side
 constexpr int kEdgeSegWords = (kEdgeSeg + 3 + 3) / 4;  // 4-byte words covering a segment at any byte shift
 
 // Byte q of the image, 0 outside [0, npix).
@@ -46,21 +47,26 @@ __device__ __forceinline__ uint32_t pixel_or_zero(const uint8_t* __restrict__ im
     return (q >= 0 && q < npix) ? (uint32_t)__ldg(img + q) : 0u;
 }
 
+// Warp w of a tile owns its pixels [w * 1024, (w + 1) * 1024): step s covers
+// 32 consecutive pixels, one per lane, so the lanes read consecutive bytes of
+// shared memory (no bank conflicts).  A step's edge pixels come out of two
+// ballots; lane s keeps step s's masks, so one warp scan orders the steps.
 __global__ void __launch_bounds__(kEdgeTPB) edges_kernel(const uint8_t* __restrict__ img, int32_t W, int32_t H,
                                                          int32_t thr2, uint32_t* __restrict__ out_a,
                                                          uint32_t* __restrict__ out_b, uint64_t cap,
                                                          unsigned long long* __restrict__ tot, ScanState* scan,
                                                          uint32_t* flags, uint64_t* data, DeviceStatus* status,
                                                          uint32_t ntiles) {
-    // seg[r] holds the image bytes from (p0 + (r - 1) * W - 1) rounded down to
-    // a 4-byte boundary; byte k of segment r is segb[r][shift[r] + k]
+    // segw[r] holds the image bytes from (p0 + (r - 1) * W - 1) rounded down
+    // to a 4-byte boundary; byte k of segment r is segb[r][shift[r] + k]
     __shared__ uint32_t segw[3][kEdgeSegWords];
     __shared__ uint32_t s_slot;
-    __shared__ uint32_t s_wa[kEdgeTPB / 32], s_wb[kEdgeTPB / 32];
+    __shared__ uint32_t s_wa[kEdgeWarps], s_wb[kEdgeWarps];
     __shared__ uint64_t s_pre[2];
     __shared__ unsigned long long s_na, s_nb;
     const uint8_t(*segb)[kEdgeSegWords * 4] = reinterpret_cast<const uint8_t(*)[kEdgeSegWords * 4]>(segw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
     const int64_t npix = (int64_t)W * H;
     const bool aligned = ((uintptr_t)img & 3u) == 0u;
     if (tid == 0) {
@@ -92,77 +98,70 @@ __global__ void __launch_bounds__(kEdgeTPB) edges_kernel(const uint8_t* __restri
         }
         __syncthreads();
 
-        // classify this thread's 32 pixels with a sliding window over the
-        // linear positions i - 1, i, i + 1 (the pixel's left and right
-        // neighbours whenever it is an interior pixel): column sums
-        // c = above + 2 * middle + below give gx = c(i+1) - c(i-1), row
-        // differences d = below - above give gy = d(i-1) + 2 d(i) + d(i+1)
-        const int64_t q0 = p0 + (int64_t)tid * kEdgePPT;
-        const int32_t y0 = (int32_t)(q0 / W), x0 = (int32_t)(q0 - (int64_t)y0 * W);
-        const int ib = tid * kEdgePPT;
-        auto column = [&](int i, int32_t& cc, int32_t& dd) {
-            const int32_t a = segb[0][shift[0] + i], m = segb[1][shift[1] + i], b = segb[2][shift[2] + i];
-            cc = a + 2 * m + b;
-            dd = b - a;
-        };
-        int32_t cp, dp, cc, dc;
-        column(ib, cp, dp);      // position i - 1 for the first pixel
-        column(ib + 1, cc, dc);  // position i
-        uint32_t is_edge = 0, is_alpha = 0;
-        {
-            int32_t x = x0, y = y0;
-#pragma unroll 8
-            for (int j = 0; j < kEdgePPT; ++j) {
-                int32_t cn, dn;
-                column(ib + j + 2, cn, dn);  // position i + 1
-                const int32_t gx = cn - cp;
-                const int32_t gy = dp + 2 * dc + dn;
-                const bool inside = q0 + j < npix && x >= 1 && x <= W - 2 && y >= 1 && y <= H - 2;
-                const bool edge = inside && gx * gx + gy * gy >= thr2;
-                is_edge |= (edge ? 1u : 0u) << j;
-                is_alpha |= (edge && abs(gx) <= abs(gy) ? 1u : 0u) << j;
-                cp = cc;
-                dp = dc;
-                cc = cn;
-                dc = dn;
-                if (++x == W) {
-                    x = 0;
-                    ++y;
-                }
+        // classify: pixel i = base + 32 s + lane of the tile; its neighbours
+        // at linear positions i - 1 and i + 1 are its left and right pixels
+        // whenever it is an interior pixel
+        const int base = warp * (32 * kEdgeSteps);
+        const int64_t qw = p0 + base + lane;  // this lane's pixel at step 0
+        int32_t y = (int32_t)(qw / W), x = (int32_t)(qw - (int64_t)y * W);
+        const int32_t step_y = 32 / W, step_x = 32 - step_y * W;  // (x, y) advance of 32 pixels
+        uint32_t my_a = 0, my_b = 0;  // lane s: step s's ALPHA and BETA masks
+#pragma unroll 4
+        for (int s = 0; s < kEdgeSteps; ++s) {
+            const int i = base + 32 * s + lane;
+            const int32_t a0 = segb[0][shift[0] + i], a1 = segb[0][shift[0] + i + 1], a2 = segb[0][shift[0] + i + 2];
+            const int32_t m0 = segb[1][shift[1] + i], m2 = segb[1][shift[1] + i + 2];
+            const int32_t b0 = segb[2][shift[2] + i], b1 = segb[2][shift[2] + i + 1], b2 = segb[2][shift[2] + i + 2];
+            const int32_t gx = (a2 + 2 * m2 + b2) - (a0 + 2 * m0 + b0);
+            const int32_t gy = (b0 + 2 * b1 + b2) - (a0 + 2 * a1 + a2);
+            const bool inside = qw + 32 * s < npix && x >= 1 && x <= W - 2 && y >= 1 && y <= H - 2;
+            const bool edge = inside && gx * gx + gy * gy >= thr2;
+            const bool alpha = edge && abs(gx) <= abs(gy);
+            const uint32_t ma = __ballot_sync(0xffffffffu, alpha);
+            const uint32_t mb = __ballot_sync(0xffffffffu, edge && !alpha);
+            if (lane == s) {
+                my_a = ma;
+                my_b = mb;
+            }
+            x += step_x;
+            y += step_y;
+            if (x >= W) {
+                x -= W;
+                ++y;
             }
         }
-        const uint32_t ca = __popc(is_alpha), cb = __popc(is_edge & ~is_alpha);
 
-        // offsets: warp scan, block scan, then the tile's look-back
-        uint32_t ia = ca, ibb = cb;
+        // offsets: scan of the steps within the warp, block scan, then the look-back
+        const uint32_t ca = __popc(my_a), cb = __popc(my_b);
+        uint32_t ia = ca, ib = cb;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
-            const uint32_t ua = __shfl_up_sync(0xffffffffu, ia, off), ub = __shfl_up_sync(0xffffffffu, ibb, off);
+            const uint32_t ua = __shfl_up_sync(0xffffffffu, ia, off), ub = __shfl_up_sync(0xffffffffu, ib, off);
             if (lane >= off) {
                 ia += ua;
-                ibb += ub;
+                ib += ub;
             }
         }
         if (lane == 31) {
             s_wa[warp] = ia;
-            s_wb[warp] = ibb;
+            s_wb[warp] = ib;
         }
         __syncthreads();
         if (warp == 0) {
-            constexpr int NW = kEdgeTPB / 32;
-            const uint32_t wa = lane < NW ? s_wa[lane] : 0u, wb = lane < NW ? s_wb[lane] : 0u;
+            const uint32_t wa = lane < kEdgeWarps ? s_wa[lane] : 0u, wb = lane < kEdgeWarps ? s_wb[lane] : 0u;
             uint32_t ja = wa, jb = wb;
 #pragma unroll
-            for (int off = 1; off < NW; off <<= 1) {
+            for (int off = 1; off < kEdgeWarps; off <<= 1) {
                 const uint32_t ua = __shfl_up_sync(0xffffffffu, ja, off), ub = __shfl_up_sync(0xffffffffu, jb, off);
                 if (lane >= off) {
                     ja += ua;
                     jb += ub;
                 }
             }
-            const uint64_t agg[2] = {__shfl_sync(0xffffffffu, ja, NW - 1), __shfl_sync(0xffffffffu, jb, NW - 1)};
+            const uint64_t agg[2] = {__shfl_sync(0xffffffffu, ja, kEdgeWarps - 1),
+                                     __shfl_sync(0xffffffffu, jb, kEdgeWarps - 1)};
             __syncwarp();
-            if (lane < NW) {
+            if (lane < kEdgeWarps) {
                 s_wa[lane] = ja - wa;
                 s_wb[lane] = jb - wb;
             }
@@ -176,24 +175,27 @@ __global__ void __launch_bounds__(kEdgeTPB) edges_kernel(const uint8_t* __restri
             }
         }
         __syncthreads();
-        // write the edge pixels only, in order
-        uint64_t oa = s_pre[0] + s_wa[warp] + (ia - ca), ob = s_pre[1] + s_wb[warp] + (ibb - cb);
-        uint32_t rest = is_edge;
-        while (rest) {
-            const int j = __ffs(rest) - 1;
-            rest &= rest - 1u;
-            int32_t x = x0 + j, y = y0;
-            while (x >= W) {  // at most kEdgePPT / W + 1 rows on
-                x -= W;
-                ++y;
-            }
-            const uint32_t pt = ((uint32_t)x & 0xffffu) | ((uint32_t)y << 16);  // hht_point {x, y}
-            if ((is_alpha >> j) & 1u) {
-                if (oa < cap) out_a[oa] = pt;
-                ++oa;
-            } else {
-                if (ob < cap) out_b[ob] = pt;
-                ++ob;
+        // write: step s's edge pixels follow the earlier steps' (exclusive scan
+        // ia - ca), lanes in order within the step
+        const uint64_t oa0 = s_pre[0] + s_wa[warp], ob0 = s_pre[1] + s_wb[warp];
+        uint32_t steps_with_edges = __ballot_sync(0xffffffffu, (my_a | my_b) != 0u);
+        while (steps_with_edges) {
+            const int s = __ffs(steps_with_edges) - 1;
+            steps_with_edges &= steps_with_edges - 1u;
+            const uint32_t ma = __shfl_sync(0xffffffffu, my_a, s), mb = __shfl_sync(0xffffffffu, my_b, s);
+            const uint32_t ea = __shfl_sync(0xffffffffu, ia - ca, s), eb = __shfl_sync(0xffffffffu, ib - cb, s);
+            const bool wa = (ma >> lane) & 1u, wb = (mb >> lane) & 1u;
+            if (wa || wb) {
+                const int64_t q = p0 + base + 32 * s + lane;
+                const int32_t yy = (int32_t)(q / W), xx = (int32_t)(q - (int64_t)yy * W);
+                const uint32_t pt = ((uint32_t)xx & 0xffffu) | ((uint32_t)yy << 16);  // hht_point {x, y}
+                if (wa) {
+                    const uint64_t o = oa0 + ea + __popc(ma & lt);
+                    if (o < cap) out_a[o] = pt;
+                } else {
+                    const uint64_t o = ob0 + eb + __popc(mb & lt);
+                    if (o < cap) out_b[o] = pt;
+                }
             }
         }
     }

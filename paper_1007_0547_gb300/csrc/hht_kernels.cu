@@ -691,14 +691,14 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
                 settle();
                 start_run(r_first);
             }
-            uint32_t kw[kChunkSteps];
+            uint32_t kw[kChunkSteps], gv[kChunkSteps];
             uint32_t cnt = 0;
 #pragma unroll
             for (int k = 0; k < kChunkSteps; ++k) {
                 const uint32_t live = rec[k].y != kNoRegion ? 0xffffffffu : 0u;
                 const Classified<I> c = classify<I>(cg, rec[k].x);
                 kw[k] = c.kw & live;
-                add_rows(rows, c.gv & live);
+                gv[k] = c.gv & live;
                 cnt += quad_counts(kw[k]);
             }
             // reserve each kept child's slots for the whole chunk (one atomic
@@ -712,17 +712,17 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
                 if (lane >= off) inc += o;
             }
             const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
-            // lanes 0..3 reserve the slots of quadrant `lane` in parallel
+            // lanes 0..3 reserve the slots of quadrant `lane` in parallel; the
+            // grandchild counts are added while the reservations are in flight
             unsigned long long mybase = 0;
-            bool over = false;
-            if (lane < 4) {
-                const uint32_t tq = (tot >> (8 * quad_byte_rt(lane))) & 0xffu;
+            const uint32_t tq_mine = lane < 4 ? (tot >> (8 * quad_byte_rt(lane))) & 0xffu : 0u;
+            if (tq_mine) {
                 const uint32_t cq = lane == 0 ? ci[0] : lane == 1 ? ci[1] : lane == 2 ? ci[2] : ci[3];
-                if (tq) {
-                    mybase = atomicAdd(&a.cursor[cq], (unsigned long long)tq);
-                    over = mybase + tq > a.cap_voters;
-                }
+                mybase = atomicAdd(&a.cursor[cq], (unsigned long long)tq_mine);
             }
+#pragma unroll
+            for (int k = 0; k < kChunkSteps; ++k) add_rows(rows, gv[k]);
+            const bool over = tq_mine && mybase + tq_mine > a.cap_voters;
             const bool any_over = __any_sync(0xffffffffu, over);
             steps += kChunkSteps;
             if (steps >= 255 - kChunkSteps) settle();  // byte counters nearly full
