@@ -15,6 +15,10 @@ from .oracle import (  # noqa: F401
     sobel,
     edges,
     detect_split,
+    lines,
+    line_parameters,
+    centroid_parameters,
+    LINE_DTYPE,
     OracleResult,
     STAT_TESTED,
     STAT_PASSED,

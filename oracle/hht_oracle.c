@@ -331,3 +331,76 @@ int oracle_edges(const uint8_t *img, int32_t W, int32_t H, int32_t threshold, in
     *n_beta = nb;
     return (na > alpha_cap || nb > beta_cap) ? ORACLE_E_CAPACITY : ORACLE_OK;
 }
+
+/*
+ * Leaves -> lines (the paper stops at the peak cells; this step is a reading
+ * of its own).  Leaves of the same half whose cells touch (|di| <= 1 and
+ * |dj| <= 1) belong to one cluster (connected components of that adjacency).
+ * Each cluster is one line: its peak is the leaf with the most votes, ties
+ * going to the leaf that comes first in the input (depth-first) order.  The
+ * line of peak cell (i, j) is the cell's centre in parameter space,
+ *   m = (2i + 1 - K) / K,   b = 2L (2j + 1 - K) / K,
+ * read as y = m x + b for half 0 and as x = m y + b for half 1 (Section 3:
+ * BETA points were processed with x and y swapped).  A cluster also gives
+ * its vote-weighted centre, kept exact as integer sums: with V the total
+ * votes, S_i = sum of votes * (2i + 1) and S_j = sum of votes * (2j + 1),
+ *   m = (S_i / V - K) / K,   b = 2L (S_j / V - K) / K,
+ * which lands between cells when several share the peak.  Lines are reported
+ * in the order of each cluster's first leaf.
+ */
+typedef struct {
+    uint32_t half, i, j, votes, cells, pad;
+    uint64_t total_votes, sum_i2, sum_j2;
+} oracle_line;
+
+static int64_t uf_find(int64_t *parent, int64_t a)
+{
+    while (parent[a] != a) a = parent[a];
+    return a;
+}
+
+int oracle_lines(const oracle_leaf *leaves, int64_t n, oracle_line *out, int64_t cap, int64_t *n_lines)
+{
+    if (n < 0 || (n > 0 && !leaves) || !n_lines) return ORACLE_E_ARG;
+    int64_t *parent = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t *line_of = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    if (!parent || !line_of) { free(parent); free(line_of); return ORACLE_E_NOMEM; }
+    for (int64_t k = 0; k < n; ++k) parent[k] = k;
+    /* every pair of touching leaves (quadratic: the oracle runs on small sets) */
+    for (int64_t a = 0; a < n; ++a)
+        for (int64_t b = a + 1; b < n; ++b) {
+            if (leaves[a].half != leaves[b].half) continue;
+            const int64_t di = (int64_t)leaves[a].i - (int64_t)leaves[b].i;
+            const int64_t dj = (int64_t)leaves[a].j - (int64_t)leaves[b].j;
+            if (di < -1 || di > 1 || dj < -1 || dj > 1) continue;
+            const int64_t ra = uf_find(parent, a), rb = uf_find(parent, b);
+            if (ra != rb) parent[ra > rb ? ra : rb] = ra < rb ? ra : rb;
+        }
+    int64_t nl = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        const int64_t r = uf_find(parent, k);
+        if (r == k) {
+            line_of[k] = nl;
+            if (nl < cap) {
+                oracle_line *L = &out[nl];
+                L->half = leaves[k].half; L->i = leaves[k].i; L->j = leaves[k].j; L->votes = leaves[k].votes;
+                L->cells = 0; L->pad = 0; L->total_votes = 0; L->sum_i2 = 0; L->sum_j2 = 0;
+            }
+            ++nl;
+        }
+        const int64_t id = line_of[r];
+        if (id < cap) {
+            oracle_line *L = &out[id];
+            L->cells += 1;
+            L->total_votes += leaves[k].votes;
+            L->sum_i2 += (uint64_t)leaves[k].votes * (2u * (uint64_t)leaves[k].i + 1u);
+            L->sum_j2 += (uint64_t)leaves[k].votes * (2u * (uint64_t)leaves[k].j + 1u);
+            if (leaves[k].votes > L->votes) { /* strictly more: ties keep the earlier leaf */
+                L->i = leaves[k].i; L->j = leaves[k].j; L->votes = leaves[k].votes;
+            }
+        }
+    }
+    *n_lines = nl;
+    free(parent); free(line_of);
+    return nl > cap ? ORACLE_E_CAPACITY : ORACLE_OK;
+}

@@ -82,6 +82,9 @@ def _load():
                                          ctypes.POINTER(ctypes.c_int64), i16p, ctypes.c_int64,
                                          ctypes.POINTER(ctypes.c_int64)]
             lib.oracle_edges.restype = ctypes.c_int
+            lib.oracle_lines.argtypes = [ctypes.POINTER(_Leaf), ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                         ctypes.POINTER(ctypes.c_int64)]
+            lib.oracle_lines.restype = ctypes.c_int
             lib.oracle_frame_side.argtypes = [ctypes.c_int32, ctypes.c_int32]
             lib.oracle_frame_side.restype = ctypes.c_int64
             _lib = lib
@@ -206,3 +209,42 @@ def detect_split(alpha: np.ndarray, beta: np.ndarray, W: int, H: int, depth: int
     lb = rb.leaves[rb.leaves[:, 0] == 1] if len(rb.leaves) else rb.leaves
     stats = np.stack([ra.stats[0], rb.stats[1]])
     return OracleResult(np.ascontiguousarray(np.concatenate([la, lb]).reshape(-1, 4)), stats, None, 0)
+
+
+LINE_DTYPE = np.dtype([("half", np.uint32), ("i", np.uint32), ("j", np.uint32), ("votes", np.uint32),
+                       ("cells", np.uint32), ("pad", np.uint32), ("total_votes", np.uint64),
+                       ("sum_i2", np.uint64), ("sum_j2", np.uint64)])
+
+
+def lines(leaves: np.ndarray) -> np.ndarray:
+    """Clusters of touching leaves (same half, 8-neighbourhood) -> one line
+    each: structured array with the peak cell (half, i, j, votes; ties to the
+    earlier leaf), the cluster's cell count and total votes, in the order of
+    each cluster's first leaf.  Quadratic: for small leaf sets."""
+    lv = np.ascontiguousarray(np.asarray(leaves, dtype=np.uint32).reshape(-1, 4))
+    n = lv.shape[0]
+    out = np.zeros(max(n, 1), dtype=LINE_DTYPE)
+    nl = ctypes.c_int64()
+    rc = _load().oracle_lines(lv.ctypes.data_as(ctypes.POINTER(_Leaf)), n, out.ctypes.data, max(n, 1),
+                              ctypes.byref(nl))
+    if rc != 0:
+        raise ValueError(f"oracle.lines failed with code {rc}")
+    return out[: nl.value].copy()
+
+
+def line_parameters(half: int, i: int, j: int, depth: int, L: int):
+    """Image line of leaf cell (i, j): its centre (m, b) as exact fractions
+    m = (2i + 1 - K) / K and b = 2L (2j + 1 - K) / K; half 0 reads y = m x + b,
+    half 1 reads x = m y + b."""
+    from fractions import Fraction
+    K = 1 << depth
+    return Fraction(2 * i + 1 - K, K), Fraction(2 * L * (2 * j + 1 - K), K)
+
+
+def centroid_parameters(line, depth: int, L: int):
+    """A cluster's vote-weighted centre (m, b) as exact fractions:
+    m = (S_i / V - K) / K, b = 2L (S_j / V - K) / K."""
+    from fractions import Fraction
+    K = 1 << depth
+    V = int(line["total_votes"])
+    return (Fraction(int(line["sum_i2"]), V) - K) / K, 2 * L * (Fraction(int(line["sum_j2"]), V) - K) / K
