@@ -296,6 +296,32 @@ int hht_detect_image(hht_ctx *ctx, const uint8_t *image, int32_t W, int32_t H, i
                      int32_t T, hht_result *out);
 
 /*
+ * Leaves -> lines (no paper counterpart: the paper stops at the peak cells;
+ * this step is this library's own reading).  For image `index` of the last
+ * job on the context (0 for hht_detect and hht_detect_image), leaves of the
+ * same half whose cells touch (|di| <= 1 and |dj| <= 1) form one cluster, and
+ * each cluster is one line, reported in the order of its first leaf in the
+ * depth-first leaf order:
+ *   - half, i, j, votes: its peak leaf (most votes; ties to the earlier leaf);
+ *   - cells: leaves in the cluster; total_votes: V, their summed votes;
+ *   - sum_i2 = sum of votes * (2i + 1), sum_j2 = sum of votes * (2j + 1): the
+ *     exact vote-weighted centre m = (sum_i2 / V - K) / K,
+ *     b = 2L (sum_j2 / V - K) / K (K = 2^depth, L the frame side).
+ * A cell's own centre is m = (2i + 1 - K) / K, b = 2L (2j + 1 - K) / K.  Half 0
+ * lines read y = m x + b; half 1 lines x = m y + b (x and y swapped back).
+ * `lines` is host or device memory of `capacity` entries; *n_lines receives
+ * the count.  With capacity < count nothing is copied and HHT_E_CAPACITY is
+ * returned (call again with a larger buffer).  Errors: HHT_E_ARG (NULL, no
+ * such image), HHT_E_CAPACITY, HHT_E_NOMEM, HHT_E_CUDA.
+ */
+typedef struct {
+    uint32_t half, i, j, votes;
+    uint32_t cells, reserved;
+    uint64_t total_votes, sum_i2, sum_j2;
+} hht_line;
+int hht_lines(hht_ctx *ctx, int32_t index, hht_line *lines, uint64_t capacity, uint64_t *n_lines);
+
+/*
  * Membership test of hht_detect and hht_detect_batch on this context.
  * HHT_PREDICATE_EXACT (default): the paper's 4-bit corner code (Section 2).
  * HHT_PREDICATE_FHT: the circumscribed-circle test of the Fast Hough

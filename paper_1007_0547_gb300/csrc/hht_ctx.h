@@ -58,6 +58,8 @@ struct hht_ctx {
     const uint8_t* job_halves = nullptr;  // during a job: per image, bit h set when half h takes its points
     // front end (hht_edges, hht_detect_image): staged image, ALPHA and BETA point lists, their counts
     DevBuf img_buf, edge_pts[2], edge_tot;
+    // leaves -> lines (hht_lines): hash table, union-find parents, per-root sums, output
+    DevBuf line_keys, line_vals, line_parent, line_cells, line_sums, line_out;
     int occ_pass_fht = 1;
 
     // job buffers

@@ -32,7 +32,7 @@ HHT_E_UNKNOWN_TICKET = -8
 EXPORTS = ("hht_create", "hht_destroy", "hht_detect", "hht_detect_batch", "hht_fetch_leaves", "hht_submit",
            "hht_poll", "hht_progress", "hht_profile_enable", "hht_profile_read", "hht_strerror", "hht_version",
            "hht_detect_noalloc", "hht_autotune", "hht_set_tuning", "hht_set_batch_mode", "hht_fetch_all_leaves",
-           "hht_inject_fault", "hht_set_predicate", "hht_edges", "hht_detect_image")
+           "hht_inject_fault", "hht_set_predicate", "hht_edges", "hht_detect_image", "hht_lines")
 BATCH_LEVELS, BATCH_PERSISTENT = 0, 1
 FAULT_NONE, FAULT_WITHHOLD_SCAN_TILE = 0, 1
 PREDICATE_EXACT, PREDICATE_FHT = 0, 1
@@ -59,6 +59,17 @@ class _Profile(ctypes.Structure):
                 ("persistent_launches", ctypes.c_uint64), ("persistent_fallbacks", ctypes.c_uint64),
                 ("edges_launches", ctypes.c_uint64), ("edges_pixels", ctypes.c_uint64),
                 ("edges_points", ctypes.c_uint64), ("edges_ms", ctypes.c_double)]
+
+
+class _Line(ctypes.Structure):
+    _fields_ = [("half", ctypes.c_uint32), ("i", ctypes.c_uint32), ("j", ctypes.c_uint32), ("votes", ctypes.c_uint32),
+                ("cells", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("total_votes", ctypes.c_uint64),
+                ("sum_i2", ctypes.c_uint64), ("sum_j2", ctypes.c_uint64)]
+
+
+LINE_DTYPE = np.dtype([("half", np.uint32), ("i", np.uint32), ("j", np.uint32), ("votes", np.uint32),
+                       ("cells", np.uint32), ("reserved", np.uint32), ("total_votes", np.uint64),
+                       ("sum_i2", np.uint64), ("sum_j2", np.uint64)])
 
 
 class _Image(ctypes.Structure):
@@ -113,6 +124,8 @@ def load(path: Optional[str] = None):
     lib.hht_inject_fault.restype = ctypes.c_int
     lib.hht_set_predicate.argtypes = [vp, i32]
     lib.hht_set_predicate.restype = ctypes.c_int
+    lib.hht_lines.argtypes = [vp, i32, vp, u64, ctypes.POINTER(u64)]
+    lib.hht_lines.restype = ctypes.c_int
     lib.hht_edges.argtypes = [vp, vp, i32, i32, i32, vp, u64, ctypes.POINTER(u64), vp, u64, ctypes.POINTER(u64)]
     lib.hht_edges.restype = ctypes.c_int
     lib.hht_detect_image.argtypes = [vp, vp, i32, i32, i32, i32, i32, ctypes.POINTER(_Result)]
@@ -456,6 +469,21 @@ class Context:
         del keep
         k = int(r.n_leaves) if rc == HHT_OK else 0
         return Result(buf[:k], _stats_of(r), int(r.depth), int(r.L), rc)
+
+    def lines(self, index: int = 0) -> np.ndarray:
+        """Lines of image `index` of the last job (hht_lines): a structured
+        numpy array (LINE_DTYPE) with each cluster's peak leaf, cell count,
+        total votes and the sums of its vote-weighted centre."""
+        lib = load()
+        n = ctypes.c_uint64()
+        rc = lib.hht_lines(self._h, int(index), None, 0, ctypes.byref(n))
+        if rc not in (HHT_OK, HHT_E_CAPACITY):
+            raise HhtError(rc, "hht_lines")
+        out = np.zeros(max(int(n.value), 1), dtype=LINE_DTYPE)
+        rc = lib.hht_lines(self._h, int(index), out.ctypes.data, len(out), ctypes.byref(n))
+        if rc != HHT_OK:
+            raise HhtError(rc, "hht_lines")
+        return out[: int(n.value)]
 
     def set_predicate(self, predicate: int) -> None:
         """PREDICATE_EXACT (the paper's 4-bit code) or PREDICATE_FHT (the

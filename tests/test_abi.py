@@ -29,7 +29,8 @@ def test_header_declares_the_api():
                                 "hht_submit", "hht_poll", "hht_progress", "hht_profile_enable", "hht_profile_read",
                                 "hht_strerror", "hht_version", "hht_detect_noalloc", "hht_autotune",
                                 "hht_set_tuning", "hht_set_batch_mode", "hht_fetch_all_leaves",
-                                "hht_inject_fault", "hht_set_predicate", "hht_edges", "hht_detect_image"}
+                                "hht_inject_fault", "hht_set_predicate", "hht_edges", "hht_detect_image",
+                                "hht_lines"}
 
 
 def test_library_exports_every_declared_symbol(lib):
@@ -63,6 +64,7 @@ def test_host_only_calls(lib):
     na, nb = ctypes.c_uint64(), ctypes.c_uint64()
     assert lib.hht_edges(None, None, 8, 8, 10, None, 0, ctypes.byref(na), None, 0, ctypes.byref(nb)) == hht.HHT_E_ARG
     assert lib.hht_detect_image(None, None, 8, 8, 10, 3, 1, ctypes.byref(r)) == hht.HHT_E_ARG
+    assert lib.hht_lines(None, 0, None, 0, ctypes.byref(na)) == hht.HHT_E_ARG
 
 
 def test_result_struct_layout_matches_header(lib):
@@ -106,7 +108,8 @@ def test_binding_structs_match_the_header_as_compiled(tmp_path):
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    mirrors = {"hht_result": hht._Result, "hht_image": hht._Image, "hht_profile_counters": hht._Profile}
+    mirrors = {"hht_result": hht._Result, "hht_image": hht._Image, "hht_profile_counters": hht._Profile,
+               "hht_line": hht._Line}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hht.h"', 'int main(void) {']
     for cname, py in mirrors.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
