@@ -250,6 +250,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-persistent", action="store_true")
     ap.add_argument("--no-fht", action="store_true", help="skip the prior-art FHT circle-test comparison")
+    ap.add_argument("--no-front-end", action="store_true", help="skip the front-end and line-extraction timings")
     ap.add_argument("--serve", action="store_true", help="open-loop serving benchmark instead of the batch line")
     ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--serve-load", type=float, default=0.8, help="offered rate as a fraction of the saturated rate")
@@ -443,6 +444,41 @@ def main():
                "votes": votes_fht, "votes_exact": votes_exact, "C_v": votes_fht / max(1, votes_exact),
                "C_t": fm / (total_ms / args.steps), "leaves": int(sum(r.n_leaves for r in fres))}
 
+    # ---------------------------------------------------------------- front end and lines (4096^2 grey image)
+    front = None
+    if not args.no_front_end and rank == 0:
+        g = synth.gray_4096()
+        gimg = torch.from_numpy(g.pixels).to(dev)
+        for _ in range(3):
+            ctx.edges(gimg, g.threshold)
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        for _ in range(5):
+            flush.zero_()
+            ea, eb = ctx.edges(gimg, g.threshold)
+        fp = ctx.profile_read()
+        ctx.profile(False)
+        e_ms = fp["edges_ms"] / max(1, fp["edges_launches"])
+        e_bytes = g.W * g.H + 4 * (len(ea) + len(eb))
+        d_ms, l_ms = [], []
+        for _ in range(3):
+            flush.zero_()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            dres = ctx.detect_image(gimg, g.threshold, g.depth, g.T)
+            e1.record(stream)
+            glines = ctx.lines(0)
+            e2.record(stream)
+            e2.synchronize()
+            d_ms.append(e0.elapsed_time(e1))
+            l_ms.append(e1.elapsed_time(e2))
+        front = {"workload": "gray_4096 (4096x4096 grey image, Sobel threshold 200, depth 12, T = 128)",
+                 "edges_kernel_ms": e_ms, "edges_points": int(len(ea) + len(eb)),
+                 "edges_algorithmic_GBps": e_bytes / (e_ms / 1e3) / 1e9,
+                 "edges_hbm_frac": e_bytes / (e_ms / 1e3) / 1e9 / read_peaks()[0],
+                 "detect_image_ms": min(d_ms), "detect_image_tests": int(dres.total_tests()),
+                 "leaves": int(dres.n_leaves), "lines_ms": min(l_ms), "lines": int(len(glines))}
+
     # ---------------------------------------------------------------- roofline of the pass kernel
     peak, peak_kind = read_peaks()
     achieved = (prof["pass_bytes"] / 1e9) / (prof["pass_ms"] / 1e3) if prof["pass_ms"] > 0 else 0.0
@@ -477,6 +513,7 @@ def main():
         "per_image_sequence": per_image,
         "persistent_form": persistent,
         "fht_form": fht,
+        "front_end": front,
         "e2e": e2e,
         "roofline": roofline,
         "cpu_baseline": cpu,
