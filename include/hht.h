@@ -311,8 +311,10 @@ int hht_detect_image(hht_ctx *ctx, const uint8_t *image, int32_t W, int32_t H, i
  * lines read y = m x + b; half 1 lines x = m y + b (x and y swapped back).
  * `lines` is host or device memory of `capacity` entries; *n_lines receives
  * the count.  With capacity < count nothing is copied and HHT_E_CAPACITY is
- * returned (call again with a larger buffer).  Errors: HHT_E_ARG (NULL, no
- * such image), HHT_E_CAPACITY, HHT_E_NOMEM, HHT_E_CUDA.
+ * returned; the lines stay in the context, so a second call for the same
+ * image (before the next detection) only copies them.  Errors: HHT_E_ARG
+ * (NULL, no such image), HHT_E_CAPACITY, HHT_E_NOMEM, HHT_E_TIMEOUT,
+ * HHT_E_CUDA.
  */
 typedef struct {
     uint32_t half, i, j, votes;

@@ -682,6 +682,7 @@ int run_waves(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int 
 
 int run_job(hht_ctx* c, const hht_image* im, int count, hht_result* outs, const uint8_t* halves = nullptr) {
     c->job_halves = halves;
+    c->job_serial += 1;
     c->job_off.assign(count, 0);
     c->job_n.assign(count, 0);
     c->job_leaves = 0;

@@ -60,6 +60,10 @@ struct hht_ctx {
     DevBuf img_buf, edge_pts[2], edge_tot;
     // leaves -> lines (hht_lines): hash table, union-find parents, per-root sums, output
     DevBuf line_keys, line_vals, line_parent, line_cells, line_sums, line_out;
+    uint64_t job_serial = 0;    // detection jobs run on the context (results of hht_lines refer to one)
+    uint64_t lines_serial = ~0ull;  // job and image whose lines line_out holds
+    int32_t lines_index = -1;
+    uint64_t lines_count = 0;
     int occ_pass_fht = 1;
 
     // job buffers

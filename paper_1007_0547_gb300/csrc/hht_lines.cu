@@ -18,7 +18,8 @@
 //      always hooking the larger root under the smaller one, so parent chains
 //      strictly decrease and the root of a cluster is its first leaf;
 //   3. per root: cells, votes, centre sums (atomic adds) and the peak (one
-//      64-bit atomic max of votes and the complemented leaf index);
+//      64-bit atomic max of votes and the complemented leaf index), after a
+//      warp-level reduction of runs of leaves with the same root;
 //   4. roots compacted in index order (block scan and the look-back scan).
 #include <cuda_runtime.h>
 
@@ -135,18 +136,55 @@ __global__ void lines_union_kernel(const DevLeaf* __restrict__ lv, uint32_t n, c
     }
 }
 
-// Final roots, then every leaf's contribution to its root's line.
+// Final roots, then every leaf's contribution to its root's line.  Leaves
+// of one cluster often sit next to each other in the depth-first order, so
+// the lanes of a warp first reduce runs of equal roots (a segmented scan that
+// never crosses a run boundary) and one lane per run does the atomics.
 __global__ void lines_gather_kernel(const DevLeaf* __restrict__ lv, uint32_t n, uint32_t* parent, uint32_t* cells,
                                     unsigned long long* sums /* [n][3] */, unsigned long long* peak) {
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const uint32_t r = uf_find(parent, k);
-        const DevLeaf f = lv[k];
-        atomicAdd(&cells[r], 1u);
-        atomicAdd(&sums[3 * (uint64_t)r + 0], (unsigned long long)f.votes);
-        atomicAdd(&sums[3 * (uint64_t)r + 1], (unsigned long long)f.votes * (2ull * f.i + 1ull));
-        atomicAdd(&sums[3 * (uint64_t)r + 2], (unsigned long long)f.votes * (2ull * f.j + 1ull));
-        // most votes, ties to the smaller leaf index
-        atomicMax(&peak[r], ((unsigned long long)f.votes << 32) | (unsigned long long)(0xffffffffu - k));
+    const int lane = threadIdx.x & 31;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t kb = blockIdx.x * blockDim.x; kb < n; kb += stride) {
+        const uint32_t k = kb + threadIdx.x;
+        const bool live = k < n;
+        uint32_t r = 0xffffffffu - (uint32_t)lane;  // a distinct key for every idle lane
+        unsigned long long v = 0, vi = 0, vj = 0, pk = 0;
+        uint32_t cnt = 0;
+        if (live) {
+            r = uf_find(parent, k);
+            const DevLeaf f = lv[k];
+            v = f.votes;
+            vi = (unsigned long long)f.votes * (2ull * f.i + 1ull);
+            vj = (unsigned long long)f.votes * (2ull * f.j + 1ull);
+            pk = ((unsigned long long)f.votes << 32) | (unsigned long long)(0xffffffffu - k);  // ties: smaller k
+            cnt = 1;
+        }
+        const uint32_t nxt = __shfl_down_sync(0xffffffffu, r, 1);
+        const uint32_t prv = __shfl_up_sync(0xffffffffu, r, 1);
+        const uint32_t ends = __ballot_sync(0xffffffffu, lane == 31 || nxt != r);
+        const int run_end = __ffs(ends & (0xffffffffu << lane)) - 1;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned long long ov = __shfl_down_sync(0xffffffffu, v, off);
+            const unsigned long long oi = __shfl_down_sync(0xffffffffu, vi, off);
+            const unsigned long long oj = __shfl_down_sync(0xffffffffu, vj, off);
+            const unsigned long long op = __shfl_down_sync(0xffffffffu, pk, off);
+            const uint32_t oc = __shfl_down_sync(0xffffffffu, cnt, off);
+            if (lane + off <= run_end) {
+                v += ov;
+                vi += oi;
+                vj += oj;
+                pk = op > pk ? op : pk;
+                cnt += oc;
+            }
+        }
+        if (live && (lane == 0 || prv != r)) {  // the first lane of each run
+            atomicAdd(&cells[r], cnt);
+            atomicAdd(&sums[3 * (uint64_t)r + 0], v);
+            atomicAdd(&sums[3 * (uint64_t)r + 1], vi);
+            atomicAdd(&sums[3 * (uint64_t)r + 2], vj);
+            atomicMax(&peak[r], pk);
+        }
     }
 }
 
@@ -256,9 +294,19 @@ extern "C" int hht_lines(hht_ctx* c, int32_t index, hht_line* lines, uint64_t ca
     const uint64_t n = c->job_n[index];
     *n_lines = 0;
     if (n == 0) return HHT_OK;
-    if (n >= 0xffffffffull) return HHT_E_ARG;
+    if (n >= 0xffffffe0ull) return HHT_E_ARG;  // leaf indices and the idle-lane keys of the gather stay distinct
     cudaSetDevice(c->device);
     cudaStream_t st = c->stream;
+    // the second call of the two-call protocol copies the lines the first one kept
+    if (c->lines_serial == c->job_serial && c->lines_index == index) {
+        const uint64_t nl = c->lines_count;
+        *n_lines = nl;
+        if (nl > capacity) return HHT_E_CAPACITY;
+        if (!lines) return HHT_E_ARG;
+        RKL(copy_out(c, lines, c->line_out.p, nl * sizeof(hht_line)));
+        CKL(cudaStreamSynchronize(st));
+        return HHT_OK;
+    }
     const DevLeaf* lv = (const DevLeaf*)c->leaves.p + c->job_off[index];
     uint64_t slots = 1024;
     while (slots < 2 * n) slots <<= 1;
@@ -303,6 +351,9 @@ extern "C" int hht_lines(hht_ctx* c, int32_t index, hht_line* lines, uint64_t ca
     if (hs.err & kErrTimeout) return HHT_E_TIMEOUT;
     if (hs.err) return HHT_E_CUDA;
     *n_lines = nl;
+    c->lines_serial = c->job_serial;
+    c->lines_index = index;
+    c->lines_count = nl;
     if (nl > capacity) return HHT_E_CAPACITY;
     if (!lines) return HHT_E_ARG;
     RKL(copy_out(c, lines, c->line_out.p, nl * sizeof(hht_line)));

@@ -106,3 +106,16 @@ def test_lines_empty_and_capacity(ctx, hht):
     assert lib.hht_lines(ctx._h, 0, small.ctypes.data, 1, ctypes.byref(n)) == hht.HHT_E_CAPACITY
     assert n.value == len(oracle.lines(oracle.detect(img.points, img.W, img.H, img.depth, img.T).leaves))
     assert lib.hht_lines(ctx._h, 1, small.ctypes.data, 1, ctypes.byref(n)) == hht.HHT_E_ARG
+
+
+def test_lines_second_call_copies_and_new_job_recomputes(ctx, hht):
+    a, b = synth.plain_128(index=1), synth.plain_128(index=2)
+    lib = hht.load()
+    n = ctypes.c_uint64()
+    for img in (a, b, a):
+        ctx.detect(img.points, img.W, img.H, img.depth, img.T)
+        assert lib.hht_lines(ctx._h, 0, None, 0, ctypes.byref(n)) == hht.HHT_E_CAPACITY
+        buf = np.zeros(int(n.value), dtype=hht.LINE_DTYPE)
+        assert lib.hht_lines(ctx._h, 0, buf.ctypes.data, len(buf), ctypes.byref(n)) == hht.HHT_OK
+        want = oracle.lines(oracle.detect(img.points, img.W, img.H, img.depth, img.T).leaves)
+        assert _rows(buf) == _rows(want)
