@@ -60,10 +60,17 @@ def read_peaks():
 
 
 def kernel_source_hash() -> str:
+    """Hash of the level (pass) kernel's source: its section of hht_kernels.cu
+    (from the pass banner to the next one) and the device helpers it uses."""
+    csrc = os.path.join(ROOT, "paper_1007_0547_gb300", "csrc")
+    with open(os.path.join(csrc, "hht_kernels.cu"), "rb") as f:
+        src = f.read()
+    start = src.index(b"// " + b"=" * 76 + b" pass")
+    end = src.index(b"// " + b"=" * 76, start + 10)
     h = hashlib.sha256()
-    for name in ("hht_kernels.cu", "hht_device.cuh", "hht_internal.h"):
-        with open(os.path.join(ROOT, "paper_1007_0547_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+    h.update(src[start:end])
+    with open(os.path.join(csrc, "hht_device.cuh"), "rb") as f:
+        h.update(f.read())
     return h.hexdigest()[:16]
 
 

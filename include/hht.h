@@ -266,6 +266,26 @@ int hht_set_tuning(hht_ctx *ctx, int32_t shape);
 int hht_set_batch_mode(hht_ctx *ctx, int32_t mode);
 
 /*
+ * One shard of a detection split by subtrees (no paper counterpart: a way to
+ * spread one large image over several GPUs).  Below level k = split_level the
+ * regions of the two halves are independent given the points, so several
+ * contexts (one per GPU) can each take some of the 2 * 4^k level-k regions:
+ * every shard computes levels 0..k in full, and a level-k region (a, b) of
+ * half h is split further only when keep[h * 4^k + a * 2^k + b] is non-zero
+ * (keep: 2 * 4^k bytes in host or device memory).  Arguments and results are
+ * those of hht_detect; the shard's leaves are those of its own subtrees, in
+ * depth-first order.  The whole detection is the union of the shards'
+ * leaves (merged in depth-first order) with statistics combined as: levels
+ * below k from any one shard, at level k the `passed` counts summed and the
+ * rest from any one shard, below k everything summed.  Every shard computes
+ * levels 0..k, so k is best kept small.  Errors: as hht_detect, and HHT_E_ARG
+ * for a NULL mask or split_level outside [1, min(depth, HHT_MAX_SPLIT_LEVEL)].
+ */
+#define HHT_MAX_SPLIT_LEVEL 10
+int hht_detect_subtrees(hht_ctx *ctx, const hht_point *points, int64_t n, int32_t W, int32_t H, int32_t depth,
+                        int32_t T, int32_t split_level, const uint8_t *keep, hht_result *out);
+
+/*
  * Front end (Section 3): Sobel's gradient operator on a grey-level image and
  * the split of its edge points into ALPHA (points on lines of absolute slope
  * <= 1) and BETA (the rest), which the paper does while the gradient is

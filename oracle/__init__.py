@@ -15,6 +15,7 @@ from .oracle import (  # noqa: F401
     sobel,
     edges,
     detect_split,
+    detect_subtrees,
     lines,
     line_parameters,
     centroid_parameters,

@@ -134,6 +134,8 @@ typedef struct {
     int64_t leaf_cap, n_leaves;
     oracle_region *regions;
     int64_t region_cap, n_regions;
+    const uint8_t *keep;    /* subtree split: keep[half * 4^k + a * 2^k + b] for regions (a, b) of level k */
+    int32_t keep_level;     /* k (used when keep is not NULL) */
 } walk_t;
 
 static uint64_t *stat_at(walk_t *w, int level, int k)
@@ -176,7 +178,13 @@ static void subdivide(walk_t *w, int level, int64_t i0, int64_t j0, int64_t S, c
         *stat_at(w, child, 0) += 1;
         *stat_at(w, child, 2) += (uint64_t)cnt;
         record_region(w, child, ci[q], cj[q], h, cnt);
-        if (cnt >= w->T) {
+        int kept = 1;
+        if (w->keep && child == w->keep_level) {
+            /* a subtree that another shard runs: tested and counted here, not split */
+            const int64_t side = (int64_t)1 << child;
+            kept = w->keep[(int64_t)w->half * side * side + (ci[q] / h) * side + cj[q] / h] != 0;
+        }
+        if (kept && cnt >= w->T) {
             *stat_at(w, child, 1) += 1;
             if (child == w->D) {
                 if (w->n_leaves < w->leaf_cap) {
@@ -201,9 +209,10 @@ static void subdivide(walk_t *w, int level, int64_t i0, int64_t j0, int64_t S, c
  *   regions: optional (may be NULL) dump of every tested region.
  * Leaves are in depth-first order (children NE, NW, SW, SE), half 0 first.
  */
-int oracle_detect(const int16_t *xy, int64_t n, int32_t W, int32_t H, int32_t depth, int32_t T, int32_t mode,
-                  oracle_leaf *leaves, int64_t leaf_cap, int64_t *n_leaves, uint64_t *stats,
-                  oracle_region *regions, int64_t region_cap, int64_t *n_regions)
+static int detect_walk(const int16_t *xy, int64_t n, int32_t W, int32_t H, int32_t depth, int32_t T, int32_t mode,
+                       oracle_leaf *leaves, int64_t leaf_cap, int64_t *n_leaves, uint64_t *stats,
+                       oracle_region *regions, int64_t region_cap, int64_t *n_regions, const uint8_t *keep,
+                       int32_t keep_level)
 {
     if (n < 0 || W < 1 || H < 1 || W > 32767 || H > 32767 || depth < 1 || depth > 24 || T < 1 || !n_leaves ||
         !stats || (n > 0 && !xy) || (leaf_cap > 0 && !leaves) || (mode != ORACLE_MODE_EXACT && mode != ORACLE_MODE_FHT))
@@ -217,6 +226,7 @@ int oracle_detect(const int16_t *xy, int64_t n, int32_t W, int32_t H, int32_t de
     w.D = depth; w.T = T; w.mode = mode;
     w.stats = stats; w.leaves = leaves; w.leaf_cap = leaf_cap;
     w.regions = regions; w.region_cap = regions ? region_cap : 0;
+    w.keep = keep; w.keep_level = keep_level;
     memset(stats, 0, sizeof(uint64_t) * 2 * (size_t)(depth + 1) * 4);
 
     int rc = ORACLE_OK;
@@ -256,6 +266,30 @@ int oracle_detect(const int16_t *xy, int64_t n, int32_t W, int32_t H, int32_t de
 done:
     free(px); free(py); free(pool); free(lists);
     return rc;
+}
+
+int oracle_detect(const int16_t *xy, int64_t n, int32_t W, int32_t H, int32_t depth, int32_t T, int32_t mode,
+                  oracle_leaf *leaves, int64_t leaf_cap, int64_t *n_leaves, uint64_t *stats,
+                  oracle_region *regions, int64_t region_cap, int64_t *n_regions)
+{
+    return detect_walk(xy, n, W, H, depth, T, mode, leaves, leaf_cap, n_leaves, stats, regions, region_cap,
+                       n_regions, NULL, 0);
+}
+
+/*
+ * One shard of a detection split by subtrees: the level-k regions (a, b) of
+ * half h with keep[h * 4^k + a * 2^k + b] == 0 are tested and counted (so the
+ * statistics of levels <= k, apart from the level-k pass count, are those of
+ * the whole detection) but never split; everything below them belongs to
+ * another shard.
+ */
+int oracle_detect_subtrees(const int16_t *xy, int64_t n, int32_t W, int32_t H, int32_t depth, int32_t T,
+                           int32_t split_level, const uint8_t *keep, oracle_leaf *leaves, int64_t leaf_cap,
+                           int64_t *n_leaves, uint64_t *stats)
+{
+    if (!keep || split_level < 1 || split_level > depth) return ORACLE_E_ARG;
+    return detect_walk(xy, n, W, H, depth, T, ORACLE_MODE_EXACT, leaves, leaf_cap, n_leaves, stats, NULL, 0, NULL,
+                       keep, split_level);
 }
 
 /*

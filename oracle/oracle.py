@@ -82,6 +82,12 @@ def _load():
                                          ctypes.POINTER(ctypes.c_int64), i16p, ctypes.c_int64,
                                          ctypes.POINTER(ctypes.c_int64)]
             lib.oracle_edges.restype = ctypes.c_int
+            lib.oracle_detect_subtrees.argtypes = [i16p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                                   ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                                   ctypes.POINTER(ctypes.c_uint8), ctypes.POINTER(_Leaf),
+                                                   ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
+                                                   ctypes.POINTER(ctypes.c_uint64)]
+            lib.oracle_detect_subtrees.restype = ctypes.c_int
             lib.oracle_lines.argtypes = [ctypes.POINTER(_Leaf), ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
                                          ctypes.POINTER(ctypes.c_int64)]
             lib.oracle_lines.restype = ctypes.c_int
@@ -248,3 +254,32 @@ def centroid_parameters(line, depth: int, L: int):
     K = 1 << depth
     V = int(line["total_votes"])
     return (Fraction(int(line["sum_i2"]), V) - K) / K, 2 * L * (Fraction(int(line["sum_j2"]), V) - K) / K
+
+
+def detect_subtrees(points: np.ndarray, W: int, H: int, depth: int, T: int, split_level: int,
+                    keep: np.ndarray) -> OracleResult:
+    """One shard of a detection split by level-`split_level` subtrees: keep is
+    uint8 [2 * 4**k] (half, a, b); regions of that level that are not kept are
+    tested and counted but not split."""
+    lib = _load()
+    pts = np.ascontiguousarray(np.asarray(points, dtype=np.int16).reshape(-1, 2))
+    km = np.ascontiguousarray(np.asarray(keep, dtype=np.uint8).reshape(-1))
+    if km.size != 2 * 4 ** split_level:
+        raise ValueError("keep must hold 2 * 4**split_level entries")
+    stats = np.zeros((2, depth + 1, 4), dtype=np.uint64)
+    nl = ctypes.c_int64(0)
+    cap = 1 << 16
+    while True:
+        leaves = (_Leaf * cap)()
+        rc = lib.oracle_detect_subtrees(pts.ctypes.data_as(ctypes.POINTER(ctypes.c_int16)), pts.shape[0], W, H,
+                                        depth, T, split_level, km.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                        leaves, cap, ctypes.byref(nl),
+                                        stats.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
+        if rc == -4:
+            cap = int(nl.value) + 1
+            continue
+        break
+    if rc != 0:
+        raise ValueError(f"oracle.detect_subtrees failed with code {rc}")
+    lv = np.frombuffer(leaves, dtype=np.uint32).reshape(-1, 4)[: int(nl.value)].copy()
+    return OracleResult(lv, stats, None, rc)

@@ -338,8 +338,8 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
     const bool fht = c->predicate == HHT_PREDICATE_FHT;
     if (fht && i64) return HHT_E_ARG;  // checked by the entry points before any device work
     const int occ_p = i64 ? c->occ_persistent64 : c->occ_persistent32;
-    const bool persistent =
-        !fht && !c->job_halves && c->batch_mode == 1 && c->plan.valid && c->plan.sig == sig && occ_p > 0;
+    const bool persistent = !fht && !c->job_halves && !c->job_keep && c->batch_mode == 1 && c->plan.valid &&
+                            c->plan.sig == sig && occ_p > 0;
     uint64_t cap_rec = 0, cap_vox = 0, cap_tiles = 0;
     if (persistent) {
         cap_rec = std::max<uint64_t>(c->plan.cap_rec, (uint64_t)n_units);
@@ -482,6 +482,8 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
         a.tile_data = (uint64_t*)c->sel_data.p;
         a.cap_tiles = sel_tiles;
         a.withhold_tile_plus1 = c->inject_tile >= 0 ? (uint32_t)(c->inject_tile + 1) : 0u;
+        a.keep = c->job_keep;
+        a.keep_level = c->job_keep_level;
         const int sel_grid = (int)std::min<uint64_t>(sel_tiles, (uint64_t)c->num_sms * c->occ_select);
         // select's capacity test on the voter stream is re-done below with the exact size
         a.cap_voters = UINT64_MAX;
@@ -756,7 +758,7 @@ void hht_destroy(hht_ctx* c) {
                      &c->preg[1],   &c->cnt[0],     &c->cnt[1],       &c->vox[0],    &c->vox[1],     &c->leaves,
                      &c->sel_flags, &c->sel_data,   &c->cursors,      &c->img_buf,   &c->edge_pts[0],
                      &c->edge_pts[1], &c->edge_tot,   &c->line_keys,    &c->line_vals, &c->line_parent,
-                     &c->line_cells, &c->line_sums,  &c->line_out};
+                     &c->line_cells, &c->line_sums,  &c->line_out,     &c->keep_buf};
     for (DevBuf* b : all) release(c, *b);
     delete c;
 }
@@ -881,6 +883,29 @@ int hht_autotune(hht_ctx* c, const hht_image* images, int32_t count, int32_t* be
     if (rc != HHT_OK) return rc;
     *best = best_shape;
     return HHT_OK;
+}
+
+int hht_detect_subtrees(hht_ctx* c, const hht_point* points, int64_t n, int32_t W, int32_t H, int32_t depth,
+                        int32_t T, int32_t split_level, const uint8_t* keep, hht_result* out) {
+    if (!c || !out || !keep) return HHT_E_ARG;
+    hht_image im{points, n, W, H, depth, T};
+    int rc = check_image(im);
+    if (rc != HHT_OK) return rc;
+    if (split_level < 1 || split_level > depth || split_level > HHT_MAX_SPLIT_LEVEL) return HHT_E_ARG;
+    std::lock_guard<std::mutex> lk(c->mu);
+    rc = check_predicate(c, im);
+    if (rc != HHT_OK) return rc;
+    cudaSetDevice(c->device);
+    const size_t bytes = (size_t)2 << (2 * split_level);  // 2 * 4^k
+    RK(ensure(c, c->keep_buf, bytes));
+    CK(cudaMemcpyAsync(c->keep_buf.p, keep, bytes, cudaMemcpyDefault, c->stream));
+    c->job_keep = (const uint8_t*)c->keep_buf.p;
+    c->job_keep_level = split_level;
+    rc = run_job(c, &im, 1, out);
+    c->job_keep = nullptr;
+    c->job_keep_level = 0;
+    if (rc != HHT_OK) return rc;
+    return out->status;
 }
 
 int hht_set_predicate(hht_ctx* c, int32_t predicate) {

@@ -56,6 +56,9 @@ struct hht_ctx {
     int64_t inject_tile = -1;  // hht_inject_fault: selection tile withheld in the next job (-1 = none)
     int predicate = 0;         // HHT_PREDICATE_EXACT or HHT_PREDICATE_FHT (hht_detect / hht_detect_batch)
     const uint8_t* job_halves = nullptr;  // during a job: per image, bit h set when half h takes its points
+    const uint8_t* job_keep = nullptr;    // during a job: device keep mask of subtree sharding (or NULL)
+    int32_t job_keep_level = 0;
+    DevBuf keep_buf;
     // front end (hht_edges, hht_detect_image): staged image, ALPHA and BETA point lists, their counts
     DevBuf img_buf, edge_pts[2], edge_tot;
     // leaves -> lines (hht_lines): hash table, union-find parents, per-root sums, output

@@ -142,6 +142,10 @@ struct LevelArgs {
     int32_t level;             // step of the level loop
     int32_t num_sms;
     uint32_t withhold_tile_plus1;  // fault injection: 1 + the selection tile that publishes nothing (0 = none)
+    // subtree sharding: a region (a, b) of level keep_level passes only when
+    // keep[half * 4^k + a * 2^k + b] != 0 (NULL = every region may pass)
+    const uint8_t* keep;
+    int32_t keep_level;
 };
 
 // Arguments of the persistent (one cooperative launch) form of a batch.

@@ -240,6 +240,17 @@ __device__ __forceinline__ void select_body(const LevelArgs& a, bool standalone)
             uint32_t pm = 0;
 #pragma unroll
             for (int q = 0; q < 4; ++q) pm |= (cnt[j][q] >= (uint32_t)U.T ? 1u : 0u) << q;
+            if (a.keep && lev == a.keep_level) {
+                // subtrees that another shard runs: tested and counted, not split
+                const uint64_t side = 1ull << lev;
+                const uint64_t base = (uint64_t)(R.unit & 1u) * side * side;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint64_t ca = 2ull * R.a + ((q == NE || q == SE) ? 1u : 0u);
+                    const uint64_t cb = 2ull * R.b + ((q == NE || q == NW) ? 1u : 0u);
+                    if (!a.keep[base + ca * side + cb]) pm &= ~(1u << q);
+                }
+            }
             pass[j] = pm;
             leafy[j] = (lev == U.D);
             // voters of a level-lev child are read by the next pass only when

@@ -32,7 +32,8 @@ HHT_E_UNKNOWN_TICKET = -8
 EXPORTS = ("hht_create", "hht_destroy", "hht_detect", "hht_detect_batch", "hht_fetch_leaves", "hht_submit",
            "hht_poll", "hht_progress", "hht_profile_enable", "hht_profile_read", "hht_strerror", "hht_version",
            "hht_detect_noalloc", "hht_autotune", "hht_set_tuning", "hht_set_batch_mode", "hht_fetch_all_leaves",
-           "hht_inject_fault", "hht_set_predicate", "hht_edges", "hht_detect_image", "hht_lines")
+           "hht_inject_fault", "hht_set_predicate", "hht_edges", "hht_detect_image", "hht_lines",
+           "hht_detect_subtrees")
 BATCH_LEVELS, BATCH_PERSISTENT = 0, 1
 FAULT_NONE, FAULT_WITHHOLD_SCAN_TILE = 0, 1
 PREDICATE_EXACT, PREDICATE_FHT = 0, 1
@@ -124,6 +125,8 @@ def load(path: Optional[str] = None):
     lib.hht_inject_fault.restype = ctypes.c_int
     lib.hht_set_predicate.argtypes = [vp, i32]
     lib.hht_set_predicate.restype = ctypes.c_int
+    lib.hht_detect_subtrees.argtypes = [vp, vp, i64, i32, i32, i32, i32, i32, vp, ctypes.POINTER(_Result)]
+    lib.hht_detect_subtrees.restype = ctypes.c_int
     lib.hht_lines.argtypes = [vp, i32, vp, u64, ctypes.POINTER(u64)]
     lib.hht_lines.restype = ctypes.c_int
     lib.hht_edges.argtypes = [vp, vp, i32, i32, i32, vp, u64, ctypes.POINTER(u64), vp, u64, ctypes.POINTER(u64)]
@@ -468,6 +471,32 @@ class Context:
             raise HhtError(rc, "hht_detect_image")
         del keep
         k = int(r.n_leaves) if rc == HHT_OK else 0
+        return Result(buf[:k], _stats_of(r), int(r.depth), int(r.L), rc)
+
+    def detect_subtrees(self, points, W: int, H: int, depth: int, T: int, split_level: int, keep,
+                        leaves_on_device: bool = True) -> Result:
+        """One shard of a detection split by level-`split_level` subtrees
+        (hht_detect_subtrees): keep is a uint8 mask of 2 * 4**split_level
+        entries (half, a, b); see shard.plan_subtrees / merge_subtrees."""
+        lib = load()
+        p = _Points(points)
+        km = np.ascontiguousarray(np.asarray(keep, dtype=np.uint8).reshape(-1))
+        if km.size != 2 * 4 ** int(split_level):
+            raise ValueError("keep must hold 2 * 4**split_level entries")
+        cap = int(self._cap_hint)
+        buf, lp = self._alloc_leaves(cap, leaves_on_device)
+        r = _Result()
+        r.leaves = lp
+        r.leaf_capacity = cap
+        rc = lib.hht_detect_subtrees(self._h, p.ptr, p.n, int(W), int(H), int(depth), int(T), int(split_level),
+                                     km.ctypes.data, ctypes.byref(r))
+        if rc == HHT_E_CAPACITY:
+            self._cap_hint = max(self._cap_hint, int(r.n_leaves))
+            buf = self._fetch(0, int(r.n_leaves), leaves_on_device)
+            rc = HHT_OK
+        if rc != HHT_OK:
+            raise HhtError(rc, "hht_detect_subtrees")
+        k = int(r.n_leaves)
         return Result(buf[:k], _stats_of(r), int(r.depth), int(r.L), rc)
 
     def lines(self, index: int = 0) -> np.ndarray:

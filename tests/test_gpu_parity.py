@@ -438,3 +438,28 @@ def test_persistent_form_replays_a_cuda_graph_on_a_stream(hht):
             for r, w in zip(got, want):
                 _same(r, w)
         c.close()
+
+
+# ------------------------------------------------------------------ one image split by subtrees
+@pytest.mark.parametrize("split_level,world", [(1, 2), (2, 3), (3, 4)])
+def test_subtree_shards_merge_to_the_whole_detection(ctx, split_level, world):
+    # the shards run one after another on this GPU, as separate ranks would;
+    # their merge equals the unsharded detection (and, for 128^2, the oracle)
+    import torch
+    from paper_1007_0547_gb300 import shard
+    for img in (synth.plain_128(index=2), synth.plain_1024(index=2)):
+        pts = torch.from_numpy(img.points).cuda()
+        whole = ctx.detect(pts, img.W, img.H, img.depth, img.T)
+        parts = []
+        for keep in shard.plan_subtrees(split_level, world):
+            r = ctx.detect_subtrees(pts, img.W, img.H, img.depth, img.T, split_level, keep)
+            parts.append((r.leaves_numpy(), r.stats))
+        lv, st = shard.merge_subtrees(parts, split_level, img.depth)
+        assert np.array_equal(lv, whole.leaves_numpy()), (img.name, split_level, world)
+        assert np.array_equal(st, whole.stats), (img.name, split_level, world)
+        if img.W == 128:
+            want = oracle.detect(img.points, img.W, img.H, img.depth, img.T)
+            assert np.array_equal(lv, want.leaves) and np.array_equal(st, want.stats)
+            one = oracle.detect_subtrees(img.points, img.W, img.H, img.depth, img.T, split_level,
+                                         shard.plan_subtrees(split_level, world)[0])
+            assert np.array_equal(parts[0][0], one.leaves) and np.array_equal(parts[0][1], one.stats)

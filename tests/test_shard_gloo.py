@@ -1,8 +1,10 @@
-"""Multi-rank sharding of a batch, on CPU with the gloo backend (world size 2).
+"""Multi-rank sharding on CPU with the gloo backend (world size 2).
 
-Each rank detects its share of the images (the CPU oracle stands in for the
-GPU here) and rank 0 gathers the results; the merged list must equal the
-unsharded run image by image."""
+Across images: each rank detects its share of the images (the CPU oracle
+stands in for the GPU here) and rank 0 gathers the results; the merged list
+must equal the unsharded run image by image.  Within one image: each rank
+runs its level-k subtrees (the oracle's subtree mode), rank 0 merges, and the
+merged leaves and statistics must equal the unsharded detection."""
 import os
 import socket
 
@@ -76,3 +78,60 @@ def test_two_gloo_ranks_merge_equals_unsharded(tmp_path):
     for (lv, st), w in zip(merged, want):
         assert np.array_equal(lv, w.leaves)
         assert np.array_equal(st, w.stats)
+
+
+def _subtree_worker(rank, world, port, image, split_level, out_path):
+    import pickle
+
+    import torch.distributed as dist
+
+    import oracle
+    from paper_1007_0547_gb300 import shard
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+
+    def gather(obj):
+        objs = [None] * world if rank == 0 else None
+        dist.gather_object(obj, objs, dst=0)
+        return objs
+
+    def detect_subtrees(im, k, keep):
+        r = oracle.detect_subtrees(im[0], im[1], im[2], im[3], im[4], k, keep)
+        return r.leaves, r.stats
+
+    merged = shard.run_subtree_sharded(image, detect_subtrees, split_level, rank, world, gather)
+    if rank == 0:
+        with open(out_path, "wb") as f:
+            pickle.dump(merged, f)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_plan_subtrees_covers_every_region_once():
+    from paper_1007_0547_gb300 import shard
+    for k in (1, 2, 3):
+        for world in (1, 2, 3, 7):
+            masks = shard.plan_subtrees(k, world)
+            total = np.sum(np.stack(masks).astype(np.int64), axis=0)
+            assert np.all(total == 1)
+            sizes = [int(m.sum()) for m in masks]
+            assert max(sizes) - min(sizes) <= 1
+
+
+@pytest.mark.parametrize("split_level", [1, 2, 3])
+def test_two_gloo_ranks_split_one_image_by_subtrees(tmp_path, split_level):
+    import pickle
+
+    import oracle
+    import torch.multiprocessing as mp
+    img = synth.plain_128(index=3)
+    image = (img.points, img.W, img.H, img.depth, img.T)
+    out = str(tmp_path / "merged.pkl")
+    mp.start_processes(_subtree_worker, args=(2, _free_port(), image, split_level, out), nprocs=2, join=True,
+                       start_method="spawn")
+    with open(out, "rb") as f:
+        lv, st = pickle.load(f)
+    want = oracle.detect(*image)
+    assert np.array_equal(lv, want.leaves)
+    assert np.array_equal(st, want.stats)
