@@ -552,6 +552,10 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
     if (err & kErrTimeout) return HHT_E_TIMEOUT;
     if (err & kErrOverflow) return HHT_E_NOMEM;
     if (err & kErrInvariant) return HHT_E_CUDA;
+    if (err & kErrBounds) {
+        if (c->debug) fprintf(stderr, "[hht] a kernel met an out-of-range index (checked build)\n");
+        return HHT_E_CUDA;
+    }
     if (!persistent) {
         // capacities for the persistent form of the same job, with a margin
         c->plan.sig = sig;
@@ -967,7 +971,10 @@ const char* hht_strerror(int code) {
 }
 
 const char* hht_version(void) {
-    return "hht 0.3 (sm_103a, level-synchronous stage/select/pass; pass tile shapes 4x256/3 2x256/4 3x256/4 4x128/6 "
+#ifdef HHT_CHECKED
+    return "hht 0.4 checked (sm_103a; every data-derived index of the level kernel bounds-checked)";
+#endif
+    return "hht 0.4 (sm_103a, level-synchronous stage/select/pass; pass tile shapes 4x256/3 2x256/4 3x256/4 4x128/6 "
            "4x256/4 4x512/2)";
 }
 

@@ -108,8 +108,19 @@ enum : uint32_t {
     kErrRange = 1u,        // a point outside the image
     kErrTimeout = 2u,      // a bounded wait expired
     kErrOverflow = 4u,     // a capacity was exceeded (host re-runs with more memory)
-    kErrInvariant = 8u     // a line did not cross the level-0 region (cannot happen)
+    kErrInvariant = 8u,    // a line did not cross the level-0 region (cannot happen)
+    kErrBounds = 16u       // HHT_CHECKED builds: an index read from the data was out of range
 };
+
+// HHT_CHECKED builds check every index that a kernel takes from its data
+// (parent and child record indices) against the current sizes; a bad index
+// sets kErrBounds and the access is skipped.  Normal builds compile the check
+// away.
+#ifdef HHT_CHECKED
+#define HHT_CHECK_INDEX(i, n, st) (((uint64_t)(i) < (uint64_t)(n)) ? true : (atomicOr(&(st)->err, kErrBounds), false))
+#else
+#define HHT_CHECK_INDEX(i, n, st) true
+#endif
 
 struct DeviceStatus {
     uint32_t err;

@@ -414,7 +414,7 @@ __device__ __forceinline__ uint32_t child_index(const PassRegion& pr, int q) {
 // `packed`), so one atomic instruction covers all sixteen cells.  Every lane
 // must call this.
 __device__ __forceinline__ void add_counts_lanes(uint32_t* __restrict__ cnt, uint32_t child_base, uint32_t packed,
-                                                 const uint32_t (&c16)[8]) {
+                                                 const uint32_t (&c16)[8], uint64_t n_children, DeviceStatus* st) {
     const int lane = threadIdx.x & 31;
     const int al = (lane >> 2) & 3, be = lane & 3;
     const int sel = 2 * al + (be & 1);
@@ -424,7 +424,7 @@ __device__ __forceinline__ void add_counts_lanes(uint32_t* __restrict__ cnt, uin
     const uint32_t c = (be & 2) ? (w >> 16) : (w & 0xffffu);
     const int q = quad_of(al >> 1, be >> 1), g = quad_of(al & 1, be & 1);
     const uint32_t ci = child_base + __popc(packed & 0xfu & ((1u << q) - 1u));
-    if (lane < 16 && c) atomicAdd(&cnt[4 * (size_t)ci + g], c);
+    if (lane < 16 && c && HHT_CHECK_INDEX(ci, n_children, st)) atomicAdd(&cnt[4 * (size_t)ci + g], c);
 }
 
 // Per-lane byte counters rows[alpha] (byte beta) -> 16-bit pairs summed over
@@ -612,6 +612,11 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
     const uint32_t lt = (1u << lane) - 1u;
     const uint64_t nin = a.info_prev->n_voters;
     if (job_aborted(a.status)) return;
+#ifdef HHT_CHECKED
+    const uint64_t n_par = a.info_prev->n_regions, n_chi = a.info->n_regions;
+#else
+    const uint64_t n_chi = 0;  // only read by the checks of HHT_CHECKED builds
+#endif
     // Work distribution: the stream is cut into grabs of G consecutive
     // records, G = a quarter of a warp's even share rounded to whole chunks
     // and kept within [kMinGrab, kMaxGrab].  Warp w takes grab w first and
@@ -650,12 +655,13 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
         if (cur != kNoRegion) {
             uint32_t c16[8];
             reduce_rows(rows, 0xffffffffu, c16);
-            add_counts_lanes(a.child_cnt, cg.pr.child_base, cg.pr.packed, c16);
+            add_counts_lanes(a.child_cnt, cg.pr.child_base, cg.pr.packed, c16, n_chi, a.status);
         }
         rows[0] = rows[1] = rows[2] = rows[3] = 0u;
         steps = 0;
     };
     auto start_run = [&](uint32_t r) {
+        if (!HHT_CHECK_INDEX(r, n_par, a.status)) r = 0u;
         cur = r;
         cg.load(a.pregions, r);
 #pragma unroll
@@ -729,7 +735,7 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
             const uint32_t tq_mine = lane < 4 ? (tot >> (8 * quad_byte_rt(lane))) & 0xffu : 0u;
             if (tq_mine) {
                 const uint32_t cq = lane == 0 ? ci[0] : lane == 1 ? ci[1] : lane == 2 ? ci[2] : ci[3];
-                mybase = atomicAdd(&a.cursor[cq], (unsigned long long)tq_mine);
+                if (HHT_CHECK_INDEX(cq, n_chi, a.status)) mybase = atomicAdd(&a.cursor[cq], (unsigned long long)tq_mine);
             }
 #pragma unroll
             for (int k = 0; k < kChunkSteps; ++k) add_rows(rows, gv[k]);
@@ -805,7 +811,8 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
                     const uint32_t bq = __ballot_sync(0xffffffffu, keep);
                     if (!bq) continue;
                     unsigned long long p = 0;
-                    if (lane == 0) p = atomicAdd(&a.cursor[ci[q]], (unsigned long long)__popc(bq));
+                    if (lane == 0 && HHT_CHECK_INDEX(ci[q], n_chi, a.status))
+                        p = atomicAdd(&a.cursor[ci[q]], (unsigned long long)__popc(bq));
                     p = __shfl_sync(0xffffffffu, p, 0);
                     const uint64_t at = p + __popc(bq & lt);
                     st_pred_v2(vout + at, keep && at < a.cap_voters, rk.x, ci[q]);
@@ -815,7 +822,7 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
             // settle the current run; every lane classifies with its own parent
             settle();
             Geo g = cg;
-            if (valid && r != cur) g.load(a.pregions, r);
+            if (valid && r != cur) g.load(a.pregions, HHT_CHECK_INDEX(r, n_par, a.status) ? r : 0u);
             uint32_t kw = 0u, gv = 0u;
             if (valid) {
                 const Classified<I> c = classify<I>(g, rk.x);
@@ -831,7 +838,8 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
                 const uint32_t gm = bq & peers;
                 const int leader = keep ? __ffs(gm) - 1 : lane;
                 unsigned long long p = 0;
-                if (keep && lane == leader) p = atomicAdd(&a.cursor[child_index(g.pr, q)], (unsigned long long)__popc(gm));
+                if (keep && lane == leader && HHT_CHECK_INDEX(child_index(g.pr, q), n_chi, a.status))
+                    p = atomicAdd(&a.cursor[child_index(g.pr, q)], (unsigned long long)__popc(gm));
                 p = __shfl_sync(0xffffffffu, p, leader);
                 const uint64_t at = p + __popc(gm & lt);
                 st_pred_v2(vout + at, keep && at < a.cap_voters, rk.x, child_index(g.pr, q));
@@ -853,7 +861,7 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
                 uint32_t c16[8];
                 reduce_rows(part, 0xffffffffu, c16);
                 add_counts_lanes(a.child_cnt, __shfl_sync(0xffffffffu, g.pr.child_base, leader),
-                                 __shfl_sync(0xffffffffu, g.pr.packed, leader), c16);
+                                 __shfl_sync(0xffffffffu, g.pr.packed, leader), c16, n_chi, a.status);
                 rest &= ~gmask;
             }
             start_run(rl);
