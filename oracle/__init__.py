@@ -16,6 +16,7 @@ from .oracle import (  # noqa: F401
     edges,
     detect_split,
     detect_subtrees,
+    detect_removal,
     lines,
     line_parameters,
     centroid_parameters,

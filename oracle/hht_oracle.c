@@ -438,3 +438,112 @@ int oracle_lines(const oracle_leaf *leaves, int64_t n, oracle_line *out, int64_t
     free(parent); free(line_of);
     return nl > cap ? ORACLE_E_CAPACITY : ORACLE_OK;
 }
+
+/*
+ * The paper's solution() step (Section 3): when a region at the leaf level
+ * gets enough votes, its voters are plotted and their codes are zeroed at
+ * every level, so they take no part in any region the depth-first traversal
+ * reaches later.  Readings where the paper is silent:
+ *   - removal is per half: the two halves are two runs of the algorithm
+ *     (ALPHA, then BETA), so a point plotted in one half still takes part in
+ *     the other (every point enters both halves here);
+ *   - the `tests` statistic of a level counts the codes actually evaluated:
+ *     for each tested region, the voters of its parent not removed by then;
+ *   - a region passes when its votes reach T, as in the order-free detection.
+ * Leaves are the accepted cells in traversal order with their votes at the
+ * time they were reached; plotted[h * n + k] is set for every point plotted
+ * in half h.
+ */
+typedef struct {
+    walk_t *w;
+    uint8_t *removed;  /* current half: 1 once plotted */
+} removal_t;
+
+static void subdivide_removal(removal_t *r, int level, int64_t i0, int64_t j0, int64_t S, const uint32_t *V,
+                              int64_t nV)
+{
+    walk_t *w = r->w;
+    const int64_t h = S / 2;
+    const int64_t ci[4] = {i0 + h, i0, i0, i0 + h};
+    const int64_t cj[4] = {j0 + h, j0 + h, j0, j0};
+    const int child = level + 1;
+    uint32_t *buf = w->lists[child];
+    for (int q = 0; q < 4; ++q) {
+        int64_t cnt = 0, evaluated = 0;
+        for (int64_t k = 0; k < nV; ++k) {
+            if (r->removed[V[k]]) continue; /* its codes were zeroed by an earlier solution() */
+            ++evaluated;
+            if (line_votes(w, V[k], ci[q], cj[q], h)) buf[cnt++] = V[k];
+        }
+        *stat_at(w, child, 0) += 1;
+        *stat_at(w, child, 2) += (uint64_t)cnt;
+        *stat_at(w, child, 3) += (uint64_t)evaluated;
+        if (cnt >= w->T) {
+            *stat_at(w, child, 1) += 1;
+            if (child == w->D) {
+                if (w->n_leaves < w->leaf_cap) {
+                    oracle_leaf *lf = &w->leaves[w->n_leaves];
+                    lf->half = (uint32_t)w->half; lf->i = (uint32_t)ci[q]; lf->j = (uint32_t)cj[q];
+                    lf->votes = (uint32_t)cnt;
+                }
+                w->n_leaves++;
+                for (int64_t k = 0; k < cnt; ++k) r->removed[buf[k]] = 1; /* solution(): plot and remove */
+            } else {
+                subdivide_removal(r, child, ci[q], cj[q], h, buf, cnt);
+            }
+        }
+    }
+}
+
+int oracle_detect_removal(const int16_t *xy, int64_t n, int32_t W, int32_t H, int32_t depth, int32_t T,
+                          oracle_leaf *leaves, int64_t leaf_cap, int64_t *n_leaves, uint64_t *stats, uint8_t *plotted)
+{
+    if (n < 0 || W < 1 || H < 1 || W > 32767 || H > 32767 || depth < 1 || depth > 24 || T < 1 || !n_leaves ||
+        !stats || (n > 0 && !xy) || (leaf_cap > 0 && !leaves))
+        return ORACLE_E_ARG;
+    for (int64_t k = 0; k < n; ++k)
+        if (xy[2 * k] < 0 || xy[2 * k] >= W || xy[2 * k + 1] < 0 || xy[2 * k + 1] >= H) return ORACLE_E_RANGE;
+    walk_t w;
+    memset(&w, 0, sizeof w);
+    w.L = oracle_frame_side(W, H);
+    w.D = depth; w.T = T; w.mode = ORACLE_MODE_EXACT;
+    w.stats = stats; w.leaves = leaves; w.leaf_cap = leaf_cap;
+    memset(stats, 0, sizeof(uint64_t) * 2 * (size_t)(depth + 1) * 4);
+    int rc = ORACLE_OK;
+    const size_t cap = (size_t)(n > 0 ? n : 1);
+    int32_t *px = (int32_t *)malloc(cap * sizeof(int32_t));
+    int32_t *py = (int32_t *)malloc(cap * sizeof(int32_t));
+    uint32_t *pool = (uint32_t *)malloc(cap * sizeof(uint32_t) * (size_t)(depth + 1));
+    uint32_t **lists = (uint32_t **)malloc(sizeof(uint32_t *) * (size_t)(depth + 1));
+    uint8_t *removed = (uint8_t *)malloc(cap);
+    if (!px || !py || !pool || !lists || !removed) { rc = ORACLE_E_NOMEM; goto done; }
+    for (int l = 0; l <= depth; ++l) lists[l] = pool + cap * (size_t)l;
+    w.lists = lists; w.px = px; w.py = py;
+    const int64_t K = (int64_t)1 << depth;
+    removal_t r;
+    r.w = &w;
+    r.removed = removed;
+    for (int half = 0; half < 2; ++half) {
+        w.half = half;
+        memset(removed, 0, cap);
+        for (int64_t k = 0; k < n; ++k) {
+            px[k] = half == 0 ? xy[2 * k] : xy[2 * k + 1];
+            py[k] = half == 0 ? xy[2 * k + 1] : xy[2 * k];
+        }
+        int64_t nv = 0;
+        for (int64_t k = 0; k < n; ++k)
+            if (line_votes(&w, (uint32_t)k, 0, 0, K)) lists[0][nv++] = (uint32_t)k;
+        if (nv != n) { rc = ORACLE_E_INVARIANT; goto done; }
+        *stat_at(&w, 0, 0) = 1;
+        *stat_at(&w, 0, 1) = 1;
+        *stat_at(&w, 0, 2) = (uint64_t)nv;
+        *stat_at(&w, 0, 3) = (uint64_t)n;
+        subdivide_removal(&r, 0, 0, 0, K, lists[0], nv);
+        if (plotted) memcpy(plotted + (size_t)half * cap, removed, (size_t)n);
+    }
+    *n_leaves = w.n_leaves;
+    if (w.n_leaves > leaf_cap) rc = ORACLE_E_CAPACITY;
+done:
+    free(px); free(py); free(pool); free(lists); free(removed);
+    return rc;
+}

@@ -88,6 +88,11 @@ def _load():
                                                    ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
                                                    ctypes.POINTER(ctypes.c_uint64)]
             lib.oracle_detect_subtrees.restype = ctypes.c_int
+            lib.oracle_detect_removal.argtypes = [i16p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                                  ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_Leaf),
+                                                  ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
+                                                  ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint8)]
+            lib.oracle_detect_removal.restype = ctypes.c_int
             lib.oracle_lines.argtypes = [ctypes.POINTER(_Leaf), ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
                                          ctypes.POINTER(ctypes.c_int64)]
             lib.oracle_lines.restype = ctypes.c_int
@@ -283,3 +288,31 @@ def detect_subtrees(points: np.ndarray, W: int, H: int, depth: int, T: int, spli
         raise ValueError(f"oracle.detect_subtrees failed with code {rc}")
     lv = np.frombuffer(leaves, dtype=np.uint32).reshape(-1, 4)[: int(nl.value)].copy()
     return OracleResult(lv, stats, None, rc)
+
+
+def detect_removal(points: np.ndarray, W: int, H: int, depth: int, T: int):
+    """Section 3 with the solution() step: the voters of every accepted leaf
+    are plotted and removed from the regions reached later (per half).
+    Returns (OracleResult with the accepted leaves in traversal order and the
+    statistics, plotted uint8 [2, n])."""
+    lib = _load()
+    pts = np.ascontiguousarray(np.asarray(points, dtype=np.int16).reshape(-1, 2))
+    n = pts.shape[0]
+    stats = np.zeros((2, depth + 1, 4), dtype=np.uint64)
+    plotted = np.zeros((2, max(n, 1)), dtype=np.uint8)
+    nl = ctypes.c_int64(0)
+    cap = 1 << 14
+    while True:
+        leaves = (_Leaf * cap)()
+        rc = lib.oracle_detect_removal(pts.ctypes.data_as(ctypes.POINTER(ctypes.c_int16)), n, W, H, depth, T,
+                                       leaves, cap, ctypes.byref(nl),
+                                       stats.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                       plotted.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)))
+        if rc == -4:
+            cap = int(nl.value) + 1
+            continue
+        break
+    if rc != 0:
+        raise ValueError(f"oracle.detect_removal failed with code {rc}")
+    lv = np.frombuffer(leaves, dtype=np.uint32).reshape(-1, 4)[: int(nl.value)].copy()
+    return OracleResult(lv, stats, None, rc), plotted[:, :n].copy()
