@@ -266,6 +266,25 @@ int hht_set_tuning(hht_ctx *ctx, int32_t shape);
 int hht_set_batch_mode(hht_ctx *ctx, int32_t mode);
 
 /*
+ * Detection with the paper's solution() step (Section 3): the regions are
+ * visited depth-first (quad1..quad4 = NE, NW, SW, SE), and when a cell of the
+ * leaf level gets votes >= T its voters are plotted and removed from every
+ * region visited after it, so each edge point is plotted at most once per
+ * half.  Readings: removal is per half (ALPHA and BETA are two runs, and every
+ * point enters both); the `tests` statistic counts the codes actually
+ * evaluated (the voters of each tested region's parent that were not removed
+ * by then).  out->leaves receives the accepted cells, half 0's then half 1's,
+ * each in visiting order, with their votes when visited; `plotted` (NULL or
+ * 2 * n bytes, host or device) receives one flag per point and half
+ * (half-major).  The visiting order makes this a sequential walk: each
+ * (image, half) is one warp on the GPU; hht_detect_removal_batch runs many
+ * images at once (no plotted flags).  Errors: as hht_detect.
+ */
+int hht_detect_removal(hht_ctx *ctx, const hht_point *points, int64_t n, int32_t W, int32_t H, int32_t depth,
+                       int32_t T, hht_result *out, uint8_t *plotted);
+int hht_detect_removal_batch(hht_ctx *ctx, const hht_image *images, int32_t count, hht_result *outs);
+
+/*
  * One shard of a detection split by subtrees (no paper counterpart: a way to
  * spread one large image over several GPUs).  Below level k = split_level the
  * regions of the two halves are independent given the points, so several

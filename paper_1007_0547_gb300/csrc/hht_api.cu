@@ -762,7 +762,8 @@ void hht_destroy(hht_ctx* c) {
                      &c->preg[1],   &c->cnt[0],     &c->cnt[1],       &c->vox[0],    &c->vox[1],     &c->leaves,
                      &c->sel_flags, &c->sel_data,   &c->cursors,      &c->img_buf,   &c->edge_pts[0],
                      &c->edge_pts[1], &c->edge_tot,   &c->line_keys,    &c->line_vals, &c->line_parent,
-                     &c->line_cells, &c->line_sums,  &c->line_out,     &c->keep_buf};
+                     &c->line_cells, &c->line_sums,  &c->line_out,     &c->keep_buf,  &c->rem_pts,
+                     &c->rem_lists,  &c->rem_bitmap, &c->rem_leaves,   &c->rem_stats, &c->rem_tasks};
     for (DevBuf* b : all) release(c, *b);
     delete c;
 }

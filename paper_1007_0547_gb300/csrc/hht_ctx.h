@@ -59,6 +59,8 @@ struct hht_ctx {
     const uint8_t* job_keep = nullptr;    // during a job: device keep mask of subtree sharding (or NULL)
     int32_t job_keep_level = 0;
     DevBuf keep_buf;
+    // solution() traversal (hht_detect_removal): points, per-level lists, removed bitmaps, leaves, stats, tasks
+    DevBuf rem_pts, rem_lists, rem_bitmap, rem_leaves, rem_stats, rem_tasks;
     // front end (hht_edges, hht_detect_image): staged image, ALPHA and BETA point lists, their counts
     DevBuf img_buf, edge_pts[2], edge_tot;
     // leaves -> lines (hht_lines): hash table, union-find parents, per-root sums, output

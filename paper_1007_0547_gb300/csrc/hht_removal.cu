@@ -1,0 +1,375 @@
+// The paper's solution() step (Section 3): the traversal is depth-first
+// (quad1..quad4 = NE, NW, SW, SE at every level), and when a cell at the leaf
+// level gets enough votes its voters are plotted and their codes zeroed at
+// every level, so they take no part in any region reached later.  A region's
+// count therefore depends on every cell accepted before it, which makes the
+// traversal order part of the result.
+//
+// GPU form: one warp per (image, half) walks that half's quadtree in the
+// paper's order, with
+//   - an explicit stack (per level: next quadrant, region, list length) in
+//     shared memory;
+//   - one voter list per level in global memory: a child's list is built
+//     from its parent's by the 32 lanes together (exact 4-bit corner codes,
+//     a ballot per 32 voters, positions from popc), skipping removed points;
+//   - a removed-point bitmap (one bit per point) read through L2, so that the
+//     warp sees its own atomic updates.
+// Many images and both halves run as independent warps.  Readings (see the
+// oracle): removal is per half; the `tests` statistic counts the codes
+// actually evaluated (parent voters not removed by then); a region passes
+// when its votes reach T.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "../../include/hht.h"
+#include "hht_ctx.h"
+#include "hht_device.cuh"
+#include "hht_internal.h"
+
+namespace hht {
+namespace {
+
+// One (image, half) of a removal job.
+struct alignas(16) RemovalTask {
+    uint64_t pts;        // offset of the image's points (int16 x, y pairs)
+    uint64_t lists;      // offset of (D + 1) voter lists of n entries
+    uint64_t bitmap;     // offset (in 32-bit words) of the removed-point bitmap
+    uint64_t leaves;     // offset of the leaf output, `cap` entries
+    uint64_t stats;      // offset of [D + 1][4] statistics
+    uint64_t cap;        // leaf capacity: at most n / T + 1 cells can be accepted
+    uint64_t max_steps;  // steps of the walk can never exceed this (see step_bound)
+    int32_t n, lL, D, T;
+    int32_t half, W, H;
+    int32_t pad[3];
+};
+
+// Upper bound on the steps of one walk: every step either evaluates a child
+// (four per region entered) or leaves a region, and at most
+// min(4^l, n * (3 * 2^l + 1)) regions of level l can be entered (a line
+// votes for at most 3 * 2^l + 1 cells of a level).  The walk ends on its own;
+// the bound only turns a corrupted stack into an error instead of a hang.
+uint64_t step_bound(uint64_t n, int D) {
+    double regions = 1.0;
+    for (int l = 1; l < D; ++l) regions += std::min(std::ldexp(1.0, 2 * l), (double)n * (3.0 * std::ldexp(1.0, l) + 1.0));
+    const double steps = 5.0 * regions + 16.0;
+    return steps > 1.8e19 ? ~0ull : (uint64_t)steps;
+}
+
+constexpr int kRemWarps = 4;  // warps per block
+
+__device__ __forceinline__ int64_t scaled_g(int64_t x, int64_t y, int64_t i, int64_t j, int64_t L2, int64_t K) {
+    // K * F at grid vertex (i, j): 4L j + 2x i - 2LK - Kx - Ky (L2 = 2L)
+    return 2 * L2 * j + 2 * x * i - L2 * K - K * x - K * y;
+}
+
+__global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTask* __restrict__ tasks, int ntasks,
+                                                                 const int16_t* __restrict__ pts_all,
+                                                                 uint32_t* __restrict__ lists_all,
+                                                                 uint32_t* __restrict__ bitmap_all,
+                                                                 DevLeaf* __restrict__ leaves_all,
+                                                                 uint64_t* __restrict__ stats_all,
+                                                                 uint64_t* __restrict__ leaf_counts,
+                                                                 DeviceStatus* status) {
+    __shared__ int32_t s_quad[kRemWarps][kMaxDepth + 1];
+    __shared__ uint32_t s_i0[kRemWarps][kMaxDepth + 1], s_j0[kRemWarps][kMaxDepth + 1];
+    __shared__ uint32_t s_len[kRemWarps][kMaxDepth + 1];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int task = blockIdx.x * kRemWarps + w;
+    if (task >= ntasks) return;
+    const RemovalTask tk = tasks[task];
+    const int16_t* pts = pts_all + 2 * tk.pts;
+    uint32_t* lists = lists_all + tk.lists;
+    uint32_t* bitmap = bitmap_all + tk.bitmap;
+    DevLeaf* leaves = leaves_all + tk.leaves;
+    uint64_t* stats = stats_all + tk.stats;
+    const int64_t n = tk.n, D = tk.D, T = tk.T;
+    const int64_t L2 = int64_t(2) << tk.lL, K = int64_t(1) << tk.D;
+    const int half = tk.half;
+
+    // level 0: every line crosses the whole parameter space (points outside
+    // the image fail the image)
+    for (int64_t k = lane; k < n; k += 32) {
+        lists[k] = (uint32_t)k;
+        const int32_t px = pts[2 * k], py = pts[2 * k + 1];
+        if (px < 0 || px >= tk.W || py < 0 || py >= tk.H) atomicOr(&status->err, kErrRange);
+    }
+    for (int64_t k = lane; k < (n + 31) / 32; k += 32) bitmap[k] = 0u;
+    if (lane == 0) {
+        stats[0] = 1;
+        stats[1] = 1;
+        stats[2] = (uint64_t)n;
+        stats[3] = (uint64_t)n;
+        s_quad[w][0] = 0;
+        s_i0[w][0] = 0;
+        s_j0[w][0] = 0;
+        s_len[w][0] = (uint32_t)n;
+    }
+    __syncwarp();
+    uint64_t nleaves = 0;
+    int level = 0;
+    // every region is entered once and left after its fourth child, so the
+    // walk ends (within tk.max_steps steps)
+    bool finished = false;
+    for (uint64_t step = 0; step < tk.max_steps; ++step) {
+        const int q = s_quad[w][level];
+        if (q == 4) {
+            if (level == 0) {
+                finished = true;
+                break;
+            }
+            --level;
+            continue;
+        }
+        __syncwarp();
+        if (lane == 0) s_quad[w][level] = q + 1;
+        const int64_t S = K >> level, h = S >> 1;
+        const int64_t ci = (int64_t)s_i0[w][level] + ((q == NE || q == SE) ? h : 0);
+        const int64_t cj = (int64_t)s_j0[w][level] + ((q == NE || q == NW) ? h : 0);
+        const uint32_t plen = s_len[w][level];
+        const uint32_t* parent = lists + (uint64_t)level * (uint64_t)n;
+        uint32_t* child = lists + (uint64_t)(level + 1) * (uint64_t)n;
+        uint32_t cnt = 0, evaluated = 0;
+        for (uint32_t base = 0; base < plen; base += 32) {
+            const uint32_t idx = base + lane;
+            bool alive = false, cross = false;
+            uint32_t v = 0;
+            if (idx < plen) {
+                v = __ldcg(&parent[idx]);
+                alive = ((__ldcg(&bitmap[v >> 5]) >> (v & 31u)) & 1u) == 0u;
+            }
+            if (alive) {
+                const int64_t px = pts[2 * (uint64_t)v], py = pts[2 * (uint64_t)v + 1];
+                const int64_t x = half ? py : px, y = half ? px : py;
+                // getcode(): NE, NW, SW, SE corners below the line
+                const uint32_t code = (scaled_g(x, y, ci + h, cj + h, L2, K) < 0 ? 8u : 0u) |
+                                      (scaled_g(x, y, ci, cj + h, L2, K) < 0 ? 4u : 0u) |
+                                      (scaled_g(x, y, ci, cj, L2, K) < 0 ? 2u : 0u) |
+                                      (scaled_g(x, y, ci + h, cj, L2, K) < 0 ? 1u : 0u);
+                cross = code != 0u && code != 15u;
+            }
+            evaluated += __popc(__ballot_sync(0xffffffffu, alive));
+            const uint32_t m = __ballot_sync(0xffffffffu, cross);
+            if (cross) child[cnt + __popc(m & lt)] = v;
+            cnt += __popc(m);
+        }
+        __syncwarp();
+        const int cl = level + 1;
+        if (lane == 0) {
+            stats[4 * cl + 0] += 1;
+            stats[4 * cl + 2] += cnt;
+            stats[4 * cl + 3] += evaluated;
+        }
+        if ((int64_t)cnt >= T) {
+            if (lane == 0) stats[4 * cl + 1] += 1;
+            if (cl == D) {
+                // solution(): plot the voters and remove them from later regions
+                if (lane == 0) {
+                    if (nleaves < tk.cap) {
+                        DevLeaf f;
+                        f.half = (uint32_t)half;
+                        f.i = (uint32_t)ci;
+                        f.j = (uint32_t)cj;
+                        f.votes = cnt;
+                        leaves[nleaves] = f;
+                    } else {
+                        atomicOr(&status->err, kErrOverflow);
+                    }
+                }
+                ++nleaves;
+                for (uint32_t k = lane; k < cnt; k += 32) {
+                    const uint32_t v = __ldcg(&child[k]);
+                    atomicOr(&bitmap[v >> 5], 1u << (v & 31u));
+                }
+                __threadfence();
+                __syncwarp();
+            } else {
+                if (lane == 0) {
+                    s_quad[w][cl] = 0;
+                    s_i0[w][cl] = (uint32_t)ci;
+                    s_j0[w][cl] = (uint32_t)cj;
+                    s_len[w][cl] = cnt;
+                }
+                __syncwarp();
+                level = cl;
+            }
+        }
+    }
+    if (!finished && lane == 0) atomicOr(&status->err, kErrInvariant);
+    if (lane == 0) leaf_counts[task] = nleaves;
+}
+
+#define CKR(call)                                    \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_); \
+    } while (0)
+#define RKR(call)                    \
+    do {                             \
+        int r_ = (call);             \
+        if (r_ != HHT_OK) return r_; \
+    } while (0)
+
+int check_removal_image(const hht_image& im) {
+    if (im.n < 0 || im.n > INT32_MAX || (im.n > 0 && !im.points)) return HHT_E_ARG;
+    if (im.W < 1 || im.H < 1 || im.W > HHT_MAX_SIDE || im.H > HHT_MAX_SIDE) return HHT_E_ARG;
+    if (im.depth < 1 || im.depth > HHT_MAX_DEPTH || im.T < 1) return HHT_E_ARG;
+    return HHT_OK;
+}
+
+// Run the solution() traversal of `count` images; outs[k] as hht_detect
+// (leaves: accepted cells, half 0's then half 1's, each in traversal order);
+// plotted[k] (may be NULL) receives 2 * n flags (half-major).
+int run_removal(hht_ctx* c, const hht_image* im, int count, hht_result* outs, uint8_t* const* plotted) {
+    cudaStream_t st = c->stream;
+    std::vector<RemovalTask> tasks((size_t)2 * count);
+    uint64_t pts_len = 0, lists_len = 0, bitmap_len = 0, leaves_len = 0, stats_len = 0;
+    std::vector<uint64_t> pts_off(count);
+    for (int g = 0; g < count; ++g) {
+        const int lL = ceil_log2_i(std::max(im[g].W, im[g].H));
+        pts_off[g] = pts_len;
+        const uint64_t n = (uint64_t)im[g].n;
+        for (int h = 0; h < 2; ++h) {
+            RemovalTask& t = tasks[(size_t)2 * g + h];
+            std::memset(&t, 0, sizeof t);
+            t.pts = pts_len;
+            t.lists = lists_len;
+            t.bitmap = bitmap_len;
+            t.leaves = leaves_len;
+            t.stats = stats_len;
+            t.cap = n / (uint64_t)im[g].T + 1;
+            t.max_steps = step_bound(n, im[g].depth);
+            t.n = (int32_t)n;
+            t.W = im[g].W;
+            t.H = im[g].H;
+            t.lL = lL;
+            t.D = im[g].depth;
+            t.T = im[g].T;
+            t.half = h;
+            lists_len += (uint64_t)(im[g].depth + 1) * std::max<uint64_t>(n, 1);
+            bitmap_len += (n + 31) / 32 + 1;
+            leaves_len += t.cap;
+            stats_len += (uint64_t)(im[g].depth + 1) * 4;
+        }
+        pts_len += n;
+    }
+    RKR(ensure(c, c->rem_pts, std::max<uint64_t>(pts_len, 1) * sizeof(hht_point)));
+    RKR(ensure(c, c->rem_lists, std::max<uint64_t>(lists_len, 1) * sizeof(uint32_t)));
+    RKR(ensure(c, c->rem_bitmap, std::max<uint64_t>(bitmap_len, 1) * sizeof(uint32_t)));
+    RKR(ensure(c, c->rem_leaves, std::max<uint64_t>(leaves_len, 1) * sizeof(DevLeaf)));
+    RKR(ensure(c, c->rem_stats, std::max<uint64_t>(stats_len, 1) * sizeof(uint64_t)));
+    RKR(ensure(c, c->rem_tasks, tasks.size() * sizeof(RemovalTask) + (size_t)2 * count * sizeof(uint64_t)));
+    RKR(ensure(c, c->status, sizeof(DeviceStatus)));
+    for (int g = 0; g < count; ++g)
+        if (im[g].n > 0)
+            CKR(cudaMemcpyAsync((hht_point*)c->rem_pts.p + pts_off[g], im[g].points, (size_t)im[g].n * sizeof(hht_point),
+                                cudaMemcpyDefault, st));
+    CKR(cudaMemcpyAsync(c->rem_tasks.p, tasks.data(), tasks.size() * sizeof(RemovalTask), cudaMemcpyHostToDevice, st));
+    CKR(cudaMemsetAsync(c->rem_stats.p, 0, std::max<uint64_t>(stats_len, 1) * sizeof(uint64_t), st));
+    CKR(cudaMemsetAsync(c->status.p, 0, sizeof(DeviceStatus), st));
+    uint64_t* d_counts = (uint64_t*)((char*)c->rem_tasks.p + tasks.size() * sizeof(RemovalTask));
+    const int ntasks = 2 * count;
+    const int grid = (ntasks + kRemWarps - 1) / kRemWarps;
+    removal_kernel<<<grid, 32 * kRemWarps, 0, st>>>((const RemovalTask*)c->rem_tasks.p, ntasks,
+                                                     (const int16_t*)c->rem_pts.p, (uint32_t*)c->rem_lists.p,
+                                                     (uint32_t*)c->rem_bitmap.p, (DevLeaf*)c->rem_leaves.p,
+                                                     (uint64_t*)c->rem_stats.p, d_counts, (DeviceStatus*)c->status.p);
+    CKR(cudaGetLastError());
+    c->prof.launches += 1;
+    std::vector<uint64_t> counts((size_t)ntasks), h_stats(stats_len);
+    DeviceStatus hs{};
+    CKR(cudaMemcpyAsync(counts.data(), d_counts, counts.size() * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    CKR(cudaMemcpyAsync(h_stats.data(), c->rem_stats.p, stats_len * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    CKR(cudaMemcpyAsync(&hs, c->status.p, sizeof hs, cudaMemcpyDeviceToHost, st));
+    CKR(cudaStreamSynchronize(st));
+    if (hs.err & kErrRange) return HHT_E_RANGE;
+    if (hs.err) return HHT_E_CUDA;
+    int rc_all = HHT_OK;
+    for (int g = 0; g < count; ++g) {
+        hht_result& r = outs[g];
+        const int D = im[g].depth;
+        r.depth = D;
+        r.L = 1 << ceil_log2_i(std::max(im[g].W, im[g].H));
+        std::memset(r.stats, 0, sizeof r.stats);
+        uint64_t nl = 0;
+        for (int h = 0; h < 2; ++h) {
+            const RemovalTask& t = tasks[(size_t)2 * g + h];
+            for (int l = 0; l <= D; ++l) {
+                const uint64_t* s = &h_stats[t.stats + 4 * (uint64_t)l];
+                r.stats[h][l].tested = s[0];
+                r.stats[h][l].passed = s[1];
+                r.stats[h][l].votes = s[2];
+                r.stats[h][l].tests = s[3];
+            }
+            nl += counts[(size_t)2 * g + h];
+        }
+        r.n_leaves = nl;
+        if (nl > r.leaf_capacity || (nl > 0 && !r.leaves)) {
+            r.status = HHT_E_CAPACITY;
+        } else {
+            r.status = HHT_OK;
+            uint64_t at = 0;
+            for (int h = 0; h < 2; ++h) {
+                const RemovalTask& t = tasks[(size_t)2 * g + h];
+                const uint64_t k = counts[(size_t)2 * g + h];
+                if (k > 0)
+                    RKR(copy_out(c, r.leaves + at, (const DevLeaf*)c->rem_leaves.p + t.leaves, k * sizeof(hht_leaf)));
+                at += k;
+            }
+        }
+        if (plotted && plotted[g] && im[g].n > 0) {
+            // bits -> one byte per point and half, on the host
+            std::vector<uint32_t> bits;
+            for (int h = 0; h < 2; ++h) {
+                const RemovalTask& t = tasks[(size_t)2 * g + h];
+                bits.resize((size_t)(im[g].n + 31) / 32);
+                CKR(cudaMemcpyAsync(bits.data(), (const uint32_t*)c->rem_bitmap.p + t.bitmap,
+                                    bits.size() * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+                CKR(cudaStreamSynchronize(st));
+                std::vector<uint8_t> bytes((size_t)im[g].n);
+                for (int64_t k = 0; k < im[g].n; ++k) bytes[k] = (bits[k >> 5] >> (k & 31)) & 1u;
+                CKR(cudaMemcpyAsync(plotted[g] + (size_t)h * im[g].n, bytes.data(), bytes.size(), cudaMemcpyDefault,
+                                    st));
+                CKR(cudaStreamSynchronize(st));
+            }
+        }
+        if (r.status != HHT_OK && rc_all == HHT_OK) rc_all = r.status;
+    }
+    CKR(cudaStreamSynchronize(st));
+    return rc_all;
+}
+
+}  // namespace
+}  // namespace hht
+
+using namespace hht;
+
+extern "C" {
+
+int hht_detect_removal(hht_ctx* c, const hht_point* points, int64_t n, int32_t W, int32_t H, int32_t depth, int32_t T,
+                       hht_result* out, uint8_t* plotted) {
+    if (!c || !out) return HHT_E_ARG;
+    hht_image im{points, n, W, H, depth, T};
+    RKR(check_removal_image(im));
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    uint8_t* pl[1] = {plotted};
+    return run_removal(c, &im, 1, out, pl);
+}
+
+int hht_detect_removal_batch(hht_ctx* c, const hht_image* images, int32_t count, hht_result* outs) {
+    if (!c || !outs || count < 0 || (count > 0 && !images) || count > (1 << 20)) return HHT_E_ARG;
+    for (int g = 0; g < count; ++g) RKR(check_removal_image(images[g]));
+    if (count == 0) return HHT_OK;
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    return run_removal(c, images, count, outs, nullptr);
+}
+
+}  // extern "C"

@@ -33,7 +33,7 @@ EXPORTS = ("hht_create", "hht_destroy", "hht_detect", "hht_detect_batch", "hht_f
            "hht_poll", "hht_progress", "hht_profile_enable", "hht_profile_read", "hht_strerror", "hht_version",
            "hht_detect_noalloc", "hht_autotune", "hht_set_tuning", "hht_set_batch_mode", "hht_fetch_all_leaves",
            "hht_inject_fault", "hht_set_predicate", "hht_edges", "hht_detect_image", "hht_lines",
-           "hht_detect_subtrees")
+           "hht_detect_subtrees", "hht_detect_removal", "hht_detect_removal_batch")
 BATCH_LEVELS, BATCH_PERSISTENT = 0, 1
 FAULT_NONE, FAULT_WITHHOLD_SCAN_TILE = 0, 1
 PREDICATE_EXACT, PREDICATE_FHT = 0, 1
@@ -125,6 +125,10 @@ def load(path: Optional[str] = None):
     lib.hht_inject_fault.restype = ctypes.c_int
     lib.hht_set_predicate.argtypes = [vp, i32]
     lib.hht_set_predicate.restype = ctypes.c_int
+    lib.hht_detect_removal.argtypes = [vp, vp, i64, i32, i32, i32, i32, ctypes.POINTER(_Result), vp]
+    lib.hht_detect_removal.restype = ctypes.c_int
+    lib.hht_detect_removal_batch.argtypes = [vp, ctypes.POINTER(_Image), i32, ctypes.POINTER(_Result)]
+    lib.hht_detect_removal_batch.restype = ctypes.c_int
     lib.hht_detect_subtrees.argtypes = [vp, vp, i64, i32, i32, i32, i32, i32, vp, ctypes.POINTER(_Result)]
     lib.hht_detect_subtrees.restype = ctypes.c_int
     lib.hht_lines.argtypes = [vp, i32, vp, u64, ctypes.POINTER(u64)]
@@ -472,6 +476,47 @@ class Context:
         del keep
         k = int(r.n_leaves) if rc == HHT_OK else 0
         return Result(buf[:k], _stats_of(r), int(r.depth), int(r.L), rc)
+
+    def detect_removal(self, points, W: int, H: int, depth: int, T: int, with_plotted: bool = True):
+        """Detection with the solution() step (hht_detect_removal): accepted
+        cells in visiting order and, with with_plotted, uint8 [2, n] flags of
+        the plotted points per half.  Returns (Result, plotted or None)."""
+        lib = load()
+        p = _Points(points)
+        cap = max(1, 2 * (p.n // max(int(T), 1) + 1))
+        buf = np.zeros((cap, 4), dtype=np.int32)
+        plotted = np.zeros((2, max(p.n, 1)), dtype=np.uint8) if with_plotted else None
+        r = _Result()
+        r.leaves = buf.ctypes.data
+        r.leaf_capacity = cap
+        rc = lib.hht_detect_removal(self._h, p.ptr, p.n, int(W), int(H), int(depth), int(T), ctypes.byref(r),
+                                    plotted.ctypes.data if with_plotted else None)
+        if rc != HHT_OK:
+            raise HhtError(rc, "hht_detect_removal")
+        k = int(r.n_leaves)
+        return Result(buf[:k], _stats_of(r), int(r.depth), int(r.L), rc), (plotted[:, : p.n] if with_plotted else None)
+
+    def detect_removal_batch(self, images: Sequence[Tuple]) -> List[Result]:
+        """hht_detect_removal_batch over (points, W, H, depth, T) tuples."""
+        lib = load()
+        pts = [_Points(im[0]) for im in images]
+        arr = (_Image * len(images))()
+        outs = (_Result * len(images))()
+        bufs = []
+        for k, (im, p) in enumerate(zip(images, pts)):
+            arr[k].points = p.ptr
+            arr[k].n = p.n
+            arr[k].W, arr[k].H, arr[k].depth, arr[k].T = (int(v) for v in im[1:5])
+            cap = max(1, 2 * (p.n // max(int(im[4]), 1) + 1))
+            b = np.zeros((cap, 4), dtype=np.int32)
+            bufs.append(b)
+            outs[k].leaves = b.ctypes.data
+            outs[k].leaf_capacity = cap
+        rc = lib.hht_detect_removal_batch(self._h, arr, len(images), outs)
+        if rc != HHT_OK:
+            raise HhtError(rc, "hht_detect_removal_batch")
+        return [Result(b[: int(o.n_leaves)], _stats_of(o), int(o.depth), int(o.L), int(o.status))
+                for b, o in zip(bufs, outs)]
 
     def detect_subtrees(self, points, W: int, H: int, depth: int, T: int, split_level: int, keep,
                         leaves_on_device: bool = True) -> Result:

@@ -30,7 +30,8 @@ def test_header_declares_the_api():
                                 "hht_strerror", "hht_version", "hht_detect_noalloc", "hht_autotune",
                                 "hht_set_tuning", "hht_set_batch_mode", "hht_fetch_all_leaves",
                                 "hht_inject_fault", "hht_set_predicate", "hht_edges", "hht_detect_image",
-                                "hht_lines", "hht_detect_subtrees"}
+                                "hht_lines", "hht_detect_subtrees", "hht_detect_removal",
+                                "hht_detect_removal_batch"}
 
 
 def test_library_exports_every_declared_symbol(lib):
@@ -66,6 +67,8 @@ def test_host_only_calls(lib):
     assert lib.hht_detect_image(None, None, 8, 8, 10, 3, 1, ctypes.byref(r)) == hht.HHT_E_ARG
     assert lib.hht_lines(None, 0, None, 0, ctypes.byref(na)) == hht.HHT_E_ARG
     assert lib.hht_detect_subtrees(None, None, 0, 8, 8, 3, 1, 1, None, ctypes.byref(r)) == hht.HHT_E_ARG
+    assert lib.hht_detect_removal(None, None, 0, 8, 8, 3, 1, ctypes.byref(r), None) == hht.HHT_E_ARG
+    assert lib.hht_detect_removal_batch(None, None, 0, None) == hht.HHT_E_ARG
 
 
 def test_result_struct_layout_matches_header(lib):
