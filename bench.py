@@ -258,6 +258,7 @@ def main():
     ap.add_argument("--no-persistent", action="store_true")
     ap.add_argument("--no-fht", action="store_true", help="skip the prior-art FHT circle-test comparison")
     ap.add_argument("--no-front-end", action="store_true", help="skip the front-end and line-extraction timings")
+    ap.add_argument("--no-removal", action="store_true", help="skip the solution() (voter removal) timing")
     ap.add_argument("--serve", action="store_true", help="open-loop serving benchmark instead of the batch line")
     ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--serve-load", type=float, default=0.8, help="offered rate as a fraction of the saturated rate")
@@ -486,6 +487,27 @@ def main():
                  "detect_image_ms": min(d_ms), "detect_image_tests": int(dres.total_tests()),
                  "leaves": int(dres.n_leaves), "lines_ms": min(l_ms), "lines": int(len(glines))}
 
+    # ---------------------------------------------------------------- solution() traversal, same images
+    removal = None
+    if not args.no_removal and rank == 0:
+        ctx.detect_removal_batch(dev_images)  # allocations
+        torch.cuda.synchronize()
+        r_ms = []
+        for _ in range(2):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rres = ctx.detect_removal_batch(dev_images)
+            e1.record(stream)
+            e1.synchronize()
+            r_ms.append(e0.elapsed_time(e1))
+        rm = min(r_ms)
+        rtests = sum(r.total_tests() for r in rres)
+        removal = {"what": "depth-first traversal with the paper's solution() step (voters of accepted cells removed "
+                           "from later regions); one warp per image and half",
+                   "ms_per_step": rm, "tests_per_s": rtests / (rm / 1e3), "images_per_s": len(dev_images) / (rm / 1e3),
+                   "accepted_cells": int(sum(r.n_leaves for r in rres))}
+
     # ---------------------------------------------------------------- roofline of the pass kernel
     peak, peak_kind = read_peaks()
     achieved = (prof["pass_bytes"] / 1e9) / (prof["pass_ms"] / 1e3) if prof["pass_ms"] > 0 else 0.0
@@ -521,6 +543,7 @@ def main():
         "persistent_form": persistent,
         "fht_form": fht,
         "front_end": front,
+        "removal_form": removal,
         "e2e": e2e,
         "roofline": roofline,
         "cpu_baseline": cpu,
