@@ -136,28 +136,43 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
         const uint32_t* parent = lists + (uint64_t)level * (uint64_t)n;
         uint32_t* child = lists + (uint64_t)(level + 1) * (uint64_t)n;
         uint32_t cnt = 0, evaluated = 0;
-        for (uint32_t base = 0; base < plen; base += 32) {
-            const uint32_t idx = base + lane;
-            bool alive = false, cross = false;
-            uint32_t v = 0;
-            if (idx < plen) {
-                v = __ldcg(&parent[idx]);
-                alive = ((__ldcg(&bitmap[v >> 5]) >> (v & 31u)) & 1u) == 0u;
+        // eight groups of 32 voters per iteration: the list entries, then their
+        // bitmap words, then their points are loaded as independent requests
+        constexpr int U = 8;
+        for (uint32_t base = 0; base < plen; base += 32 * U) {
+            uint32_t v[U], bw[U], xy[U];
+            bool in[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t idx = base + 32 * u + lane;
+                in[u] = idx < plen;
+                v[u] = in[u] ? __ldcg(&parent[idx]) : 0u;
             }
-            if (alive) {
-                const int64_t px = pts[2 * (uint64_t)v], py = pts[2 * (uint64_t)v + 1];
-                const int64_t x = half ? py : px, y = half ? px : py;
-                // getcode(): NE, NW, SW, SE corners below the line
-                const uint32_t code = (scaled_g(x, y, ci + h, cj + h, L2, K) < 0 ? 8u : 0u) |
-                                      (scaled_g(x, y, ci, cj + h, L2, K) < 0 ? 4u : 0u) |
-                                      (scaled_g(x, y, ci, cj, L2, K) < 0 ? 2u : 0u) |
-                                      (scaled_g(x, y, ci + h, cj, L2, K) < 0 ? 1u : 0u);
-                cross = code != 0u && code != 15u;
+#pragma unroll
+            for (int u = 0; u < U; ++u) bw[u] = in[u] ? __ldcg(&bitmap[v[u] >> 5]) : 0u;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                in[u] = in[u] && ((bw[u] >> (v[u] & 31u)) & 1u) == 0u;  // not removed
+                xy[u] = in[u] ? __ldg(reinterpret_cast<const uint32_t*>(pts) + v[u]) : 0u;
             }
-            evaluated += __popc(__ballot_sync(0xffffffffu, alive));
-            const uint32_t m = __ballot_sync(0xffffffffu, cross);
-            if (cross) child[cnt + __popc(m & lt)] = v;
-            cnt += __popc(m);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                bool cross = false;
+                if (in[u]) {
+                    const int64_t px = (int16_t)(xy[u] & 0xffffu), py = (int16_t)(xy[u] >> 16);
+                    const int64_t x = half ? py : px, y = half ? px : py;
+                    // getcode(): NE, NW, SW, SE corners below the line
+                    const uint32_t code = (scaled_g(x, y, ci + h, cj + h, L2, K) < 0 ? 8u : 0u) |
+                                          (scaled_g(x, y, ci, cj + h, L2, K) < 0 ? 4u : 0u) |
+                                          (scaled_g(x, y, ci, cj, L2, K) < 0 ? 2u : 0u) |
+                                          (scaled_g(x, y, ci + h, cj, L2, K) < 0 ? 1u : 0u);
+                    cross = code != 0u && code != 15u;
+                }
+                evaluated += __popc(__ballot_sync(0xffffffffu, in[u]));
+                const uint32_t m = __ballot_sync(0xffffffffu, cross);
+                if (cross) child[cnt + __popc(m & lt)] = v[u];
+                cnt += __popc(m);
+            }
         }
         __syncwarp();
         const int cl = level + 1;
