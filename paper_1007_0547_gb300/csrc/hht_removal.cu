@@ -136,9 +136,9 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
         const uint32_t* parent = lists + (uint64_t)level * (uint64_t)n;
         uint32_t* child = lists + (uint64_t)(level + 1) * (uint64_t)n;
         uint32_t cnt = 0, evaluated = 0;
-        // eight groups of 32 voters per iteration: the list entries, then their
+        // four groups of 32 voters per iteration: the list entries, then their
         // bitmap words, then their points are loaded as independent requests
-        constexpr int U = 8;
+        constexpr int U = 4;
         for (uint32_t base = 0; base < plen; base += 32 * U) {
             uint32_t v[U], bw[U], xy[U];
             bool in[U];
