@@ -112,6 +112,30 @@ typedef struct hht_ctx hht_ctx;
  */
 int hht_create(hht_ctx **out, int device, void *cuda_stream, uint64_t mem_budget_bytes);
 
+/*
+ * A caller's device allocator, for processes whose device memory belongs to
+ * another allocator (for instance PyTorch's caching allocator): alloc returns
+ * at least `bytes` of device memory of the context's device, 256-byte aligned
+ * (NULL when it cannot), for use on `cuda_stream`; free takes back a block
+ * with the size it was asked for.  Both are called only from inside hht_*
+ * calls on the context, on the calling thread; a block is freed only after
+ * the context's stream has finished with it.
+ */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *cuda_stream, void *user);
+    void (*free)(void *ptr, size_t bytes, void *cuda_stream, void *user);
+    void *user;
+} hht_allocator;
+
+/*
+ * hht_create with every device allocation of the context (its scratch
+ * memory) made through `allocator` (NULL: cudaMalloc and cudaFree, as
+ * hht_create).  The budget still caps what the context holds.
+ * Errors: as hht_create, and HHT_E_ARG when alloc or free is NULL.
+ */
+int hht_create_with_allocator(hht_ctx **out, int device, void *cuda_stream, uint64_t mem_budget_bytes,
+                              const hht_allocator *allocator);
+
 /* Destroy a context (NULL is ignored).  Waits for the context's stream. */
 void hht_destroy(hht_ctx *ctx);
 

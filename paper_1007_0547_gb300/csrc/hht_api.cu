@@ -24,6 +24,7 @@
 #include "hht_internal.h"
 #include "hht_ctx.h"
 #include "hht_serve.h"
+#include "hht_trace.h"
 
 using namespace hht;
 
@@ -32,6 +33,24 @@ namespace hht {
 int cuda_fail(cudaError_t e) {
     if (e == cudaErrorMemoryAllocation) return HHT_E_NOMEM;
     return HHT_E_CUDA;
+}
+
+// Device memory of the context: the caller's allocator when it gave one
+// (hht_create_with_allocator), else cudaMalloc / cudaFree.  Frees happen
+// after the context's stream has been synchronised.
+static cudaError_t dev_alloc(hht_ctx* c, void** p, size_t bytes) {
+    if (c->has_allocator) {
+        *p = c->allocator.alloc(bytes, (void*)c->stream, c->allocator.user);
+        return (*p && ((uintptr_t)*p % 256) == 0) ? cudaSuccess : cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+static void dev_free(hht_ctx* c, void* p, size_t bytes) {
+    if (!p) return;
+    if (c->has_allocator)
+        c->allocator.free(p, bytes, (void*)c->stream, c->allocator.user);
+    else
+        cudaFree(p);
 }
 
 // Grow a device buffer to at least `bytes` (contents are not preserved).
@@ -46,17 +65,18 @@ int ensure(hht_ctx* c, DevBuf& b, size_t bytes, bool zero) {
     }
     if (b.p) {
         cudaStreamSynchronize(c->stream);
-        cudaFree(b.p);
+        dev_free(c, b.p, b.bytes);
         c->held -= b.bytes;
         b.p = nullptr;
         b.bytes = 0;
     }
     void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, want);
+    cudaError_t e = dev_alloc(c, &p, want);
     if (e != cudaSuccess) {
         cudaGetLastError();
+        if (p) dev_free(c, p, want);  // an allocator's block without the needed alignment
         if (c->debug)
-            fprintf(stderr, "[hht] cudaMalloc of %.3f GB failed (context holds %.3f GB)\n", want / 1e9, c->held / 1e9);
+            fprintf(stderr, "[hht] allocation of %.3f GB failed (context holds %.3f GB)\n", want / 1e9, c->held / 1e9);
         return HHT_E_NOMEM;
     }
     b.p = p;
@@ -80,14 +100,15 @@ int ensure_keep(hht_ctx* c, DevBuf& b, size_t bytes, size_t keep) {
         if (c->held + want > c->budget) return HHT_E_NOMEM;
     }
     void* p = nullptr;
-    if (cudaMalloc(&p, want) != cudaSuccess) {
+    if (dev_alloc(c, &p, want) != cudaSuccess) {
         cudaGetLastError();
+        if (p) dev_free(c, p, want);
         return HHT_E_NOMEM;
     }
     c->held += want;
     cudaError_t e = cudaMemcpyAsync(p, b.p, std::min(keep, b.bytes), cudaMemcpyDeviceToDevice, c->stream);
     cudaStreamSynchronize(c->stream);
-    cudaFree(b.p);
+    dev_free(c, b.p, b.bytes);
     c->held -= b.bytes;
     b.p = p;
     b.bytes = want;
@@ -96,7 +117,7 @@ int ensure_keep(hht_ctx* c, DevBuf& b, size_t bytes, size_t keep) {
 
 void release(hht_ctx* c, DevBuf& b) {
     if (b.p) {
-        cudaFree(b.p);
+        dev_free(c, b.p, b.bytes);
         c->held -= b.bytes;
     }
     b.p = nullptr;
@@ -411,6 +432,7 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
         f.n_images = count;
         f.Dmax = Dmax;
         {
+            TraceRange tr_k("persistent level loop");
             ProfScope ps(c, 2);
             RK(launch_persistent_graph(c, f, i64, c->num_sms * occ_p));
         }
@@ -431,6 +453,7 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
         }
     }
     if (!persistent) {
+        TraceRange tr_k("stage");
         ProfScope ps(c, 0);
         if (launch_stage((const int16_t*)c->pts.p, total, (const Unit*)c->units.p, count,
                          (const uint64_t*)c->img_start.p, (const uint32_t*)c->img_unit.p, (Voter*)c->vox[0].p,
@@ -443,6 +466,7 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
     // ---- level loop (sizes recorded as the plan of the persistent form)
     uint64_t plan_rec = (uint64_t)n_units, plan_vox = v0_len;
     for (int s = 1; s <= Dmax && !persistent; ++s) {
+        TraceRange tr_level(level_name(s));
         const int pi = (s - 1) & 1, ci = s & 1;
         const uint64_t P = c->h_infos[s - 1].n_regions;
         if (P == 0) break;
@@ -488,6 +512,7 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
         // select's capacity test on the voter stream is re-done below with the exact size
         a.cap_voters = UINT64_MAX;
         {
+            TraceRange tr_k("select");
             ProfScope ps(c, 1);
             if (launch_select(a, 256, std::max(sel_grid, 1), st) != 0) return HHT_E_CUDA;
         }
@@ -524,6 +549,7 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
         const uint64_t want_blocks = (nin + tile - 1) / tile;
         const int pass_grid = (int)std::min<uint64_t>(want_blocks, (uint64_t)c->num_sms * occ);
         {
+            TraceRange tr_k("pass");
             ProfScope ps(c, 2);
             if (launch_pass(a, i64, std::max(pass_grid, 1), st, shape, fht) != 0) return HHT_E_CUDA;
         }
@@ -687,6 +713,7 @@ int run_waves(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int 
 }
 
 int run_job(hht_ctx* c, const hht_image* im, int count, hht_result* outs, const uint8_t* halves = nullptr) {
+    TraceRange tr("hht detection job");
     c->job_halves = halves;
     c->job_serial += 1;
     c->job_off.assign(count, 0);
@@ -704,7 +731,13 @@ int run_job(hht_ctx* c, const hht_image* im, int count, hht_result* outs, const 
 extern "C" {
 
 int hht_create(hht_ctx** out, int device, void* cuda_stream, uint64_t mem_budget_bytes) {
+    return hht_create_with_allocator(out, device, cuda_stream, mem_budget_bytes, nullptr);
+}
+
+int hht_create_with_allocator(hht_ctx** out, int device, void* cuda_stream, uint64_t mem_budget_bytes,
+                              const hht_allocator* allocator) {
     if (!out) return HHT_E_ARG;
+    if (allocator && (!allocator->alloc || !allocator->free)) return HHT_E_ARG;
     *out = nullptr;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
@@ -716,6 +749,10 @@ int hht_create(hht_ctx** out, int device, void* cuda_stream, uint64_t mem_budget
     hht_ctx* c = new (std::nothrow) hht_ctx();
     if (!c) return HHT_E_NOMEM;
     c->device = device;
+    if (allocator) {
+        c->allocator = *allocator;
+        c->has_allocator = true;
+    }
     c->debug = getenv("HHT_DEBUG") && getenv("HHT_DEBUG")[0] == '1';
     c->stream = (cudaStream_t)cuda_stream;
     c->budget = mem_budget_bytes;

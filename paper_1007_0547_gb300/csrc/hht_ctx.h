@@ -29,6 +29,8 @@ inline int ceil_log2_i(int v) {
 struct hht_ctx {
     using DevBuf = hht::DevBuf;
     int device = 0;
+    hht_allocator allocator{};   // the caller's device allocator (hht_create_with_allocator)
+    bool has_allocator = false;
     bool debug = false;          // HHT_DEBUG=1: wave and allocation trace on stderr
     bool copy_engine_only = false;  // HHT_COPY_ENGINE=1: leaves to host memory by cudaMemcpyAsync only
     uint64_t wave_cap = 0;       // largest wave estimate known to fit (0 = none failed yet)

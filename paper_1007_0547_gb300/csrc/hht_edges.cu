@@ -29,6 +29,7 @@
 #include "hht_ctx.h"
 #include "hht_device.cuh"
 #include "hht_internal.h"
+#include "hht_trace.h"
 
 int hht_internal_run_job_halves(hht_ctx* c, const hht_image* im, int count, hht_result* outs, const uint8_t* halves);
 
@@ -232,6 +233,7 @@ bool args_ok(const uint8_t* image, int32_t W, int32_t H, int32_t threshold) {
 // *na and *nb receive the counts.  The image is host or device memory.
 int run_edges(hht_ctx* c, const uint8_t* image, int32_t W, int32_t H, int32_t threshold, uint64_t* na,
               uint64_t* nb) {
+    TraceRange tr("front end");
     cudaStream_t st = c->stream;
     const uint64_t npix = (uint64_t)W * (uint64_t)H;
     const uint8_t* d_img = image;

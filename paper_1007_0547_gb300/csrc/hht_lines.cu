@@ -32,6 +32,7 @@
 #include "hht_ctx.h"
 #include "hht_device.cuh"
 #include "hht_internal.h"
+#include "hht_trace.h"
 
 namespace hht {
 namespace {
@@ -288,6 +289,7 @@ __global__ void __launch_bounds__(kEmitTPB) lines_emit_kernel(const DevLeaf* __r
 using namespace hht;
 
 extern "C" int hht_lines(hht_ctx* c, int32_t index, hht_line* lines, uint64_t capacity, uint64_t* n_lines) {
+    hht::TraceRange tr("leaves to lines");
     if (!c || !n_lines) return HHT_E_ARG;
     std::lock_guard<std::mutex> lk(c->mu);
     if (index < 0 || (size_t)index >= c->job_n.size()) return HHT_E_ARG;

@@ -31,6 +31,7 @@
 #include "hht_ctx.h"
 #include "hht_device.cuh"
 #include "hht_internal.h"
+#include "hht_trace.h"
 
 namespace hht {
 namespace {
@@ -242,6 +243,7 @@ int check_removal_image(const hht_image& im) {
 // (leaves: accepted cells, half 0's then half 1's, each in traversal order);
 // plotted[k] (may be NULL) receives 2 * n flags (half-major).
 int run_removal(hht_ctx* c, const hht_image* im, int count, hht_result* outs, uint8_t* const* plotted) {
+    TraceRange tr("solution() walk");
     cudaStream_t st = c->stream;
     std::vector<RemovalTask> tasks((size_t)2 * count);
     uint64_t pts_len = 0, lists_len = 0, bitmap_len = 0, leaves_len = 0, stats_len = 0;

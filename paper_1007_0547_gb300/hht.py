@@ -33,7 +33,8 @@ EXPORTS = ("hht_create", "hht_destroy", "hht_detect", "hht_detect_batch", "hht_f
            "hht_poll", "hht_progress", "hht_profile_enable", "hht_profile_read", "hht_strerror", "hht_version",
            "hht_detect_noalloc", "hht_autotune", "hht_set_tuning", "hht_set_batch_mode", "hht_fetch_all_leaves",
            "hht_inject_fault", "hht_set_predicate", "hht_edges", "hht_detect_image", "hht_lines",
-           "hht_detect_subtrees", "hht_detect_removal", "hht_detect_removal_batch")
+           "hht_detect_subtrees", "hht_detect_removal", "hht_detect_removal_batch",
+           "hht_create_with_allocator")
 BATCH_LEVELS, BATCH_PERSISTENT = 0, 1
 FAULT_NONE, FAULT_WITHHOLD_SCAN_TILE = 0, 1
 PREDICATE_EXACT, PREDICATE_FHT = 0, 1
@@ -73,6 +74,32 @@ LINE_DTYPE = np.dtype([("half", np.uint32), ("i", np.uint32), ("j", np.uint32), 
                        ("sum_i2", np.uint64), ("sum_j2", np.uint64)])
 
 
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class _Allocator(ctypes.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("user", ctypes.c_void_p)]
+
+
+def _torch_allocator(device: int) -> _Allocator:
+    """The library's scratch memory from PyTorch's caching allocator (on the
+    context's stream), so that it shows up in torch's memory statistics and
+    its blocks return to torch's cache when the context frees them."""
+    import torch
+
+    def alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device, int(stream or 0))
+        except Exception:  # out of memory: the library reports HHT_E_NOMEM
+            return None
+
+    def free(ptr, nbytes, stream, user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    return _Allocator(_ALLOC_FN(alloc), _FREE_FN(free), None)
+
+
 class _Image(ctypes.Structure):
     _fields_ = [("points", ctypes.c_void_p), ("n", ctypes.c_int64), ("W", ctypes.c_int32), ("H", ctypes.c_int32),
                 ("depth", ctypes.c_int32), ("T", ctypes.c_int32)]
@@ -95,6 +122,8 @@ def load(path: Optional[str] = None):
     vp, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
     lib.hht_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, u64]
     lib.hht_create.restype = ctypes.c_int
+    lib.hht_create_with_allocator.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, u64, ctypes.POINTER(_Allocator)]
+    lib.hht_create_with_allocator.restype = ctypes.c_int
     lib.hht_destroy.argtypes = [vp]
     lib.hht_destroy.restype = None
     lib.hht_detect.argtypes = [vp, vp, i64, i32, i32, i32, i32, ctypes.POINTER(_Result)]
@@ -217,7 +246,9 @@ class Context:
     """One library context: device, CUDA stream (the current torch stream at
     creation unless given) and the scratch memory it holds."""
 
-    def __init__(self, device: int = 0, stream=None, mem_budget: int = 0):
+    def __init__(self, device: int = 0, stream=None, mem_budget: int = 0, allocator: Optional[str] = None):
+        """allocator: None (the library's cudaMalloc) or "torch" (PyTorch's
+        caching allocator holds the context's scratch memory)."""
         import torch
         lib = load()
         self.device = int(device)
@@ -226,7 +257,14 @@ class Context:
         self.stream = stream
         handle = ctypes.c_void_p()
         sp = ctypes.c_void_p(int(stream.cuda_stream)) if hasattr(stream, "cuda_stream") else ctypes.c_void_p(stream)
-        rc = lib.hht_create(ctypes.byref(handle), self.device, sp, int(mem_budget))
+        if allocator not in (None, "torch"):
+            raise ValueError('allocator must be None or "torch"')
+        self._allocator = _torch_allocator(self.device) if allocator == "torch" else None
+        if self._allocator is not None:
+            rc = lib.hht_create_with_allocator(ctypes.byref(handle), self.device, sp, int(mem_budget),
+                                               ctypes.byref(self._allocator))
+        else:
+            rc = lib.hht_create(ctypes.byref(handle), self.device, sp, int(mem_budget))
         if rc != HHT_OK:
             raise HhtError(rc, "hht_create")
         self._h = handle

@@ -31,7 +31,7 @@ def test_header_declares_the_api():
                                 "hht_set_tuning", "hht_set_batch_mode", "hht_fetch_all_leaves",
                                 "hht_inject_fault", "hht_set_predicate", "hht_edges", "hht_detect_image",
                                 "hht_lines", "hht_detect_subtrees", "hht_detect_removal",
-                                "hht_detect_removal_batch"}
+                                "hht_detect_removal_batch", "hht_create_with_allocator"}
 
 
 def test_library_exports_every_declared_symbol(lib):
@@ -48,6 +48,9 @@ def test_host_only_calls(lib):
     assert hht.strerror(12345) == "unknown error"
     # argument errors are reported before any device work
     assert lib.hht_create(None, 0, None, 0) == hht.HHT_E_ARG
+    assert lib.hht_create_with_allocator(None, 0, None, 0, None) == hht.HHT_E_ARG
+    h = ctypes.c_void_p()
+    assert lib.hht_create_with_allocator(ctypes.byref(h), 0, None, 0, ctypes.byref(hht._Allocator())) == hht.HHT_E_ARG
     r = hht._Result()
     assert lib.hht_detect(None, None, 0, 8, 8, 3, 1, ctypes.byref(r)) == hht.HHT_E_ARG
     assert lib.hht_detect_batch(None, None, 0, None) == hht.HHT_E_ARG

@@ -463,3 +463,31 @@ def test_subtree_shards_merge_to_the_whole_detection(ctx, split_level, world):
             one = oracle.detect_subtrees(img.points, img.W, img.H, img.depth, img.T, split_level,
                                          shard.plan_subtrees(split_level, world)[0])
             assert np.array_equal(parts[0][0], one.leaves) and np.array_equal(parts[0][1], one.stats)
+
+
+
+# ------------------------------------------------------------------ a caller's allocator
+def test_torch_allocator_holds_the_scratch(hht):
+    import torch
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated(0)
+    c = hht.Context(device=0, allocator="torch")
+    try:
+        for img in (synth.plain_128(index=1), synth.random_small(4321, max_side=300, max_n=2500, max_depth=9,
+                                                                  max_T=10)):
+            _same(c.detect(img.points, img.W, img.H, img.depth, img.T),
+                  oracle.detect(img.points, img.W, img.H, img.depth, img.T))
+        big = synth.plain_1024()
+        got = c.detect(big.points, big.W, big.H, big.depth, big.T)
+        ref = hht.Context(device=0)
+        want = ref.detect(big.points, big.W, big.H, big.depth, big.T)
+        ref.close()
+        assert np.array_equal(got.leaves_numpy(), want.leaves_numpy())
+        assert np.array_equal(got.stats, want.stats)
+        # the context's scratch is torch memory while the context lives
+        assert torch.cuda.memory_allocated(0) - before > (64 << 20)
+    finally:
+        c.close()
+    del got, want
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated(0) - before < (64 << 20)
