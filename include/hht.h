@@ -302,7 +302,11 @@ int hht_set_batch_mode(hht_ctx *ctx, int32_t mode);
  * 2 * n bytes, host or device) receives one flag per point and half
  * (half-major).  The visiting order makes this a sequential walk: each
  * (image, half) is one warp on the GPU; hht_detect_removal_batch runs many
- * images at once (no plotted flags).  Errors: as hht_detect.
+ * images at once (no plotted flags).  Every accepted cell plots at least T
+ * points, so a buffer of 2 * (n / T + 1) leaves always suffices; with a
+ * smaller one the call returns HHT_E_CAPACITY with n_leaves set and copies
+ * nothing (these cells are not kept for hht_fetch_leaves: call again).
+ * Errors: HHT_E_ARG, HHT_E_RANGE, HHT_E_CAPACITY, HHT_E_NOMEM, HHT_E_CUDA.
  */
 int hht_detect_removal(hht_ctx *ctx, const hht_point *points, int64_t n, int32_t W, int32_t H, int32_t depth,
                        int32_t T, hht_result *out, uint8_t *plotted);
