@@ -243,12 +243,35 @@ def test_capacity_two_call_protocol(ctx, hht):
     _same(ctx.detect(img.points, img.W, img.H, img.depth, img.T, leaf_capacity=1), want)
 
 
-def test_deterministic_repeat(ctx):
+def test_deterministic_repeat(ctx, hht):
+    # atomics decide the order of voters inside a segment, never a result:
+    # repeated runs are byte-identical (ten plain runs, batches, the FHT
+    # form, the solution() walk and line extraction)
     img = synth.plain_1024(index=1)
     a = ctx.detect(img.points, img.W, img.H, img.depth, img.T)
-    b = ctx.detect(img.points, img.W, img.H, img.depth, img.T)
-    assert np.array_equal(a.leaves_numpy(), b.leaves_numpy())
-    assert np.array_equal(a.stats, b.stats)
+    la = a.leaves_numpy().copy()
+    lines0 = ctx.lines(0)
+    for _ in range(9):
+        b = ctx.detect(img.points, img.W, img.H, img.depth, img.T)
+        assert np.array_equal(b.leaves_numpy(), la)
+        assert np.array_equal(a.stats, b.stats)
+    assert np.array_equal(ctx.lines(0), lines0)
+    batch = [(im.points, im.W, im.H, im.depth, im.T) for im in synth.batch_256(12)]
+    first = [(r.leaves_numpy().copy(), r.stats) for r in ctx.detect_batch(batch)]
+    for _ in range(2):
+        for (lv, st), r in zip(first, ctx.detect_batch(batch)):
+            assert np.array_equal(r.leaves_numpy(), lv) and np.array_equal(r.stats, st)
+    f = hht.Context(device=0)
+    try:
+        f.set_predicate(hht.PREDICATE_FHT)
+        f1 = f.detect(img.points, img.W, img.H, img.depth, img.T)
+        f2 = f.detect(img.points, img.W, img.H, img.depth, img.T)
+        assert np.array_equal(f1.leaves_numpy(), f2.leaves_numpy()) and np.array_equal(f1.stats, f2.stats)
+    finally:
+        f.close()
+    r1, p1 = ctx.detect_removal(img.points, img.W, img.H, img.depth, img.T)
+    r2, p2 = ctx.detect_removal(img.points, img.W, img.H, img.depth, img.T)
+    assert np.array_equal(r1.leaves_numpy(), r2.leaves_numpy()) and np.array_equal(p1, p2)
 
 
 # ------------------------------------------------------------------ batches
