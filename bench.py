@@ -252,11 +252,12 @@ def run_serving(args, rank):
             if tickets:
                 ctx.progress()
                 now = time.perf_counter() - t0
-                for t, j in list(tickets.items()):
-                    if ctx.poll(t) is not None:
-                        t_done[j] = now
-                        del tickets[t]
-                        done += 1
+                for t in ctx.done_tickets():  # only finished requests are polled
+                    j = tickets.pop(t)
+                    if ctx.poll(t) is None:
+                        raise RuntimeError("a listed ticket was still pending")
+                    t_done[j] = now
+                    done += 1
             elif k < n:
                 time.sleep(max(0.0, min(0.01, arrivals[k] - now)))
         return t_arr, t_done, time.perf_counter() - t0

@@ -201,6 +201,14 @@ int hht_poll(hht_ctx *ctx, uint64_t ticket, hht_result *out);
 int hht_progress(hht_ctx *ctx);
 
 /*
+ * Completion list of the serving interface: writes up to `capacity` tickets
+ * of requests that have finished (successfully or not) and have not been
+ * polled or listed before, oldest completion first, and their number into
+ * *count, so that a client polls only finished requests.  Errors: HHT_E_ARG.
+ */
+int hht_done_tickets(hht_ctx *ctx, uint64_t *tickets, uint64_t capacity, uint64_t *count);
+
+/*
  * Kernel timing.  hht_profile_enable(ctx, 1) resets the counters and makes the
  * context record CUDA events on its stream around every kernel it launches
  * (0 stops recording).  hht_profile_read() copies the accumulated counters.

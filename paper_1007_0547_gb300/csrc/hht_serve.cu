@@ -54,6 +54,7 @@ struct ServeState {
     uint64_t next_ticket = 1;
     std::map<uint64_t, Request> reqs;
     std::deque<uint64_t> waiting;
+    std::deque<uint64_t> finished;  // tickets done and not yet listed by hht_done_tickets
 
     // engine
     bool init = false;
@@ -264,6 +265,7 @@ int engine_complete(hht_ctx* c, ServeState* S, uint64_t step_leaves) {
         off += nl;
         r.status = r.range_error ? HHT_E_RANGE : HHT_OK;
         r.done = true;
+        S->finished.push_back(fin[k]);
         r.pts.clear();
         r.pts.shrink_to_fit();
         S->free_slots.push_back(r.slot);
@@ -395,6 +397,7 @@ int hht_progress(hht_ctx* c) {
             r.done = true;
             r.status = rc;
             s->free_slots.push_back(r.slot);
+            s->finished.push_back(t);
         }
         s->order.clear();
         s->in_flight_bytes = 0;
@@ -405,6 +408,21 @@ int hht_progress(hht_ctx* c) {
     }
     std::lock_guard<std::mutex> lk2(s->mu);
     return (int)(s->order.size() + s->waiting.size());
+}
+
+int hht_done_tickets(hht_ctx* c, uint64_t* tickets, uint64_t capacity, uint64_t* count) {
+    if (!c || !count || (capacity > 0 && !tickets)) return HHT_E_ARG;
+    ServeState* s = serve_of(c);
+    std::lock_guard<std::mutex> lk(s->mu);
+    uint64_t n = 0;
+    while (n < capacity && !s->finished.empty()) {
+        const uint64_t t = s->finished.front();
+        s->finished.pop_front();
+        if (s->reqs.find(t) == s->reqs.end()) continue;  // already polled
+        tickets[n++] = t;
+    }
+    *count = n;
+    return HHT_OK;
 }
 
 int hht_poll(hht_ctx* c, uint64_t ticket, hht_result* out) {

@@ -34,7 +34,7 @@ EXPORTS = ("hht_create", "hht_destroy", "hht_detect", "hht_detect_batch", "hht_f
            "hht_detect_noalloc", "hht_autotune", "hht_set_tuning", "hht_set_batch_mode", "hht_fetch_all_leaves",
            "hht_inject_fault", "hht_set_predicate", "hht_edges", "hht_detect_image", "hht_lines",
            "hht_detect_subtrees", "hht_detect_removal", "hht_detect_removal_batch",
-           "hht_create_with_allocator")
+           "hht_create_with_allocator", "hht_done_tickets")
 BATCH_LEVELS, BATCH_PERSISTENT = 0, 1
 FAULT_NONE, FAULT_WITHHOLD_SCAN_TILE = 0, 1
 PREDICATE_EXACT, PREDICATE_FHT = 0, 1
@@ -140,6 +140,8 @@ def load(path: Optional[str] = None):
     lib.hht_poll.restype = ctypes.c_int
     lib.hht_progress.argtypes = [vp]
     lib.hht_progress.restype = ctypes.c_int
+    lib.hht_done_tickets.argtypes = [vp, ctypes.POINTER(u64), u64, ctypes.POINTER(u64)]
+    lib.hht_done_tickets.restype = ctypes.c_int
     lib.hht_profile_enable.argtypes = [vp, ctypes.c_int]
     lib.hht_profile_enable.restype = ctypes.c_int
     lib.hht_profile_read.argtypes = [vp, ctypes.POINTER(_Profile)]
@@ -642,21 +644,35 @@ class Context:
             raise HhtError(rc, "hht_progress")
         return rc
 
+    def done_tickets(self, max_count: int = 4096) -> List[int]:
+        """Tickets of finished requests not polled or listed before
+        (hht_done_tickets), oldest completion first."""
+        buf = (ctypes.c_uint64 * max_count)()
+        n = ctypes.c_uint64()
+        rc = load().hht_done_tickets(self._h, buf, max_count, ctypes.byref(n))
+        if rc != HHT_OK:
+            raise HhtError(rc, "hht_done_tickets")
+        return list(buf[: int(n.value)])
+
     def poll(self, ticket: int, leaves_on_device: bool = False) -> Optional[Result]:
+        """None while the request is pending; else its Result (the ticket is
+        then released).  A pending poll allocates nothing: the first call asks
+        with an empty buffer, and only a finished request gets one of its size."""
         lib = load()
-        cap = self._cap_hint
-        while True:
+        r = _Result()
+        r.leaves = None
+        r.leaf_capacity = 0
+        rc = lib.hht_poll(self._h, int(ticket), ctypes.byref(r))
+        if rc == HHT_E_PENDING:
+            return None
+        buf, ptr = self._alloc_leaves(0, leaves_on_device)
+        while rc == HHT_E_CAPACITY:
+            cap = int(r.n_leaves)
             buf, ptr = self._alloc_leaves(cap, leaves_on_device)
             r = _Result()
             r.leaves = ptr
             r.leaf_capacity = cap
             rc = lib.hht_poll(self._h, int(ticket), ctypes.byref(r))
-            if rc == HHT_E_PENDING:
-                return None
-            if rc == HHT_E_CAPACITY:
-                cap = int(r.n_leaves)
-                continue
-            break
         if rc != HHT_OK:
             raise HhtError(rc, "hht_poll")
         return Result(buf[: int(r.n_leaves)], _stats_of(r), int(r.depth), int(r.L), rc)

@@ -31,7 +31,8 @@ def test_header_declares_the_api():
                                 "hht_set_tuning", "hht_set_batch_mode", "hht_fetch_all_leaves",
                                 "hht_inject_fault", "hht_set_predicate", "hht_edges", "hht_detect_image",
                                 "hht_lines", "hht_detect_subtrees", "hht_detect_removal",
-                                "hht_detect_removal_batch", "hht_create_with_allocator"}
+                                "hht_detect_removal_batch", "hht_create_with_allocator",
+                                "hht_done_tickets"}
 
 
 def test_library_exports_every_declared_symbol(lib):
@@ -72,6 +73,7 @@ def test_host_only_calls(lib):
     assert lib.hht_detect_subtrees(None, None, 0, 8, 8, 3, 1, 1, None, ctypes.byref(r)) == hht.HHT_E_ARG
     assert lib.hht_detect_removal(None, None, 0, 8, 8, 3, 1, ctypes.byref(r), None) == hht.HHT_E_ARG
     assert lib.hht_detect_removal_batch(None, None, 0, None) == hht.HHT_E_ARG
+    assert lib.hht_done_tickets(None, None, 0, ctypes.byref(na)) == hht.HHT_E_ARG
 
 
 def test_result_struct_layout_matches_header(lib):

@@ -110,3 +110,28 @@ def test_bad_request_fails_alone(hht):
     with pytest.raises(hht.HhtError):
         ctx.poll(tb)  # the ticket was released
     ctx.close()
+
+
+def test_completion_list_names_each_finished_request_once(hht):
+    imgs = _mixed_requests()
+    want = _alone(hht, imgs)
+    ctx = hht.Context(device=0)
+    try:
+        tickets = {ctx.submit(im.points, im.W, im.H, im.depth, im.T): k for k, im in enumerate(imgs)}
+        seen, got = set(), {}
+        for _ in range(100000):
+            if len(got) == len(imgs):
+                break
+            ctx.progress()
+            for t in ctx.done_tickets():
+                assert t in tickets and t not in seen
+                seen.add(t)
+                r = ctx.poll(t)
+                assert r is not None
+                got[tickets[t]] = r
+        assert len(got) == len(imgs)
+        for k, r in got.items():
+            _same(r, want[k])
+        assert ctx.done_tickets() == []
+    finally:
+        ctx.close()
