@@ -455,6 +455,16 @@ int hht_poll(hht_ctx* c, uint64_t ticket, hht_result* out) {
     *out = res;
     out->status = rc;
     s->reqs.erase(it);
+    // A client that polls without draining hht_done_tickets leaves polled
+    // tickets on the completion list: drop them once they outnumber the live
+    // requests two to one, so the list stays bounded (amortised O(log n) per
+    // request, since after a pass it holds live tickets only).
+    if (s->finished.size() > 2 * s->reqs.size() + 64) {
+        std::deque<uint64_t> live;
+        for (uint64_t t : s->finished)
+            if (s->reqs.count(t)) live.push_back(t);
+        s->finished.swap(live);
+    }
     return rc;
 }
 

@@ -135,3 +135,25 @@ def test_completion_list_names_each_finished_request_once(hht):
         assert ctx.done_tickets() == []
     finally:
         ctx.close()
+
+
+def test_completion_list_stays_bounded_when_only_polled(hht):
+    """A client that polls tickets without draining the completion list: the
+    list is compacted once polled tickets outnumber the live ones, and a later
+    drain names exactly the finished tickets not yet polled, in completion
+    order."""
+    imgs = [synth.random_small(1700 + s, max_side=64, max_n=60, max_depth=6, max_T=6) for s in range(150)]
+    ctx = hht.Context(device=0)
+    try:
+        tickets = [ctx.submit(im.points, im.W, im.H, im.depth, im.T) for im in imgs]
+        for _ in range(100000):
+            if ctx.progress() == 0:
+                break
+        for t in tickets[:-5]:
+            assert ctx.poll(t) is not None
+        assert sorted(ctx.done_tickets()) == sorted(tickets[-5:])
+        assert ctx.done_tickets() == []
+        for t in tickets[-5:]:
+            assert ctx.poll(t) is not None
+    finally:
+        ctx.close()
