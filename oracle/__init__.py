@@ -6,6 +6,7 @@ use) through ctypes and shares no code with the CUDA library.
 """
 from .oracle import (  # noqa: F401
     build,
+    loaded_path,
     detect,
     count_region,
     getcode,

@@ -37,16 +37,34 @@ class _Region(ctypes.Structure):
                 ("j0", ctypes.c_uint32), ("size", ctypes.c_uint32), ("votes", ctypes.c_uint32)]
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain C11, -O2) into oracle/_build/."""
+# Flags of the "sanitized" variant: AddressSanitizer and UBSan, stopping at the
+# first undefined behaviour.  A process that loads it must preload libasan.
+_SANITIZED_FLAGS = ["-O1", "-g", "-fsanitize=address,undefined", "-fno-sanitize-recover=undefined",
+                    "-fno-omit-frame-pointer"]
+
+
+def build(force: bool = False, variant: Optional[str] = None) -> str:
+    """Compile the oracle with gcc (plain C11) into oracle/_build/: -O2 by
+    default; variant "sanitized" (or $HHT_ORACLE_VARIANT=sanitized) builds it
+    with AddressSanitizer and UBSan instead."""
+    variant = variant if variant is not None else os.environ.get("HHT_ORACLE_VARIANT", "")
+    if variant not in ("", "sanitized"):
+        raise ValueError(f"unknown oracle variant {variant!r}")
+    path = _LIB_PATH if not variant else os.path.join(_OUT_DIR, f"liboracle_{variant}.so")
+    flags = ["-O2"] if not variant else _SANITIZED_FLAGS
     os.makedirs(_OUT_DIR, exist_ok=True)
-    stale = (not os.path.exists(_LIB_PATH)) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC)
+    stale = (not os.path.exists(path)) or os.path.getmtime(path) < os.path.getmtime(_SRC)
     if force or stale:
-        tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-Wall", "-Wextra",
+        tmp = path + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", *flags, "-std=gnu11", "-fPIC", "-shared", "-Wall", "-Wextra",
                                "-o", tmp, _SRC])
-        os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+        os.replace(tmp, path)
+    return path
+
+
+def loaded_path() -> str:
+    """Path of the oracle library this process loaded."""
+    return _load()._name
 
 
 def _load():
