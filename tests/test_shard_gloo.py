@@ -1,12 +1,16 @@
-"""Multi-rank sharding on CPU with the gloo backend (world size 2).
+"""Multi-rank sharding on CPU with the gloo backend (world sizes 2 and 3).
 
 Across images: each rank detects its share of the images (the CPU oracle
 stands in for the GPU here) and rank 0 gathers the results; the merged list
 must equal the unsharded run image by image.  Within one image: each rank
 runs its level-k subtrees (the oracle's subtree mode), rank 0 merges, and the
-merged leaves and statistics must equal the unsharded detection."""
+merged leaves and statistics must equal the unsharded detection.  The
+benchmark's reference arm under torchrun prints one line, from rank 0."""
+import json
 import os
 import socket
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -135,3 +139,56 @@ def test_two_gloo_ranks_split_one_image_by_subtrees(tmp_path, split_level):
     want = oracle.detect(*image)
     assert np.array_equal(lv, want.leaves)
     assert np.array_equal(st, want.stats)
+
+
+def test_three_gloo_ranks_with_an_empty_share(tmp_path):
+    """More ranks than images: one rank's share is empty, it still takes part
+    in the gather, and the merged list is the unsharded one."""
+    import pickle
+
+    import torch.multiprocessing as mp
+    imgs = [synth.random_small(90 + s, max_side=120, max_n=400, max_depth=6, max_T=5) for s in range(2)]
+    batch = [(im.points, im.W, im.H, im.depth, im.T) for im in imgs]
+    from paper_1007_0547_gb300 import shard
+    assert sum(1 for s in shard.plan_shards(batch, 3) if not s) == 1
+    out = str(tmp_path / "merged.pkl")
+    mp.start_processes(_worker, args=(3, _free_port(), batch, out), nprocs=3, join=True, start_method="spawn")
+    with open(out, "rb") as f:
+        merged = pickle.load(f)
+    want = _oracle_batch(batch)
+    assert len(merged) == len(want)
+    for (lv, st), w in zip(merged, want):
+        assert np.array_equal(lv, w.leaves)
+        assert np.array_equal(st, w.stats)
+
+
+def test_three_gloo_ranks_split_one_image_by_subtrees(tmp_path):
+    import pickle
+
+    import oracle
+    import torch.multiprocessing as mp
+    img = synth.plain_128(index=1)
+    image = (img.points, img.W, img.H, img.depth, img.T)
+    out = str(tmp_path / "merged.pkl")
+    mp.start_processes(_subtree_worker, args=(3, _free_port(), image, 2, out), nprocs=3, join=True,
+                       start_method="spawn")
+    with open(out, "rb") as f:
+        lv, st = pickle.load(f)
+    want = oracle.detect(*image)
+    assert np.array_equal(lv, want.leaves)
+    assert np.array_equal(st, want.stats)
+
+
+def test_bench_reference_arm_under_torchrun_prints_one_line_from_rank_0():
+    repo = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), "bench.py", "--impl", "reference",
+           "--gpus", "2", "--steps", "1", "--warmup", "0"]
+    run = subprocess.run(cmd, cwd=repo, capture_output=True, text=True, timeout=600)
+    assert run.returncode == 0, run.stderr[-3000:]
+    lines = [ln for ln in run.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, run.stdout
+    rec = json.loads(lines[0])
+    assert rec["impl"] == "reference" and rec["n_gpus"] == 2 and rec["steps"] == 1
+    assert rec["value"] > 0 and rec["e2e"]["value"] == rec["value"]
+    assert rec["cpu_baseline"]["kind"] == "oracle" and rec["cpu_baseline"]["cores"] >= 1
