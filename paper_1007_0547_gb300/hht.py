@@ -214,6 +214,11 @@ _RESULT_DTYPE = np.dtype({
     "itemsize": ctypes.sizeof(_Result)})
 
 
+# A status the library never writes: marks the results of images that a batch
+# call returned without reaching.
+_NOT_REACHED = 1
+
+
 def _stats_of(r: _Result) -> np.ndarray:
     st = np.frombuffer(r.stats, dtype=np.uint64).reshape(2, MAX_DEPTH + 1, 4)
     return st[:, : r.depth + 1].copy()
@@ -353,23 +358,36 @@ class Context:
         buffer, e.g. pinned host memory reused across calls); each result's
         leaves are a view of that buffer."""
         lib = load()
+        nimg = len(images)
+        if nimg == 0:
+            return []
         pts = [_Points(im[0]) for im in images]
-        arr = (_Image * len(images))()
+        arr = (_Image * nimg)()
         for k, (im, p) in enumerate(zip(images, pts)):
             arr[k].points = p.ptr
             arr[k].n = p.n
             arr[k].W, arr[k].H, arr[k].depth, arr[k].T = (int(v) for v in im[1:5])
         # no leaves are copied by the batch call itself: all leaves of the job
         # are fetched afterwards with one copy, and each image gets a view
-        outs = (_Result * len(images))()
-        rc = lib.hht_detect_batch(self._h, arr, len(images), outs)
-        for k in range(len(images)):
+        outs = (_Result * nimg)()
+        np.frombuffer(outs, dtype=_RESULT_DTYPE)["status"] = _NOT_REACHED
+        rc = lib.hht_detect_batch(self._h, arr, nimg, outs)
+        if (np.frombuffer(outs, dtype=_RESULT_DTYPE)["status"] == _NOT_REACHED).any():
+            # the call returned before reporting every image (an argument error,
+            # or a wave that failed as a whole): the context holds no complete
+            # job of these images, so nothing is fetched
+            code = rc if rc != HHT_OK else HHT_E_CUDA
+            if raise_on_error:
+                raise HhtError(code, "hht_detect_batch")
+            empty = self._alloc_leaves(0, leaves_on_device)[0][:0]
+            return [Result(empty, np.zeros((2, int(im[3]) + 1, 4), np.uint64), int(im[3]), 0, code)
+                    for im in images]
+        for k in range(nimg):
             if outs[k].status == HHT_E_CAPACITY:
                 outs[k].status = HHT_OK
         if rc == HHT_E_CAPACITY:
             rc = HHT_OK
         total = ctypes.c_uint64()
-        nimg = len(images)
         offs = (ctypes.c_uint64 * nimg)()
         cnts = (ctypes.c_uint64 * nimg)()
         lib.hht_fetch_all_leaves(self._h, None, 0, offs, cnts, ctypes.byref(total))

@@ -514,3 +514,22 @@ def test_torch_allocator_holds_the_scratch(hht):
     del got, want
     torch.cuda.synchronize()
     assert torch.cuda.memory_allocated(0) - before < (64 << 20)
+
+
+def test_batch_calls_that_run_nothing_fetch_nothing(ctx, hht):
+    """After a batch of three images, an empty batch returns [] and a batch
+    rejected by its argument checks raises HHT_E_ARG (or, without raising,
+    reports its image failed with no leaves): neither touches the earlier
+    job's leaves or offsets, and the next batch is exact."""
+    imgs = [synth.plain_128(index=k) for k in range(3)]
+    batch = [(im.points, 128, 128, 7, 20) for im in imgs]
+    ctx.detect_batch(batch)
+    assert ctx.detect_batch([]) == []
+    bad = [(imgs[0].points, 128, 128, 0, 20)]  # depth 0
+    with pytest.raises(hht.HhtError) as e:
+        ctx.detect_batch(bad)
+    assert e.value.code == hht.HHT_E_ARG
+    res = ctx.detect_batch(bad, raise_on_error=False)
+    assert len(res) == 1 and res[0].status == hht.HHT_E_ARG and res[0].n_leaves == 0
+    for r, im in zip(ctx.detect_batch(batch), imgs):
+        _same(r, oracle.detect(im.points, 128, 128, 7, 20))
