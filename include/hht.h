@@ -179,8 +179,11 @@ int hht_fetch_leaves(hht_ctx *ctx, int32_t index, hht_leaf *leaves, uint64_t cap
  * with one copy: `leaves` receives *total entries (host or device memory,
  * `capacity` entries), and image k's leaves are leaves[offsets[k] ..
  * offsets[k] + counts[k]) (offsets and counts: one entry per image of the
- * job, may be NULL).  Images that failed have count 0.  With capacity < total
- * nothing is copied and HHT_E_CAPACITY is returned with *total set.
+ * job, may be NULL).  The job is the last hht_detect_batch call that passed
+ * its argument checks: a call that returned HHT_E_ARG (or had count 0) did not
+ * replace it, so size offsets and counts by that call's count.  Images that
+ * failed have count 0.  With capacity < total nothing is copied (and offsets
+ * and counts are not written) and HHT_E_CAPACITY is returned with *total set.
  * Errors: HHT_E_ARG, HHT_E_CAPACITY, HHT_E_CUDA.
  */
 int hht_fetch_all_leaves(hht_ctx *ctx, hht_leaf *leaves, uint64_t capacity, uint64_t *offsets, uint64_t *counts,
