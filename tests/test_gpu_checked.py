@@ -1,9 +1,8 @@
 """The bounds-checked build (-DHHT_CHECKED): every index that the level kernel
 takes from its data (parent and child record indices, cursors) is checked
 against the current sizes, and a bad one sets an error status instead of
-being used.  compute-sanitizer is closed on this machine, so this build, run on
-the parity cases, is the out-of-bounds check: it must report no error and
-give the oracle's results.  It runs in a child process because a process
+being used.  Run on the parity cases, this build is the out-of-bounds check
+of the level kernel: it must report no error and give the oracle's results.  It runs in a child process because a process
 loads one build of the library."""
 import os
 import subprocess
