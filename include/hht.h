@@ -15,13 +15,13 @@
  *     quadrants NE, NW, SW, SE (Section 3).
  *   - A line's 4-bit code for a region has one bit per corner in the order NE,
  *     NW, SW, SE; a bit is 1 when that corner lies strictly below the line
- *     (Section 2: F = y0 - m*x0 - b < 0; a corner on the line is "above").
+ *     (Section 2: F = y0 - m*x0 - b < 0; a corner on the line counts as above).
  *     The line votes for the region when the code is neither 0000 nor 1111
- *     (Section 3, steps 5 and 12).
+ *     (Section 3).
  *   - A region whose votes reach T (votes >= T) is split again; the level-0
  *     region is always split.  At level `depth` the regions are cells of a
  *     K x K grid, K = 2^depth, and each cell that reaches T is reported as a
- *     leaf (Section 3, step 13; the paper's solution() output step, without
+ *     leaf (Section 3: the paper's solution() output, without
  *     the removal of plotted voters).
  *
  * Leaf cell (i, j) of half h spans m in [-1 + 2i/K, -1 + 2(i+1)/K] and

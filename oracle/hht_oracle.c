@@ -21,28 +21,29 @@
  *     below the line, i.e. F = y0 - m*x0 - b < 0 for the corner (x0, y0) and
  *     the line's slope m and intercept b (Section 2, getcode() in Section 3).
  *   - A line votes for a region when its code is neither 0000 nor 1111
- *     (Section 3, steps 5 and 12.v).
+ *     (Section 3).
  *   - A region whose votes reach the threshold T is split further, down to
- *     level `depth`, where it is reported as a peak cell (Section 3, step 13).
+ *     level `depth`, where it is reported as a peak cell (Section 3).
  *
  * Readings where the paper is silent or ambiguous:
  *   - The grid is dyadic: at depth D there are K = 2^D cells per side, with
  *     m_i = -1 + 2i/K and b_j = -2L + 4Lj/K.  All arithmetic is done on
  *     K * F, which is an exact integer (int64 here; int128 for the squared
  *     circle test).
- *   - Threshold: a region passes when votes >= T (the pseudocode's
- *     "vote > THRESHOLD" is the same rule with T = THRESHOLD + 1).
- *   - The level-0 region is always split (step 6 of the pseudocode has no
- *     threshold test).
+ *   - Threshold: a region passes when votes >= T (the paper's algorithm
+ *     compares the votes strictly with its threshold, which is the same rule
+ *     with T one larger).
+ *   - The level-0 region is always split (the paper's algorithm subdivides it
+ *     without a threshold test).
  *   - The solution() removal of plotted voters is not applied, so the result
  *     is independent of traversal order.
- *   - The parent-code child-exclusion shortcut (step 12.i) is not applied:
- *     every child code is computed, which cannot change any result.
+ *   - The shortcut that skips children from the parent's code is not
+ *     applied: every child code is computed, which cannot change any result.
  *
- * The traversal follows the pseudocode's depth-first order (NE, NW, SW, SE)
- * with one voter list per level instead of one code array per level: a point
- * is only tested for a child when it voted for the parent, which is what the
- * code test "(level-1).linecode != 0000 and != 1111" of step 12.b decides.
+ * The traversal visits regions in the paper's depth-first order (NE, NW, SW,
+ * SE) with one voter list per level instead of one code array per level: a
+ * point is tested for a child only when it voted for the parent, the same
+ * condition under which the paper's algorithm computes a child's code.
  * Leaves are reported in the order this traversal reaches them (half 0
  * first), which is the order in which solution() would be called.
  *

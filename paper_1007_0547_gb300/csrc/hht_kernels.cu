@@ -3,7 +3,7 @@
 //   stage   level 0: range-check the points, write the level-0 voter streams of
 //           both halves and count the votes of the four level-1 quadrants.
 //   select  level s: a level-(s-1) region's child passes when its votes >= T
-//           (Section 3, step 13).  Passed children become the level-s region
+//           (Section 3).  Passed children become the level-s region
 //           records (or leaves at the unit's depth); a look-back scan gives
 //           every child its record index.  Also writes the level statistics.
 //   pass    level s: one read of the level-(s-1) voter stream.  Per voter the

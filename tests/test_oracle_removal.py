@@ -1,10 +1,11 @@
 """Pins of the oracle's solution() mode (Section 3: voters of an accepted leaf
 are plotted and removed from every region reached later).
 
-- the paper's pseudocode written out literally on tiny inputs: per-level
-  linecode arrays over all edge points, level.quad / level.vote, and
-  solution() zeroing a plotted point's codes at every level; its accepted
-  cells, statistics and plotted points must equal the oracle's;
+- a restatement from the definition on tiny inputs: regions visited depth
+  first (NE, NW, SW, SE) by recursion, a set of points not yet plotted, and
+  crossing decided on exact rational corners (the pins' Fraction vertex
+  table, not the oracle's arithmetic); its accepted cells, statistics and
+  plotted points must equal the oracle's;
 - a hand-worked case: eight collinear points whose lines meet at a grid
   vertex fill two cells with 8 votes each; the first in depth-first order
   (NE before NW) takes all eight points and the second is left with none;
@@ -20,65 +21,62 @@ import synth
 from tests import pins
 
 
-def _pseudocode(points, W, H, D, T):
-    """Section 3's algorithm as printed, one half after the other."""
-    L = oracle.frame_side(W, H)
+def _crosses(below, i0, j0, S):
+    """The line of a point crosses the region with corners (i0, j0) and
+    (i0 + S, j0 + S): its corner code is neither 0000 nor 1111."""
+    code = ((below[i0 + S][j0 + S] << 3) | (below[i0][j0 + S] << 2) | (below[i0][j0] << 1)
+            | below[i0 + S][j0])
+    return code not in (0, 15)
+
+
+def _removal_by_definition(points, W, H, D, T):
+    """solution() from its description: a plotted point takes no part in any
+    region reached after its leaf.  Crossing is monotone (a line that crosses
+    a region crosses every region containing it), so when a child is reached
+    the points tested for it are the unplotted points that cross its parent,
+    and its votes are those among them that cross the child.  A leaf that
+    reaches T plots its voters at once.  Returns (leaves in visiting order,
+    stats [2, D + 1, 4], plotted [2, n])."""
+    L = pins.frame_side(W, H)
     K = 1 << D
-    leaves, plotted = [], np.zeros((2, len(points)), np.uint8)
+    n = len(points)
+    leaves = []
+    plotted = np.zeros((2, n), np.uint8)
     stats = np.zeros((2, D + 1, 4), np.uint64)
     for half in (0, 1):
         pts = pins.half_points(points, half)
-        E = len(pts)
-        code = np.zeros((D + 1, E), np.int64)
-        for e in range(E):
-            code[0, e] = oracle.getcode(int(pts[e, 0]), int(pts[e, 1]), 0, 0, K, L, D)
-        stats[half, 0] = (1, 1, sum(1 for e in range(E) if code[0, e] not in (0, 15)), E)
-        region = {0: (0, 0, K)}
-        quad = {1: 0}
-        level = 1
-        while level > 0:
-            quad[level] += 1
-            if quad[level] <= 4:
-                i0, j0, S = region[level - 1]
-                h = S // 2
-                q = quad[level] - 1  # quad1..quad4 = NE, NW, SW, SE
-                ci = i0 + (h if q in (0, 3) else 0)
-                cj = j0 + (h if q in (0, 1) else 0)
-                vote = 0
-                evaluated = 0
-                for e in range(E):
-                    if code[level - 1, e] not in (0, 15):
-                        evaluated += 1
-                        c = oracle.getcode(int(pts[e, 0]), int(pts[e, 1]), ci, cj, h, L, D)
-                        code[level, e] = c
-                        if c not in (0, 15):
-                            vote += 1
-                    else:
-                        code[level, e] = 0
-                stats[half, level, 0] += 1
-                stats[half, level, 2] += vote
-                stats[half, level, 3] += evaluated
-                if vote >= T:
-                    stats[half, level, 1] += 1
-                    if level == D:
-                        leaves.append((half, ci, cj, vote))
-                        for e in range(E):  # solution(): plot and zero the codes at every level
-                            if code[D, e] not in (0, 15):
-                                plotted[half, e] = 1
-                                code[:, e] = 0
-                    else:
-                        region[level] = (ci, cj, h)
-                        level += 1
-                        quad[level] = 0
-            else:
-                level -= 1
+        below = [pins._vertex_below_table(int(x), int(y), L, K) for x, y in pts]
+        live = np.ones(n, bool)
+        root_votes = sum(1 for e in range(n) if _crosses(below[e], 0, 0, K))
+        stats[half, 0] = (1, 1, root_votes, n)
+
+        def visit(level, i0, j0, S):
+            h = S // 2
+            for ci, cj in ((i0 + h, j0 + h), (i0, j0 + h), (i0, j0), (i0 + h, j0)):
+                tested = [e for e in range(n) if live[e] and _crosses(below[e], i0, j0, S)]
+                voters = [e for e in tested if _crosses(below[e], ci, cj, h)]
+                row = stats[half, level + 1]
+                row[0] += 1
+                row[2] += len(voters)
+                row[3] += len(tested)
+                if len(voters) < T:
+                    continue
+                row[1] += 1
+                if level + 1 == D:
+                    leaves.append((half, ci, cj, len(voters)))
+                    live[voters] = False
+                    plotted[half, voters] = 1
+                else:
+                    visit(level + 1, ci, cj, h)
+
+        visit(0, 0, 0, K)
     return np.array(leaves, dtype=np.uint32).reshape(-1, 4), stats, plotted
 
 
 @pytest.mark.parametrize("seed", range(40))
-def test_against_the_pseudocode_written_out(seed):
+def test_against_the_definition_restated(seed):
     img = synth.random_small(81000 + seed, max_side=16, max_n=40, max_depth=4, max_T=4)
-    want_leaves, want_stats, want_plotted = _pseudocode(img.points, img.W, img.H, img.depth, img.T)
+    want_leaves, want_stats, want_plotted = _removal_by_definition(img.points, img.W, img.H, img.depth, img.T)
     got, plotted = oracle.detect_removal(img.points, img.W, img.H, img.depth, img.T)
     assert np.array_equal(got.leaves, want_leaves), seed
     assert np.array_equal(got.stats, want_stats), seed
