@@ -168,7 +168,14 @@ def detect(points: np.ndarray, W: int, H: int, depth: int, T: int, mode: str = "
     nl = ctypes.c_int64(0)
     nr = ctypes.c_int64(0)
     regions = (_Region * region_cap)() if dump_regions else None
+    # Start from an upper bound of the leaf count, so that the detection runs
+    # once: a line's slope is below 1/2 in cell units, so it crosses at most 3
+    # cells of each of the K columns, and every leaf holds at least T votes;
+    # capped at 2^22 leaves (64 MB), beyond which a second run sizes the buffer.
     cap = 1 << 16
+    if 1 <= depth <= 24 and T >= 1:
+        K = 1 << depth
+        cap = max(cap, min(2 * K * K, 2 * (3 * K * n // T + 1), 1 << 22))
     while True:
         leaves = (_Leaf * cap)()
         rc = lib.oracle_detect(pts.ctypes.data_as(ctypes.POINTER(ctypes.c_int16)), n, W, H, depth, T, m,
