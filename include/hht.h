@@ -54,7 +54,8 @@ enum {
                                 depth outside [1, 24], T < 1, bad image count */
     HHT_E_RANGE = -2,        /* a point lies outside [0, W) x [0, H); result invalid */
     HHT_E_CAPACITY = -3,     /* leaf buffer too small; n_leaves holds the needed count */
-    HHT_E_NOMEM = -4,        /* device memory (or the context's budget) exhausted */
+    HHT_E_NOMEM = -4,        /* device memory (or the context's budget) exhausted, or one level of a job
+                                could hold more than 2^32 - 2 regions (4 children per parent) */
     HHT_E_TIMEOUT = -5,      /* a bounded device-side wait expired; result invalid */
     HHT_E_CUDA = -6,         /* a CUDA runtime call failed */
     HHT_E_PENDING = -7,      /* hht_poll: the request has not finished yet */

@@ -470,6 +470,7 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
         const int pi = (s - 1) & 1, ci = s & 1;
         const uint64_t P = c->h_infos[s - 1].n_regions;
         if (P == 0) break;
+        if (4 * P > kMaxLevelRecords) return HHT_E_NOMEM;
         RK(ensure(c, c->preg[pi], P * sizeof(PassRegion)));
         RK(ensure(c, c->rec[ci], 4 * P * sizeof(Region)));
         RK(ensure(c, c->cnt[ci], 4 * P * 4 * sizeof(uint32_t)));

@@ -24,6 +24,12 @@ namespace hht {
 
 constexpr int kMaxDepth = 24;
 
+// The region records of one level are addressed by 32-bit indices (a voter
+// record's parent word; 0xffffffff marks no region), so a level holds at most
+// this many.  The host refuses a level whose parents could give more children
+// (4 per parent) with HHT_E_NOMEM, which splits a batch into smaller waves.
+constexpr uint64_t kMaxLevelRecords = 0xfffffffeull;
+
 // Quadrant order of the paper's quad1..quad4.
 enum Quad : int { NE = 0, NW = 1, SW = 2, SE = 3 };
 

@@ -294,6 +294,7 @@ int engine_step(hht_ctx* c, ServeState* S) {
     SV_CK(cudaMemsetAsync(&d_infos[np], 0, sizeof(LevelInfo), st));
     SV_CK(cudaMemsetAsync(S->leaf_total.p, 0, sizeof(uint64_t), st));
     LevelInfo h_next{};
+    if (4 * P > kMaxLevelRecords) return HHT_E_NOMEM;
     if (P > 0) {
         const uint64_t sel_tiles = (P + 1023) / 1024;
         SV_RK(ensure(c, S->preg[cp], P * sizeof(PassRegion)));
