@@ -10,6 +10,7 @@ from __future__ import annotations
 import ctypes
 import dataclasses
 import os
+import sys
 from typing import List, Optional, Sequence, Tuple
 
 import numpy as np
@@ -283,6 +284,11 @@ class Context:
             self._h = None
 
     def __del__(self):  # pragma: no cover
+        # At interpreter exit PyTorch may already be torn down: a context whose
+        # memory comes from torch's allocator is then left to the process exit
+        # instead of calling back into torch.
+        if sys.is_finalizing() and getattr(self, "_allocator", None) is not None:
+            return
         try:
             self.close()
         except Exception:
