@@ -11,6 +11,7 @@
 """
 import json
 import os
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -72,6 +73,31 @@ def test_concurrency_vertex(case):
     assert all(int(v) == n for h, i, j, v in r_eq.leaves)
     r_gt = oracle.detect(pts, c["W"], c["H"], c["depth"], n + 1)
     assert len(r_gt.leaves) == 0
+
+
+def test_concurrency_vertex_at_the_largest_frame():
+    """The concurrency pin at the largest frame and depth (L = 2^15, K = 2^24),
+    where the exact corner values reach 2^41.  Points with even x on the image
+    line y = x/2 + 100 give parameter-space lines that all pass through
+    (m, b) = (1/2, 100), which is the grid vertex (i, j) = (3 * 2^22,
+    65636 * 128) at depth 24.  Around it the cells whose NE and NW corners are
+    the vertex get every line, the one whose SE corner it is gets the lines
+    with x > 0, and the one whose SW corner it is gets none."""
+    W = H = 32767
+    D, K, L = 24, 1 << 24, 1 << 15
+    xs = [0, 2, 4, 6, 8, 10, 12, 14, 16, 18, 20, 22, 30000, 32766]
+    pts = np.array([[x, x // 2 + 100] for x in xs], np.int16)
+    n, pos = len(xs), sum(1 for x in xs if x > 0)
+    i, j = 3 << 22, 65636 * 128
+    assert Fraction(-1) + Fraction(2 * i, K) == Fraction(1, 2)
+    assert Fraction(-2 * L) + Fraction(4 * L * j, K) == 100
+    r = oracle.detect(pts, W, H, D, pos)
+    got = {(int(a), int(b)): int(v) for h, a, b, v in r.leaves if h == 0}
+    assert got.get((i - 1, j - 1)) == n      # NE corner at the vertex
+    assert got.get((i, j - 1)) == n          # NW corner
+    assert got.get((i - 1, j)) == pos        # SE corner: the lines with x > 0
+    assert (i, j) not in got                 # SW corner: no line
+    assert len(oracle.detect(pts, W, H, D, n + 1).leaves) == 0
 
 
 # ----------------------------------------------------------------- brute force
