@@ -134,6 +134,15 @@ def test_int64_corner_arithmetic(ctx):
     _same(ctx.detect(pts2, 16, 16, 24, 4), oracle.detect(pts2, 16, 16, 24, 4))
 
 
+def test_largest_frame_and_depth(ctx):
+    # 32767 x 32767 at depth 24 (corner values up to 2^41): lines meeting at a
+    # grid vertex, so that the hierarchy reaches the leaf level around it
+    xs = [0, 2, 4, 6, 8, 10, 12, 14, 16, 18, 20, 22, 30000, 32766]
+    pts = np.array([[x, x // 2 + 100] for x in xs], np.int16)
+    for T in (13, 14, 15):
+        _same(ctx.detect(pts, 32767, 32767, 24, T), oracle.detect(pts, 32767, 32767, 24, T))
+
+
 def test_range_error_and_bad_arguments(ctx, hht):
     with pytest.raises(hht.HhtError) as e:
         ctx.detect(np.array([[3, 64]], np.int16), 64, 64, 5, 1)
