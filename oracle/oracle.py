@@ -71,7 +71,9 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
+            # $HHT_ORACLE_LIB names a prebuilt oracle library (the tests load
+            # deliberately broken builds this way to check that the pins fail)
+            lib = ctypes.CDLL(os.environ.get("HHT_ORACLE_LIB") or build())
             i16p = ctypes.POINTER(ctypes.c_int16)
             lib.oracle_detect.argtypes = [i16p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(_Leaf), ctypes.c_int64,
