@@ -49,6 +49,8 @@ MUTANTS = [
     ("removed points still counted as tested",
      "if (r->removed[V[k]]) continue; /* its codes were zeroed by an earlier solution() */\n            ++evaluated;",
      "++evaluated;\n            if (r->removed[V[k]]) continue;", 1, REMOVAL, None),
+    ("subtree keep mask read transposed", "+ (ci[q] / h) * side + cj[q] / h] != 0;",
+     "+ (cj[q] / h) * side + ci[q] / h] != 0;", 1, "tests/test_shard_gloo.py", "one_shard"),
     ("lines: 4-neighbourhood instead of 8", "if (di < -1 || di > 1 || dj < -1 || dj > 1) continue;",
      "if (di < -1 || di > 1 || dj < -1 || dj > 1 || (di != 0 && dj != 0)) continue;", 1, LINES, None),
 ]

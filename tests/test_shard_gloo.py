@@ -192,3 +192,25 @@ def test_bench_reference_arm_under_torchrun_prints_one_line_from_rank_0():
     assert rec["impl"] == "reference" and rec["n_gpus"] == 2 and rec["steps"] == 1
     assert rec["value"] > 0 and rec["e2e"]["value"] == rec["value"]
     assert rec["cpu_baseline"]["kind"] == "oracle" and rec["cpu_baseline"]["cores"] >= 1
+
+
+@pytest.mark.parametrize("split_level", [1, 2, 3])
+def test_one_shard_keeps_exactly_the_leaves_below_its_regions(split_level):
+    """The keep mask's layout (entry half * 4^k + a * 2^k + b for the level-k
+    region (a, b)): a shard's leaves are the unsharded leaves whose level-k
+    ancestor, (i >> (D - k), j >> (D - k)), it keeps; its statistics below k
+    are those of the unsharded run and at level k it passes only kept regions."""
+    import oracle
+    img = synth.plain_128(index=2)
+    D, k = img.depth, split_level
+    whole = oracle.detect(img.points, img.W, img.H, D, img.T)
+    side = 1 << k
+    rng = np.random.default_rng(100 + k)
+    keep = (rng.random(2 * side * side) < 0.5).astype(np.uint8)
+    part = oracle.detect_subtrees(img.points, img.W, img.H, D, img.T, k, keep)
+    lv = whole.leaves
+    sel = keep[lv[:, 0].astype(np.int64) * side * side + (lv[:, 1] >> (D - k)) * side + (lv[:, 2] >> (D - k))] == 1
+    assert np.array_equal(part.leaves, lv[sel])
+    assert np.array_equal(part.stats[:, :k], whole.stats[:, :k])
+    assert np.array_equal(part.stats[:, k, [0, 2, 3]], whole.stats[:, k, [0, 2, 3]])
+    assert np.all(part.stats[:, k, 1] <= whole.stats[:, k, 1])
