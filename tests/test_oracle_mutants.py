@@ -51,6 +51,11 @@ MUTANTS = [
      "++evaluated;\n            if (r->removed[V[k]]) continue;", 1, REMOVAL, None),
     ("subtree keep mask read transposed", "+ (ci[q] / h) * side + cj[q] / h] != 0;",
      "+ (cj[q] / h) * side + ci[q] / h] != 0;", 1, "tests/test_shard_gloo.py", "one_shard"),
+    ("lines: centre sums not weighted by votes",
+     "L->sum_i2 += (uint64_t)leaves[k].votes * (2u * (uint64_t)leaves[k].i + 1u);",
+     "L->sum_i2 += (2u * (uint64_t)leaves[k].i + 1u);", 1, LINES, None),
+    ("lines: peak ties go to the later leaf", "if (leaves[k].votes > L->votes) {", "if (leaves[k].votes >= L->votes) {",
+     1, LINES, None),
     ("lines: 4-neighbourhood instead of 8", "if (di < -1 || di > 1 || dj < -1 || dj > 1) continue;",
      "if (di < -1 || di > 1 || dj < -1 || dj > 1 || (di != 0 && dj != 0)) continue;", 1, LINES, None),
 ]
