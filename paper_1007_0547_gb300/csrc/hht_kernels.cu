@@ -924,14 +924,6 @@ __global__ void __launch_bounds__(256, 4) persistent_kernel(PersistentArgs f) {
 
 
 // ============================================================================ launchers
-namespace {
-int grid_for(const void* fn, int tpb, int num_sms) {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, tpb, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
-    return per_sm * num_sms;
-}
-}  // namespace
-
 int occupancy_select() {
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, select_kernel, kSelTPB, 0);
