@@ -195,7 +195,6 @@ int check_predicate(const hht_ctx* c, const hht_image& im) {
 
 constexpr int kSelTile = 1024;   // parents per select tile
 constexpr int kPersistentRetry = 1;  // run_wave: persistent capacities too small, run again level by level
-constexpr int kPassTile = 256 * 8;  // voters per pass block below which fewer blocks are launched
 
 #define CK(call)                                   \
     do {                                           \
