@@ -159,6 +159,20 @@ def count_region(points: np.ndarray, W: int, H: int, depth: int, half: int, i0: 
                                            W, H, depth, half, i0, j0, S))
 
 
+def _leaf_cap(n: int, depth: int, T: int) -> int:
+    """Leaf buffer size that lets a detection run once: an upper bound of the
+    leaf count.  A line's slope is below 1/2 in cell units, so it crosses at
+    most 3 cells of each of the K columns, and every leaf holds at least T
+    votes.  Capped at 2^26 leaves (1 GiB of address space; numpy leaves the
+    pages untouched until the oracle writes them), beyond which a second run
+    sizes the buffer."""
+    cap = 1 << 16
+    if 1 <= depth <= 24 and T >= 1:
+        K = 1 << depth
+        cap = max(cap, min(2 * K * K, 2 * (3 * K * n // T + 1), 1 << 26))
+    return cap
+
+
 def detect(points: np.ndarray, W: int, H: int, depth: int, T: int, mode: str = "exact",
            dump_regions: bool = False, region_cap: int = 1 << 22) -> OracleResult:
     """Run the oracle; raises ValueError on argument/range errors."""
@@ -170,18 +184,11 @@ def detect(points: np.ndarray, W: int, H: int, depth: int, T: int, mode: str = "
     nl = ctypes.c_int64(0)
     nr = ctypes.c_int64(0)
     regions = (_Region * region_cap)() if dump_regions else None
-    # Start from an upper bound of the leaf count, so that the detection runs
-    # once: a line's slope is below 1/2 in cell units, so it crosses at most 3
-    # cells of each of the K columns, and every leaf holds at least T votes;
-    # capped at 2^22 leaves (64 MB), beyond which a second run sizes the buffer.
-    cap = 1 << 16
-    if 1 <= depth <= 24 and T >= 1:
-        K = 1 << depth
-        cap = max(cap, min(2 * K * K, 2 * (3 * K * n // T + 1), 1 << 22))
+    cap = _leaf_cap(n, depth, T)
     while True:
-        leaves = (_Leaf * cap)()
+        leaves = np.empty((cap, 4), dtype=np.uint32)
         rc = lib.oracle_detect(pts.ctypes.data_as(ctypes.POINTER(ctypes.c_int16)), n, W, H, depth, T, m,
-                               leaves, cap, ctypes.byref(nl),
+                               leaves.ctypes.data_as(ctypes.POINTER(_Leaf)), cap, ctypes.byref(nl),
                                stats.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
                                regions, region_cap if dump_regions else 0, ctypes.byref(nr))
         if rc == -4:
@@ -195,7 +202,8 @@ def detect(points: np.ndarray, W: int, H: int, depth: int, T: int, mode: str = "
     if rc != 0:
         raise RuntimeError(f"oracle failed with code {rc}")
     k = int(nl.value)
-    lv = np.frombuffer(leaves, dtype=np.uint32).reshape(-1, 4)[:k].copy()
+    lv = leaves[:k].copy()
+    del leaves
     reg = None
     if dump_regions:
         r = min(int(nr.value), region_cap)
@@ -300,12 +308,12 @@ def detect_subtrees(points: np.ndarray, W: int, H: int, depth: int, T: int, spli
         raise ValueError("keep must hold 2 * 4**split_level entries")
     stats = np.zeros((2, depth + 1, 4), dtype=np.uint64)
     nl = ctypes.c_int64(0)
-    cap = 1 << 16
+    cap = _leaf_cap(pts.shape[0], depth, T)
     while True:
-        leaves = (_Leaf * cap)()
+        leaves = np.empty((cap, 4), dtype=np.uint32)
         rc = lib.oracle_detect_subtrees(pts.ctypes.data_as(ctypes.POINTER(ctypes.c_int16)), pts.shape[0], W, H,
                                         depth, T, split_level, km.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
-                                        leaves, cap, ctypes.byref(nl),
+                                        leaves.ctypes.data_as(ctypes.POINTER(_Leaf)), cap, ctypes.byref(nl),
                                         stats.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)))
         if rc == -4:
             cap = int(nl.value) + 1
@@ -313,7 +321,7 @@ def detect_subtrees(points: np.ndarray, W: int, H: int, depth: int, T: int, spli
         break
     if rc != 0:
         raise ValueError(f"oracle.detect_subtrees failed with code {rc}")
-    lv = np.frombuffer(leaves, dtype=np.uint32).reshape(-1, 4)[: int(nl.value)].copy()
+    lv = leaves[: int(nl.value)].copy()
     return OracleResult(lv, stats, None, rc)
 
 
