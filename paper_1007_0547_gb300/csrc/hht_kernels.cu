@@ -199,7 +199,8 @@ __device__ __forceinline__ void select_totals(const LevelArgs& a) {
 // caller does after a grid-wide barrier.
 __device__ __forceinline__ void select_body(const LevelArgs& a, bool standalone) {
     __shared__ uint32_t s_slot;
-    __shared__ uint32_t s_wrec[8], s_wleaf[8], s_wvox[8];
+    __shared__ uint32_t s_wrec[8], s_wleaf[8];
+    __shared__ uint64_t s_wvox[8];
     __shared__ uint64_t s_prefix[3];
     __shared__ unsigned long long s_nrec, s_nleaf, s_nvox;
 
@@ -220,7 +221,10 @@ __device__ __forceinline__ void select_body(const LevelArgs& a, bool standalone)
         uint32_t cnt[kSelPPT][4];
         uint32_t pass[kSelPPT], wmask[kSelPPT], geo[kSelPPT];
         bool leafy[kSelPPT];
-        uint32_t my_rec = 0, my_leaf = 0, my_vox = 0;
+        // voters to copy are summed in 64 bits at every stage: a tile's
+        // parents can hand their children more than 2^32 voters
+        uint32_t my_rec = 0, my_leaf = 0;
+        uint64_t my_vox = 0;
         // statistics run (records are sorted by unit)
         uint32_t run_unit = kNoRegion;
         int run_lev = 0;
@@ -300,25 +304,27 @@ __device__ __forceinline__ void select_body(const LevelArgs& a, bool standalone)
             }
         }
         // scan of (records, leaves, copied voters) over the tile
-        uint32_t inc_rec = my_rec, inc_leaf = my_leaf, inc_vox = my_vox;
+        uint32_t inc_rec = my_rec, inc_leaf = my_leaf;
+        uint64_t inc_vox = my_vox;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
             const uint32_t r = __shfl_up_sync(0xffffffffu, inc_rec, off);
             const uint32_t l = __shfl_up_sync(0xffffffffu, inc_leaf, off);
-            const uint32_t v = __shfl_up_sync(0xffffffffu, inc_vox, off);
+            const uint64_t v = __shfl_up_sync(0xffffffffu, inc_vox, off);
             if (lane >= off) { inc_rec += r; inc_leaf += l; inc_vox += v; }
         }
         if (lane == 31) { s_wrec[warp] = inc_rec; s_wleaf[warp] = inc_leaf; s_wvox[warp] = inc_vox; }
         __syncthreads();
         if (warp == 0) {
             const uint32_t wr = lane < 8 ? s_wrec[lane] : 0u, wl = lane < 8 ? s_wleaf[lane] : 0u;
-            const uint32_t wv = lane < 8 ? s_wvox[lane] : 0u;
-            uint32_t ir = wr, il = wl, iv = wv;
+            const uint64_t wv = lane < 8 ? s_wvox[lane] : 0ull;
+            uint32_t ir = wr, il = wl;
+            uint64_t iv = wv;
 #pragma unroll
             for (int off = 1; off < 8; off <<= 1) {
                 const uint32_t r = __shfl_up_sync(0xffffffffu, ir, off);
                 const uint32_t l = __shfl_up_sync(0xffffffffu, il, off);
-                const uint32_t v = __shfl_up_sync(0xffffffffu, iv, off);
+                const uint64_t v = __shfl_up_sync(0xffffffffu, iv, off);
                 if (lane >= off) { ir += r; il += l; iv += v; }
             }
             const uint64_t agg[3] = {__shfl_sync(0xffffffffu, ir, 7), __shfl_sync(0xffffffffu, il, 7),
