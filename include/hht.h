@@ -253,20 +253,23 @@ int hht_profile_read(hht_ctx *ctx, hht_profile_counters *out);
 /*
  * Single-image detection that allocates no memory (no paper counterpart:
  * this is a library-integration variant of hht_detect).  For callers that
- * cannot let a library call cudaMalloc: code being captured into a CUDA
- * graph (allocations and frees cannot be captured, and cudaFree synchronises
- * the device), processes whose device memory belongs to another allocator,
- * and latency-critical paths.  All scratch lives in one static device array
- * of HHT_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * cannot let a library call cudaMalloc: processes whose device memory belongs
+ * to another framework's allocator (a stray allocation can fail or fragment
+ * its pool), and loops that cannot take the device-wide synchronisation of an
+ * allocation or free.  All scratch lives in one static device array of
+ * HHT_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
  * the process exits; no context is needed.
  *   points: n points in host or device memory; leaves: caller buffer (host or
- *   device) of leaf_capacity entries; out: statistics and n_leaves (host);
- *   cuda_stream: the stream to run on (NULL = legacy default stream).
- * The call synchronises `cuda_stream` before it returns.  The first call on a
- * device looks up the array's device address (make it before any stream
- * capture).  The array keeps the previous call's contents; each call clears
- * what it needs.  Calls that overlap on the GPU (other streams or threads on
- * the same device) race on the array and must not be made.
+ *   device) of leaf_capacity entries; out: statistics, n_leaves and status
+ *   (host); cuda_stream: the stream to run on (NULL = legacy default stream).
+ * The call synchronises `cuda_stream` once per level (the level's totals size
+ * the next level) and before it returns, on success and on every error after
+ * its first device work.  The first call on a device looks up the array's
+ * device address and keeps it for the process's life, so make that first
+ * call before any stream capture begins; a cudaDeviceReset between calls is
+ * not supported.  The array keeps the previous call's contents; each call
+ * clears what it needs.  Calls that overlap on the GPU (other streams or
+ * threads on the same device) race on the array and must not be made.
  * Limits: n <= HHT_NOALLOC_MAX_POINTS, depth <= HHT_NOALLOC_MAX_DEPTH, at most
  * HHT_NOALLOC_MAX_LEAVES leaves, and the per-level voter lists must fit the
  * array; beyond them the call returns HHT_E_NOMEM (the limits on n and depth

@@ -1,21 +1,25 @@
 // hht_detect_noalloc: single-image detection that allocates nothing.
 //
-// Some callers cannot let a library allocate device memory: code that is
-// being captured into a CUDA graph (cudaMalloc / cudaFree cannot be captured,
-// and cudaFree synchronises the whole device), code running where another
-// framework owns the device memory and a stray cudaMalloc could fail or
-// fragment its pool, and latency-critical loops where an allocation's
-// implicit synchronisation is not acceptable.  For them this entry point runs
-// the same stage / select / pass kernels as hht_detect, with every piece of
-// scratch carved from one file-scope device array of kScratchBytes.
+// Some callers cannot let a library allocate device memory: code running where
+// another framework owns the device memory, so that a stray cudaMalloc could
+// fail or fragment its pool, and loops where the implicit device-wide
+// synchronisation of an allocation or free is not acceptable.  For them this
+// entry point runs the same stage / select / pass kernels as hht_detect, with
+// every piece of scratch carved from one file-scope device array of
+// kScratchBytes.  It synchronises its stream once per level, to read the
+// level's totals that size the next level.
 //
 // That array exists on every GPU that loads the library, from load until
-// the process exits.  Its device address is looked up once per device (the
-// first call on that device; make that first call before any stream capture)
-// with cudaGetSymbolAddress.  Every call shares the array and it keeps the
-// last call's contents, so everything a call needs at zero is cleared by that
-// call, and calls that overlap on the GPU (different streams, or different
-// host threads on the same device) race on it and must not be issued.
+// the process exits.  Its device address is looked up once per device, by
+// the first call on that device (make that first call before any stream
+// capture begins), with cudaGetSymbolAddress, and kept for the process's
+// life: a cudaDeviceReset between calls is not supported.  Every call shares
+// the array and it keeps the last call's contents, so everything a call needs
+// at zero is cleared by that call, and calls that overlap on the GPU
+// (different streams, or different host threads on the same device) race on
+// it and must not be issued.  Every return after the call's first device work
+// synchronises the stream first, so no kernel of a failed call is still
+// writing the array when it returns.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -88,16 +92,10 @@ struct TwoSided {
     }
 };
 
-}  // namespace
-
-extern "C" int hht_detect_noalloc(const hht_point* points, int64_t n, int32_t W, int32_t H, int32_t depth,
-                                  int32_t T, hht_leaf* leaves, uint64_t leaf_capacity, hht_result* out,
-                                  void* cuda_stream) {
-    if (!out || n < 0 || (n > 0 && !points) || W < 1 || H < 1 || W > HHT_MAX_SIDE || H > HHT_MAX_SIDE ||
-        depth < 1 || depth > HHT_MAX_DEPTH || T < 1)
-        return HHT_E_ARG;
-    if (n > HHT_NOALLOC_MAX_POINTS || depth > HHT_NOALLOC_MAX_DEPTH) return HHT_E_NOMEM;
-    cudaStream_t st = (cudaStream_t)cuda_stream;
+// The detection proper.  *touched is set once the call has queued device work
+// on `st` (the caller then synchronises before any error return).
+int noalloc_body(const hht_point* points, int64_t n, int32_t W, int32_t H, int32_t depth, int32_t T,
+                 hht_leaf* leaves, uint64_t leaf_capacity, hht_result* out, cudaStream_t st, bool* touched) {
     unsigned char* base = nullptr;
     int rc = scratch_for_current_device(&base);
     if (rc != HHT_OK) return rc;
@@ -166,6 +164,7 @@ extern "C" int hht_detect_noalloc(const hht_point* points, int64_t n, int32_t W,
         }                                           \
     } while (0)
     // everything a call relies on being zero or freshly written is set here
+    *touched = true;
     if (n > 0) NA_CK(cudaMemcpyAsync(d_pts, points, (size_t)n * sizeof(hht_point), cudaMemcpyDefault, st));
     NA_CK(cudaMemcpyAsync(d_units, units, sizeof units, cudaMemcpyHostToDevice, st));
     NA_CK(cudaMemcpyAsync(d_img_start, img_start, sizeof img_start, cudaMemcpyHostToDevice, st));
@@ -275,13 +274,36 @@ extern "C" int hht_detect_noalloc(const hht_point* points, int64_t n, int32_t W,
         nl += su[4 * depth + 1];
     }
     out->n_leaves = nl;
-    if (img_err) return out->status = HHT_E_RANGE;
-    if (nl != leaf_total) return out->status = HHT_E_CUDA;
-    if (nl > leaf_capacity || (nl > 0 && !leaves)) return out->status = HHT_E_CAPACITY;
+    if (img_err) return HHT_E_RANGE;
+    if (nl != leaf_total) return HHT_E_CUDA;
+    if (nl > leaf_capacity || (nl > 0 && !leaves)) return HHT_E_CAPACITY;
     if (nl > 0) {
         NA_CK(cudaMemcpyAsync(leaves, d_leaves, nl * sizeof(hht_leaf), cudaMemcpyDefault, st));
         NA_CK(cudaStreamSynchronize(st));
     }
 #undef NA_CK
-    return out->status = HHT_OK;
+    return HHT_OK;
+}
+
+}  // namespace
+
+extern "C" int hht_detect_noalloc(const hht_point* points, int64_t n, int32_t W, int32_t H, int32_t depth,
+                                  int32_t T, hht_leaf* leaves, uint64_t leaf_capacity, hht_result* out,
+                                  void* cuda_stream) {
+    if (!out || n < 0 || (n > 0 && !points) || W < 1 || H < 1 || W > HHT_MAX_SIDE || H > HHT_MAX_SIDE ||
+        depth < 1 || depth > HHT_MAX_DEPTH || T < 1)
+        return HHT_E_ARG;
+    if (n > HHT_NOALLOC_MAX_POINTS || depth > HHT_NOALLOC_MAX_DEPTH) return HHT_E_NOMEM;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    out->n_leaves = 0;
+    bool touched = false;
+    const int rc = noalloc_body(points, n, W, H, depth, T, leaves, leaf_capacity, out, st, &touched);
+    if (rc != HHT_OK && touched) {
+        // a failed call may still have kernels writing the shared array: wait
+        // for them (this wait's own error is not the one to report)
+        cudaStreamSynchronize(st);
+        cudaGetLastError();
+    }
+    out->status = rc;
+    return rc;
 }
