@@ -289,7 +289,15 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
     for (int g = 0; g < count; ++g) {
         const int lL = ceil_log2_i(std::max(im[g].W, im[g].H));
         Dmax = std::max(Dmax, im[g].depth);
-        if (lL + im[g].depth > 27) i64 = true;  // int32 corner arithmetic is exact only below this
+        // int32 corner arithmetic is exact while lL + depth <= 27: then
+        // |G| <= 4LK = 2^29 at every vertex of the parameter space, and the
+        // level kernel's partial sums (u0 = dJ - 1 - G(SW) built as
+        // W0 - x*A + (x + y)*K, with |x*A|, (x + y)*K < 2^28, and its column
+        // steps of at most 4x*S/4 < 2^28) stay within 1.5 * 2^30; the FHT's
+        // 2G values stay within 8LK = 2^30.  Both sides of the switch (27 and
+        // 28, on 32767^2 and 16^2 frames, points at the far corners and on
+        // lines through one vertex) are checked against the oracle on the GPU.
+        if (lL + im[g].depth > 27) i64 = true;
         img_start[g] = total;
         for (int h = 0; h < 2; ++h) {
             Unit& U = units[2 * g + h];

@@ -1,12 +1,13 @@
 """Serving with continuous batching (hht_submit / hht_progress / hht_poll).
 
 Requests join a running level loop at different steps and share every launch
-with the requests already in flight; each result must be identical to the
-same image run alone with hht_detect (exact: results are integers)."""
+with the requests already in flight; each result must equal the oracle's and
+the same image run alone with hht_detect (exact: results are integers)."""
 import numpy as np
 import pytest
 
 import synth
+from tests import full_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -65,6 +66,60 @@ def test_requests_joining_mid_flight_match_alone(hht):
     for k in range(len(imgs)):
         _same(results[k], want[k])
     ctx.close()
+
+
+def _oracle_futures(ex, imgs):
+    """The oracle's runs of each request, started on the host pool: requests
+    with a large n * 2^depth as level-2 subtree shares.  Returns per request
+    (split level, futures)."""
+    jobs = []
+    for im in imgs:
+        if im.n * (1 << im.depth) > 500_000_000:
+            jobs.append((2, full_oracle.submit_shares(ex, im.points, im.W, im.H, im.depth, im.T, 2)))
+        else:
+            jobs.append((0, full_oracle.submit_whole(ex, im.points, im.W, im.H, im.depth, im.T)))
+    return jobs
+
+
+def _oracle_result(job, depth):
+    split, futs = job
+    if split == 0:
+        r = futs[0].result()
+        return r.leaves, r.stats
+    return full_oracle.combine([f.result() for f in futs], split, depth)
+
+
+def test_serving_stream_against_oracle(hht):
+    """The first 40 requests of the serving stream (sides log-uniform in
+    64-4096, 1-256 segments, noise 0-3 %, depth ceil(log2 side), T in
+    16-256), arriving a few per step while earlier ones run, so that small and
+    4096-wide requests share launches: every result equals the oracle's."""
+    imgs = synth.serving_requests(40)
+    assert max(im.W for im in imgs) > 3500 and min(im.W for im in imgs) < 128
+    with full_oracle.pool() as ex:
+        # the oracle runs on the host cores while the GPU serves the stream
+        # (host threads only: no process is forked after the first GPU call)
+        want = _oracle_futures(ex, imgs)
+        ctx = hht.Context(device=0)
+        try:
+            tickets, results, pending, steps = {}, {}, list(range(len(imgs))), 0
+            while pending or len(results) < len(imgs):
+                for _ in range(3):
+                    if pending:
+                        k = pending.pop(0)
+                        im = imgs[k]
+                        tickets[ctx.submit(im.points, im.W, im.H, im.depth, im.T)] = k
+                ctx.progress()
+                steps += 1
+                for t in ctx.done_tickets():
+                    results[tickets.pop(t)] = ctx.poll(t)
+                assert steps < 5000
+        finally:
+            ctx.close()
+        for k, im in enumerate(imgs):
+            lv, st = _oracle_result(want[k], im.depth)
+            assert np.array_equal(results[k].stats, st), im.name
+            assert np.array_equal(results[k].leaves_numpy(), lv), im.name
 
 
 def test_small_budget_admits_gradually(hht):
