@@ -251,18 +251,13 @@ def run_front_end(args, rank):
     ctx.close()
 
 
-def run_serving(args, rank):
-    """Open-loop Poisson stream of detection requests through hht_submit /
-    hht_progress / hht_poll (continuous batching).  Rate = --serve-load x the
-    saturated request rate measured first on the same requests."""
+def serving_leg(ctx, n_requests: int, load: float):
+    """Open-loop Poisson stream of `n_requests` serving requests through
+    hht_submit / hht_progress / hht_done_tickets / hht_poll (continuous
+    batching) on `ctx`.  Rate = `load` x the saturated request rate measured
+    first on the same requests.  Returns the latency / throughput record."""
     import torch
-    from paper_1007_0547_gb300 import build as hbuild
-    hbuild.build()
-    from paper_1007_0547_gb300 import hht
-    if rank != 0:
-        return
-    reqs = synth.serving_requests(args.serve_requests)
-    ctx = hht.Context(device=0)
+    reqs = synth.serving_requests(n_requests)
 
     def drain(arrivals):
         """Submit request k at arrivals[k] (s after start); return per-request
@@ -300,18 +295,52 @@ def run_serving(args, rank):
     torch.cuda.synchronize()
     _, _, sat_s = drain([0.0] * len(reqs))
     sat_rate = len(reqs) / sat_s
-    rate = args.serve_load * sat_rate
+    rate = load * sat_rate
     arrivals = list(synth.poisson_arrivals(len(reqs), rate))
     t_arr, t_done, total_s = drain(arrivals)
     lat = sorted((d - a) * 1e3 for a, d in zip(t_arr, t_done))
-    line = {"metric": "serving latency p50/p99 (ms) and images/s", "value": lat[len(lat) // 2], "unit": "ms",
-            "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
-            "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+    return {"p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
             "images_per_s": len(reqs) / total_s, "saturated_images_per_s": sat_rate,
-            "offered_rate_per_s": rate, "load": args.serve_load,
-            "config": {"workload": "serving", "requests": len(reqs),
-                       "description": "side log-uniform 64-4096, 1-256 segments, noise 0-3%, depth ceil(log2 side), "
-                                      "T uniform 16-256; Poisson arrivals"}}
+            "offered_rate_per_s": rate, "load": load, "requests": len(reqs),
+            "description": "side log-uniform 64-4096, 1-256 segments, noise 0-3%, depth ceil(log2 side), "
+                           "T uniform 16-256; Poisson arrivals; latency = done - arrival (wall clock)"}
+
+
+def single_image_latency(ctx, runs: int = 30):
+    """Wall-clock latency of one hht_detect call (points resident on the
+    device, leaves into a device buffer) on the 128x128 and 1024x1024
+    workloads, after warm-up: p50 / p99 over `runs` calls."""
+    import torch
+    out = {}
+    for name, fn in (("plain_128", synth.plain_128), ("plain_1024", synth.plain_1024)):
+        im = fn()
+        pts = torch.from_numpy(im.points).cuda()
+        for _ in range(5):
+            ctx.detect(pts, im.W, im.H, im.depth, im.T)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(runs):
+            t0 = time.perf_counter()
+            ctx.detect(pts, im.W, im.H, im.depth, im.T)
+            ts.append((time.perf_counter() - t0) * 1e3)
+        ts.sort()
+        out[name] = {"p50_ms": ts[len(ts) // 2], "p99_ms": ts[min(len(ts) - 1, int(0.99 * len(ts)))],
+                     "runs": runs, "n": im.n}
+    return out
+
+
+def run_serving(args, rank):
+    """The serving leg alone, at --serve-requests and --serve-load."""
+    from paper_1007_0547_gb300 import build as hbuild
+    hbuild.build()
+    from paper_1007_0547_gb300 import hht
+    if rank != 0:
+        return
+    ctx = hht.Context(device=0)
+    leg = serving_leg(ctx, args.serve_requests, args.serve_load)
+    line = {"metric": "serving latency p50/p99 (ms) and images/s", "value": leg["p50_ms"], "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "data": "synthetic", **leg,
+            "config": {"workload": "serving", "requests": leg["requests"], "description": leg["description"]}}
     print(json.dumps(line), flush=True)
     ctx.close()
 
@@ -326,10 +355,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--no-persistent", action="store_true")
+    ap.add_argument("--no-persistent", "--no-levels", dest="no_persistent", action="store_true",
+                    help="skip the level-form comparison")
     ap.add_argument("--no-fht", action="store_true", help="skip the prior-art FHT circle-test comparison")
     ap.add_argument("--no-front-end", action="store_true", help="skip the front-end and line-extraction timings")
     ap.add_argument("--no-removal", action="store_true", help="skip the solution() (voter removal) timing")
+    ap.add_argument("--no-latency", action="store_true",
+                    help="skip the single-image latency (128x128, 1024x1024) and serving legs of the default line")
+    ap.add_argument("--leg-requests", type=int, default=200,
+                    help="requests of the serving leg in the default line")
     ap.add_argument("--serve", action="store_true", help="open-loop serving benchmark instead of the batch line")
     ap.add_argument("--front-end", action="store_true",
                     help="time only the front-end kernel (Sobel and split) on the 4096x4096 grey image")
@@ -377,6 +411,20 @@ def main():
             return [ctx.detect(*dev_images[0])]
         return ctx.detect_batch(dev_images)
 
+    # the first call of the fresh context: sizes from upper bounds, one CUDA
+    # graph captured and launched (wall clock, allocations included)
+    ctx.profile(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    step()
+    torch.cuda.synchronize()
+    fp = ctx.profile_read()
+    first_call = {"ms": (time.perf_counter() - t0) * 1e3, "graph_launches": int(fp["graph_launches"]),
+                  "graph_captures": int(fp["graph_captures"]), "graph_fallbacks": int(fp["graph_fallbacks"]),
+                  "what": "first detection call of a new context on this workload (wall clock; device memory "
+                          "allocated and the level loop's CUDA graph captured inside it)"}
+    ctx.profile(False)
+
     tuning = None
     if not args.no_autotune:
         # tile shape of the level kernel for this workload (cached per device and workload class)
@@ -398,6 +446,11 @@ def main():
     sampler = ClockSampler(phys)
     if world > 1:
         dist.barrier()
+    torch.cuda.synchronize()
+    # profiling adds event records to the captured graph: capture that graph
+    # in an untimed step, then reset the counters for the timed steps
+    ctx.profile(True)
+    step()
     torch.cuda.synchronize()
     ctx.profile(True)
     sampler.start()
@@ -483,14 +536,13 @@ def main():
         per_image = {"images_per_s": len(dev_images) / (seq_ms / 1e3),
                      "tests_per_s": tests_per_step / (seq_ms / 1e3), "ms": seq_ms}
 
-    # ---------------------------------------------------------------- persistent form (one launch per batch)
-    persistent = None
-    if len(dev_images) > 1 and not args.no_persistent:
-        ctx.set_batch_mode(hht.BATCH_PERSISTENT)
-        step()  # plans (level by level) the first time
-        step()
+    # ---------------------------------------------------------------- level form (host-driven, one sync per level)
+    levels = None
+    if not args.no_persistent:
+        ctx.set_batch_mode(hht.BATCH_LEVELS)
+        step()  # allocations
         torch.cuda.synchronize()
-        pts_ms = []
+        lv_ms = []
         for _ in range(max(2, args.steps // 2)):
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -498,11 +550,13 @@ def main():
             step()
             e1.record(stream)
             e1.synchronize()
-            pts_ms.append(e0.elapsed_time(e1))
-        ctx.set_batch_mode(hht.BATCH_LEVELS)
-        pm = sum(pts_ms) / len(pts_ms)
-        persistent = {"ms_per_step": pm, "images_per_s": len(dev_images) / (pm / 1e3),
-                      "tests_per_s": tests_per_step / (pm / 1e3)}
+            lv_ms.append(e0.elapsed_time(e1))
+        ctx.set_batch_mode(hht.BATCH_GRAPH)
+        lm = sum(lv_ms) / len(lv_ms)
+        levels = {"what": "the same detection in the level form: one selection and one pass launch per level with "
+                          "a host synchronisation each, buffers sized exactly",
+                  "ms_per_step": lm, "images_per_s": len(dev_images) / (lm / 1e3),
+                  "tests_per_s": tests_per_step / (lm / 1e3)}
 
     # ---------------------------------------------------------------- prior-art FHT circle test, same images
     fht = None
@@ -584,6 +638,16 @@ def main():
                    "ms_per_step": rm, "tests_per_s": rtests / (rm / 1e3), "images_per_s": len(dev_images) / (rm / 1e3),
                    "accepted_cells": int(sum(r.n_leaves for r in rres))}
 
+    # ---------------------------------------------------------------- single images and serving (configs 1, 2, 5)
+    latency, serving = None, None
+    if not args.no_latency and rank == 0:
+        lctx = hht.Context(device=local, stream=stream)
+        latency = single_image_latency(lctx)
+        lctx.close()
+        sctx = hht.Context(device=local)
+        serving = serving_leg(sctx, args.leg_requests, args.serve_load)
+        sctx.close()
+
     # ---------------------------------------------------------------- roofline of the pass kernel
     peak, peak_kind = read_peaks()
     achieved = (prof["pass_bytes"] / 1e9) / (prof["pass_ms"] / 1e3) if prof["pass_ms"] > 0 else 0.0
@@ -616,10 +680,19 @@ def main():
         "latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
                        "what": "one step (whole batch)"},
         "per_image_sequence": per_image,
-        "persistent_form": persistent,
+        "execution_form": {"headline": "graph: the whole level loop of a step is one CUDA-graph launch (stage, "
+                                       "then selection and pass per level, sizes read on the device), one host "
+                                       "synchronisation per step",
+                           "graph_launches_timed": int(prof["graph_launches"]),
+                           "graph_captures_timed": int(prof["graph_captures"]),
+                           "graph_fallbacks_timed": int(prof["graph_fallbacks"])},
+        "first_call": first_call,
+        "levels_form": levels,
         "fht_form": fht,
         "front_end": front,
         "removal_form": removal,
+        "single_image_latency": latency,
+        "serving": serving,
         "e2e": e2e,
         "roofline": roofline,
         "cpu_baseline": cpu,

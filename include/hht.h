@@ -239,12 +239,13 @@ typedef struct {
     double pass_ms;             /* summed device time of the pass launches */
     double select_ms;
     double stage_ms;
-    uint64_t persistent_launches;   /* batches run as one persistent launch (its time counts as pass_ms) */
-    uint64_t persistent_fallbacks;  /* persistent launches that ran out of room and were rerun level by level */
+    uint64_t graph_launches;   /* waves run as one CUDA-graph launch of the device-driven level loop */
+    uint64_t graph_fallbacks;  /* graph launches that ran out of room and were rerun level by level */
     uint64_t edges_launches;        /* front-end (Sobel and split) launches */
     uint64_t edges_pixels;          /* pixels they read */
     uint64_t edges_points;          /* edge points they wrote */
     double edges_ms;                /* their summed device time */
+    uint64_t graph_captures;        /* CUDA graphs of the level loop captured (the rest were replays) */
 } hht_profile_counters;
 
 int hht_profile_enable(hht_ctx *ctx, int on);
@@ -300,17 +301,28 @@ int hht_autotune(hht_ctx *ctx, const hht_image *images, int32_t count, int32_t *
 int hht_set_tuning(hht_ctx *ctx, int32_t shape);
 
 /*
- * Batch execution form.  HHT_BATCH_LEVELS (default): one selection and one
- * level-kernel launch per level, buffers sized exactly between levels.
- * HHT_BATCH_PERSISTENT: a job that this context has already run level by
- * level (same images, sizes, depths and thresholds) runs as one persistent
- * cooperative kernel launch for the whole level loop, with buffers sized from
- * that earlier run; if the data needs more room, the launch reports it and the
- * job is rerun level by level.  Results are the same in both forms.
+ * Execution form of hht_detect and hht_detect_batch (the results are the same
+ * in both).
+ * HHT_BATCH_GRAPH (default): the device-driven level loop.  Every buffer is
+ * sized from hard upper bounds of the job (a line crosses at most
+ * 2^l + (W - 1) 2^l / (2L) + 2 regions of level l, and a region passes with T
+ * votes or more), the stage kernel and every level's selection and level
+ * kernel read their sizes from device memory, and the whole loop is one CUDA
+ * graph, captured once per argument set and replayed: one graph launch and
+ * one host synchronisation per job, first call included.  On the legacy
+ * default stream (no capture possible) the same kernels are launched one after
+ * another with no host synchronisation between them.  Jobs whose bounds do
+ * not fit the memory budget, circle-test (FHT) jobs and subtree shards run in
+ * the level form.
+ * HHT_BATCH_LEVELS: one selection and one level-kernel launch per level, with
+ * a host synchronisation per level and every buffer sized exactly from the
+ * previous selection; a batch that does not fit the budget runs in waves.
+ * HHT_BATCH_PERSISTENT is the earlier name of HHT_BATCH_GRAPH.
  * Errors: HHT_E_ARG.
  */
 #define HHT_BATCH_LEVELS 0
-#define HHT_BATCH_PERSISTENT 1
+#define HHT_BATCH_GRAPH 1
+#define HHT_BATCH_PERSISTENT HHT_BATCH_GRAPH
 int hht_set_batch_mode(hht_ctx *ctx, int32_t mode);
 
 /*
@@ -444,12 +456,19 @@ int hht_set_predicate(hht_ctx *ctx, int32_t predicate);
  * nothing sets; each wait gives up after its bounded spin (about a second or
  * two), the job returns HHT_E_TIMEOUT, and the context stays usable for the
  * next call.  A selection with at most `arg` + 1 tiles is unaffected.
+ * HHT_FAULT_GRAPH_CAPACITY: in the next job of this context that runs in the
+ * graph form, the kernels are told that the stream of level 1 holds at most
+ * `arg` voter records (the buffer itself keeps its size), so that a level-1
+ * stream longer than that makes the selection report an overflow, every later
+ * kernel of the graph skips its work and the job is rerun level by level
+ * (counted in graph_fallbacks).
  * HHT_FAULT_NONE clears a pending injection.  No GPU fault, trap or endless
  * wait is involved.  Errors: HHT_E_ARG (NULL context, unknown kind, arg
  * outside [0, 2^32 - 1)).
  */
 #define HHT_FAULT_NONE 0
 #define HHT_FAULT_WITHHOLD_SCAN_TILE 1
+#define HHT_FAULT_GRAPH_CAPACITY 2
 int hht_inject_fault(hht_ctx *ctx, int32_t kind, int64_t arg);
 
 /* Short description of an HHT_* code (static string). */

@@ -194,7 +194,6 @@ int check_predicate(const hht_ctx* c, const hht_image& im) {
 }
 
 constexpr int kSelTile = 1024;   // parents per select tile
-constexpr int kPersistentRetry = 1;  // run_wave: persistent capacities too small, run again level by level
 
 #define CK(call)                                   \
     do {                                           \
@@ -235,60 +234,29 @@ int hht::copy_out(hht_ctx* c, void* dst, const void* src, size_t bytes) {
 
 namespace {
 
-// The persistent launch, through a CUDA graph captured once per argument set
-// (replayed while the buffers and sizes are unchanged).  Capture is not
-// possible on the legacy default stream or inside another capture; then the
-// kernel is launched directly.
-int launch_persistent_graph(hht_ctx* c, const PersistentArgs& f, bool i64, int grid) {
-    cudaStream_t st = c->stream;
-    const unsigned char* fb = reinterpret_cast<const unsigned char*>(&f);
-    std::vector<unsigned char> key(fb, fb + sizeof f);
-    key.push_back(i64 ? 1 : 0);
-    if (c->graph_exec && c->graph_grid == grid && key == c->graph_args) {
-        CK(cudaGraphLaunch(c->graph_exec, st));
-        return HHT_OK;
-    }
-    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-    const bool can_capture = st != nullptr && !c->graph_capture_failed &&
-                             cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
-    if (can_capture) {
-        cudaGraph_t g = nullptr;
-        cudaGraphExec_t ge = nullptr;
-        bool ok = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-        if (ok) {
-            const int lr = launch_persistent(f, i64, grid, st);
-            ok = cudaStreamEndCapture(st, &g) == cudaSuccess && lr == 0 && g != nullptr;
-        }
-        if (ok) ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
-        if (g) cudaGraphDestroy(g);
-        if (ok) {
-            if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
-            c->graph_exec = ge;
-            c->graph_args = key;
-            c->graph_grid = grid;
-            CK(cudaGraphLaunch(c->graph_exec, st));
-            return HHT_OK;
-        }
-        cudaGetLastError();
-        c->graph_capture_failed = true;  // launch directly from now on
-    }
-    return launch_persistent(f, i64, grid, st) == 0 ? HHT_OK : HHT_E_CUDA;
-}
+// Host-side description of one wave of a job: its units (two per image),
+// where each image's points start, and the sizes every form needs.
+struct Wave {
+    int count = 0, n_units = 0, Dmax = 0;
+    bool i64 = false, fht = false;
+    uint64_t total = 0, v0_len = 0;  // points of all images; level-0 voter records
+    size_t stats_words = 0;
+    std::vector<Unit> units;
+    std::vector<uint64_t> img_start;
+    std::vector<uint32_t> img_unit;
+    uint64_t leaf_base = 0;  // leaves of the job's earlier waves (this wave's follow them)
+};
 
-// Run one wave of images through the level loop; fills outs[k] for k in
-// [0, count).  Returns HHT_OK or a job-level error (per-image errors are in
-// outs[k].status).
-int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int job_first) {
-    cudaStream_t st = c->stream;
-    const int n_units = 2 * count;
-    int Dmax = 0;
-    bool i64 = false;
-    uint64_t total = 0, v0_len = 0;
-    std::vector<Unit> units(n_units);
-    std::vector<uint64_t> img_start(count + 1);
+void describe_wave(hht_ctx* c, const hht_image* im, int count, int job_first, Wave& w) {
+    w.count = count;
+    w.n_units = 2 * count;
+    w.fht = c->predicate == HHT_PREDICATE_FHT;
+    w.units.assign(w.n_units, Unit{});
+    w.img_start.assign(count + 1, 0);
+    w.img_unit.assign(count, 0);
     for (int g = 0; g < count; ++g) {
         const int lL = ceil_log2_i(std::max(im[g].W, im[g].H));
-        Dmax = std::max(Dmax, im[g].depth);
+        w.Dmax = std::max(w.Dmax, im[g].depth);
         // int32 corner arithmetic is exact while lL + depth <= 27: then
         // |G| <= 4LK = 2^29 at every vertex of the parameter space, and the
         // level kernel's partial sums (u0 = dJ - 1 - G(SW) built as
@@ -297,10 +265,11 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
         // 2G values stay within 8LK = 2^30.  Both sides of the switch (27 and
         // 28, on 32767^2 and 16^2 frames, points at the far corners and on
         // lines through one vertex) are checked against the oracle on the GPU.
-        if (lL + im[g].depth > 27) i64 = true;
-        img_start[g] = total;
+        if (lL + im[g].depth > 27) w.i64 = true;
+        w.img_start[g] = w.total;
+        w.img_unit[g] = (uint32_t)(2 * g);
         for (int h = 0; h < 2; ++h) {
-            Unit& U = units[2 * g + h];
+            Unit& U = w.units[2 * g + h];
             U.lL = lL;
             U.D = im[g].depth;
             U.T = im[g].T;
@@ -316,163 +285,119 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
             U.inactive = on ? 0u : 1u;
             if (!on) U.n = 0;
             U.pad2 = 0;
-            U.v0_off = v0_len;
-            if (U.D >= 2 && on) v0_len += (uint64_t)im[g].n;
+            U.v0_off = w.v0_len;
+            if (U.D >= 2 && on) w.v0_len += (uint64_t)im[g].n;
         }
-        total += (uint64_t)im[g].n;
+        w.total += (uint64_t)im[g].n;
     }
-    img_start[count] = total;
+    w.img_start[count] = w.total;
+    w.stats_words = (size_t)w.n_units * (kMaxDepth + 1) * 4;
+    w.leaf_base = c->job_leaves;
+}
 
-    // ---- inputs and job state
-    RK(ensure(c, c->pts, std::max<uint64_t>(total, 1) * sizeof(hht_point)));
+// Inputs and job state on the device, common to both forms: points, units,
+// image table, statistics (level 0 filled in), level totals, the level-0
+// region records and counters, status, leaf count.
+int upload_wave(hht_ctx* c, const hht_image* im, const Wave& w) {
+    cudaStream_t st = c->stream;
+    const int count = w.count, n_units = w.n_units;
+    RK(ensure(c, c->pts, std::max<uint64_t>(w.total, 1) * sizeof(hht_point)));
     for (int g = 0; g < count; ++g)
         if (im[g].n > 0)
-            CK(cudaMemcpyAsync((char*)c->pts.p + img_start[g] * sizeof(hht_point), im[g].points,
+            CK(cudaMemcpyAsync((char*)c->pts.p + w.img_start[g] * sizeof(hht_point), im[g].points,
                                (size_t)im[g].n * sizeof(hht_point), cudaMemcpyDefault, st));
     RK(ensure(c, c->units, n_units * sizeof(Unit)));
     RK(ensure(c, c->img_start, (count + 1) * sizeof(uint64_t)));
     RK(ensure(c, c->img_unit, count * sizeof(uint32_t)));
-    std::vector<uint32_t> img_unit(count);
-    for (int g = 0; g < count; ++g) img_unit[g] = (uint32_t)(2 * g);
     RK(ensure(c, c->img_err, count * sizeof(uint32_t)));
-    const size_t stats_words = (size_t)n_units * (kMaxDepth + 1) * 4;
-    RK(ensure(c, c->stats, stats_words * sizeof(uint64_t)));
+    RK(ensure(c, c->stats, w.stats_words * sizeof(uint64_t)));
     RK(ensure(c, c->infos, (kMaxDepth + 1) * sizeof(LevelInfo)));
     RK(ensure(c, c->status, sizeof(DeviceStatus)));
     RK(ensure(c, c->leaf_total, sizeof(uint64_t)));
+    RK(ensure(c, c->dims, sizeof(JobDims)));
+    RK(ensure(c, c->rec[0], n_units * sizeof(Region)));
+    RK(ensure(c, c->cnt[0], n_units * 4 * sizeof(uint32_t)));
+    RK(ensure(c, c->vox[0], std::max<uint64_t>(w.v0_len, 1) * sizeof(Voter)));
 
-    c->h_stats.assign(stats_words, 0);
+    c->h_stats.assign(w.stats_words, 0);
     for (int u = 0; u < n_units; ++u) {
         uint64_t* s0 = &c->h_stats[(size_t)u * (kMaxDepth + 1) * 4];
         s0[0] = 1;                       // level 0: one region tested
         s0[1] = 1;                       // ... and always split
-        s0[3] = (uint64_t)units[u].n;    // one code per point
+        s0[3] = (uint64_t)w.units[u].n;  // one code per point
     }
     c->h_infos.assign(kMaxDepth + 1, LevelInfo{});
     c->h_infos[0].n_regions = (uint64_t)n_units;
-    c->h_infos[0].n_voters = v0_len;
-    std::vector<Region> roots(n_units);
-    for (int u = 0; u < n_units; ++u) roots[u] = Region{(uint32_t)u, 0u, 0u, (uint32_t)units[u].n};
-
-    // job signature for the persistent form's size plan
-    uint64_t sig = 1469598103934665603ull;
-    auto mix = [&](uint64_t v) { sig = (sig ^ v) * 1099511628211ull; };
-    mix((uint64_t)count);
-    for (int g = 0; g < count; ++g) {
-        mix((uint64_t)im[g].n);
-        mix(((uint64_t)im[g].W << 32) | (uint64_t)im[g].H);
-        mix(((uint64_t)im[g].depth << 32) | (uint64_t)im[g].T);
-    }
-    const bool fht = c->predicate == HHT_PREDICATE_FHT;
-    if (fht && i64) return HHT_E_ARG;  // checked by the entry points before any device work
-    const int occ_p = i64 ? c->occ_persistent64 : c->occ_persistent32;
-    const bool persistent = !fht && !c->job_halves && !c->job_keep && c->batch_mode == 1 && c->plan.valid &&
-                            c->plan.sig == sig && occ_p > 0;
-    uint64_t cap_rec = 0, cap_vox = 0, cap_tiles = 0;
-    if (persistent) {
-        cap_rec = std::max<uint64_t>(c->plan.cap_rec, (uint64_t)n_units);
-        cap_vox = std::max<uint64_t>(c->plan.cap_vox, v0_len);
-        cap_tiles = (cap_rec + kSelTile - 1) / kSelTile + 1;
-        for (int k = 0; k < 2; ++k) {
-            RK(ensure(c, c->rec[k], cap_rec * sizeof(Region)));
-            RK(ensure(c, c->preg[k], cap_rec * sizeof(PassRegion)));
-            RK(ensure(c, c->cnt[k], cap_rec * 4 * sizeof(uint32_t)));
-            RK(ensure(c, c->vox[k], std::max<uint64_t>(cap_vox, 1) * sizeof(Voter)));
-        }
-        RK(ensure(c, c->cursors, cap_rec * sizeof(unsigned long long)));
-        RK(ensure_keep(c, c->leaves, (c->job_leaves + c->plan.cap_leaves + 1) * sizeof(DevLeaf),
-                       c->job_leaves * sizeof(DevLeaf)));
-        if (cap_tiles * 4 > c->sel_flags.bytes) RK(ensure(c, c->sel_flags, cap_tiles * 4, true));
-        RK(ensure(c, c->sel_data, cap_tiles * 2 * 3 * sizeof(uint64_t)));
-    }
-    RK(ensure(c, c->rec[0], n_units * sizeof(Region)));
-    RK(ensure(c, c->cnt[0], n_units * 4 * sizeof(uint32_t)));
-    RK(ensure(c, c->vox[0], std::max<uint64_t>(v0_len, 1) * sizeof(Voter)));
-    CK(cudaMemcpyAsync(c->units.p, units.data(), n_units * sizeof(Unit), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(c->img_start.p, img_start.data(), (count + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(c->img_unit.p, img_unit.data(), count * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(c->stats.p, c->h_stats.data(), stats_words * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(c->infos.p, c->h_infos.data(), (kMaxDepth + 1) * sizeof(LevelInfo), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(c->rec[0].p, roots.data(), n_units * sizeof(Region), cudaMemcpyHostToDevice, st));
+    c->h_infos[0].n_voters = w.v0_len;
+    c->h_roots.resize(n_units);
+    for (int u = 0; u < n_units; ++u) c->h_roots[u] = Region{(uint32_t)u, 0u, 0u, (uint32_t)w.units[u].n};
+    c->h_dims = JobDims{w.total, count, 0};
+    CK(cudaMemcpyAsync(c->units.p, w.units.data(), n_units * sizeof(Unit), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->img_start.p, w.img_start.data(), (count + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice,
+                       st));
+    CK(cudaMemcpyAsync(c->img_unit.p, w.img_unit.data(), count * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->stats.p, c->h_stats.data(), w.stats_words * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->infos.p, c->h_infos.data(), (kMaxDepth + 1) * sizeof(LevelInfo), cudaMemcpyHostToDevice,
+                       st));
+    CK(cudaMemcpyAsync(c->rec[0].p, c->h_roots.data(), n_units * sizeof(Region), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->dims.p, &c->h_dims, sizeof(JobDims), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(c->cnt[0].p, 0, n_units * 4 * sizeof(uint32_t), st));
     CK(cudaMemsetAsync(c->status.p, 0, sizeof(DeviceStatus), st));
-    // this wave's leaves follow those of the job's earlier waves
-    const uint64_t wave_leaf_base = c->job_leaves;
     CK(cudaMemcpyAsync(c->leaf_total.p, &c->job_leaves, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(c->img_err.p, 0, count * sizeof(uint32_t), st));
+    return HHT_OK;
+}
 
-    LevelInfo* d_infos = (LevelInfo*)c->infos.p;
+// The level form's and the graph form's arguments of step s, apart from the
+// capacities and the voter streams, which each form sets.
+LevelArgs level_args(hht_ctx* c, int s) {
+    const int pi = (s - 1) & 1, ci = s & 1;
+    LevelArgs a{};
+    a.units = (const Unit*)c->units.p;
+    a.parents = (const Region*)c->rec[pi].p;
+    a.pregions = (PassRegion*)c->preg[pi].p;
+    a.parent_cnt = (const uint32_t*)c->cnt[pi].p;
+    a.children = (Region*)c->rec[ci].p;
+    a.child_cnt = (uint32_t*)c->cnt[ci].p;
+    a.cursor = (unsigned long long*)c->cursors.p;
+    a.leaves = (DevLeaf*)c->leaves.p;
+    a.stats = (uint64_t*)c->stats.p;
+    a.info_prev = (LevelInfo*)c->infos.p + (s - 1);
+    a.info = (LevelInfo*)c->infos.p + s;
+    a.leaf_total = (uint64_t*)c->leaf_total.p;
+    a.status = (DeviceStatus*)c->status.p;
+    a.level = s;
+    a.num_sms = c->num_sms;
+    a.scan = (ScanState*)c->scan_states.p;
+    a.tile_flags = (uint32_t*)c->sel_flags.p;
+    a.tile_data = (uint64_t*)c->sel_data.p;
+    a.withhold_tile_plus1 = c->inject_tile >= 0 ? (uint32_t)(c->inject_tile + 1) : 0u;
+    a.keep = c->job_keep;
+    a.keep_level = c->job_keep_level;
+    return a;
+}
+
+// The level form: stage, then per level one selection and one pass launch,
+// every buffer sized exactly from the selection's totals (one host
+// synchronisation per level).  On return *leaf_total holds the leaf count
+// after the wave and *err the device status bits.
+int run_levels(hht_ctx* c, const Wave& w, uint64_t* leaf_total, uint32_t* err) {
+    cudaStream_t st = c->stream;
     DeviceStatus* d_status = (DeviceStatus*)c->status.p;
-    ScanState* d_scan = (ScanState*)c->scan_states.p;
-
-    uint64_t leaf_total = wave_leaf_base;
-    uint32_t err = 0;
-    if (persistent) {
-        PersistentArgs f{};
-        f.base.units = (const Unit*)c->units.p;
-        f.base.cursor = (unsigned long long*)c->cursors.p;
-        f.base.leaves = (DevLeaf*)c->leaves.p;
-        f.base.stats = (uint64_t*)c->stats.p;
-        f.base.leaf_total = (uint64_t*)c->leaf_total.p;
-        f.base.scan = d_scan + 0;
-        f.base.tile_flags = (uint32_t*)c->sel_flags.p;
-        f.base.tile_data = (uint64_t*)c->sel_data.p;
-        f.base.status = d_status;
-        f.base.cap_children = cap_rec;
-        f.base.cap_voters = cap_vox;
-        f.base.cap_leaves = c->leaves.bytes / sizeof(DevLeaf);
-        f.base.cap_tiles = cap_tiles;
-        f.base.num_sms = c->num_sms;
-        f.base.withhold_tile_plus1 = c->inject_tile >= 0 ? (uint32_t)(c->inject_tile + 1) : 0u;
-        for (int k = 0; k < 2; ++k) {
-            f.rec[k] = (Region*)c->rec[k].p;
-            f.preg[k] = (PassRegion*)c->preg[k].p;
-            f.cnt[k] = (uint32_t*)c->cnt[k].p;
-            f.vox[k] = (Voter*)c->vox[k].p;
-        }
-        f.infos = d_infos;
-        f.pts = (const int16_t*)c->pts.p;
-        f.total_pts = total;
-        f.img_start = (const uint64_t*)c->img_start.p;
-        f.img_unit = (const uint32_t*)c->img_unit.p;
-        f.img_err = (uint32_t*)c->img_err.p;
-        f.n_images = count;
-        f.Dmax = Dmax;
-        {
-            TraceRange tr_k("persistent level loop");
-            ProfScope ps(c, 2);
-            RK(launch_persistent_graph(c, f, i64, c->num_sms * occ_p));
-        }
-        c->prof.launches += 1;
-        CK(cudaMemcpyAsync(&leaf_total, c->leaf_total.p, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
-        CK(cudaMemcpyAsync(c->h_infos.data(), d_infos, (Dmax + 1) * sizeof(LevelInfo), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        c->persistent_runs += 1;
-        c->prof.persistent_launches += 1;
-        // algorithmic bytes of the level passes inside the launch (as if launched one by one)
-        for (int s = 1; s < Dmax; ++s) {
-            const uint64_t nin = c->h_infos[s - 1].n_voters, nout = c->h_infos[s].n_voters;
-            if (nin == 0) continue;
-            c->prof.pass_launches += 1;
-            c->prof.voters_read += nin;
-            c->prof.voters_written += nout;
-            c->prof.pass_bytes += 8 * (nin + nout);
-        }
-    }
-    if (!persistent) {
+    LevelInfo* d_infos = (LevelInfo*)c->infos.p;
+    *leaf_total = w.leaf_base;
+    *err = 0;
+    {
         TraceRange tr_k("stage");
         ProfScope ps(c, 0);
-        if (launch_stage((const int16_t*)c->pts.p, total, (const Unit*)c->units.p, count,
+        if (launch_stage((const int16_t*)c->pts.p, w.total, (const Unit*)c->units.p, w.count,
                          (const uint64_t*)c->img_start.p, (const uint32_t*)c->img_unit.p, (Voter*)c->vox[0].p,
-                         (uint32_t*)c->cnt[0].p, (uint64_t*)c->stats.p, (uint32_t*)c->img_err.p, d_status, i64,
-                         st, fht) != 0)
+                         (uint32_t*)c->cnt[0].p, (uint64_t*)c->stats.p, (uint32_t*)c->img_err.p, d_status, w.i64,
+                         st, w.fht) != 0)
             return HHT_E_CUDA;
-        if (total > 0) c->prof.launches += 1;
+        if (w.total > 0) c->prof.launches += 1;
     }
-
-    // ---- level loop (sizes recorded as the plan of the persistent form)
-    uint64_t plan_rec = (uint64_t)n_units, plan_vox = v0_len;
-    for (int s = 1; s <= Dmax && !persistent; ++s) {
+    for (int s = 1; s <= w.Dmax; ++s) {
         TraceRange tr_level(level_name(s));
         const int pi = (s - 1) & 1, ci = s & 1;
         const uint64_t P = c->h_infos[s - 1].n_regions;
@@ -481,44 +406,20 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
         RK(ensure(c, c->preg[pi], P * sizeof(PassRegion)));
         RK(ensure(c, c->rec[ci], 4 * P * sizeof(Region)));
         RK(ensure(c, c->cnt[ci], 4 * P * 4 * sizeof(uint32_t)));
-        const uint64_t cap_leaves = leaf_total + 4 * P;
-        RK(ensure_keep(c, c->leaves, cap_leaves * sizeof(DevLeaf), leaf_total * sizeof(DevLeaf)));
+        const uint64_t cap_leaves = *leaf_total + 4 * P;
+        RK(ensure_keep(c, c->leaves, cap_leaves * sizeof(DevLeaf), *leaf_total * sizeof(DevLeaf)));
         const uint64_t sel_tiles = (P + kSelTile - 1) / kSelTile;
-        if ((sel_tiles + 1) * 4 > c->sel_flags.bytes) {
-            RK(ensure(c, c->sel_flags, (sel_tiles + 1) * 4, true));
-        }
+        if ((sel_tiles + 1) * 4 > c->sel_flags.bytes) RK(ensure(c, c->sel_flags, (sel_tiles + 1) * 4, true));
         RK(ensure(c, c->sel_data, (sel_tiles + 1) * 2 * 3 * sizeof(uint64_t)));
         RK(ensure(c, c->cursors, 4 * P * sizeof(unsigned long long)));
 
-        LevelArgs a{};
-        a.units = (const Unit*)c->units.p;
-        a.parents = (const Region*)c->rec[pi].p;
-        a.pregions = (PassRegion*)c->preg[pi].p;
-        a.parent_cnt = (const uint32_t*)c->cnt[pi].p;
-        a.children = (Region*)c->rec[ci].p;
-        a.child_cnt = (uint32_t*)c->cnt[ci].p;
-        a.cursor = (unsigned long long*)c->cursors.p;
-        a.leaves = (DevLeaf*)c->leaves.p;
-        a.stats = (uint64_t*)c->stats.p;
-        a.info_prev = d_infos + (s - 1);
-        a.info = d_infos + s;
-        a.leaf_total = (uint64_t*)c->leaf_total.p;
-        a.status = d_status;
+        LevelArgs a = level_args(c, s);
         a.cap_children = 4 * P;
         a.cap_leaves = cap_leaves;
-        a.cap_voters = c->vox[ci].bytes / sizeof(Voter);
-        a.level = s;
-        a.num_sms = c->num_sms;
-        a.scan = d_scan + 0;
-        a.tile_flags = (uint32_t*)c->sel_flags.p;
-        a.tile_data = (uint64_t*)c->sel_data.p;
         a.cap_tiles = sel_tiles;
-        a.withhold_tile_plus1 = c->inject_tile >= 0 ? (uint32_t)(c->inject_tile + 1) : 0u;
-        a.keep = c->job_keep;
-        a.keep_level = c->job_keep_level;
-        const int sel_grid = (int)std::min<uint64_t>(sel_tiles, (uint64_t)c->num_sms * c->occ_select);
         // select's capacity test on the voter stream is re-done below with the exact size
         a.cap_voters = UINT64_MAX;
+        const int sel_grid = (int)std::min<uint64_t>(sel_tiles, (uint64_t)c->num_sms * c->occ_select);
         {
             TraceRange tr_k("select");
             ProfScope ps(c, 1);
@@ -531,17 +432,15 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
         DeviceStatus hs{};
         CK(cudaMemcpyAsync(&hs, d_status, sizeof hs, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        err = hs.err;
+        *err = hs.err;
         if (c->debug)
             fprintf(stderr, "[hht]   step %d: parents %llu, regions %llu, voters in %llu, out %llu, leaves %llu, held %.2f GB\n",
                     s, (unsigned long long)P, (unsigned long long)c->h_infos[s].n_regions,
                     (unsigned long long)c->h_infos[s - 1].n_voters, (unsigned long long)c->h_infos[s].n_voters,
                     (unsigned long long)c->h_infos[s].n_leaves, c->held / 1e9);
-        if (err) break;
-        leaf_total += c->h_infos[s].n_leaves;
-        plan_rec = std::max<uint64_t>(plan_rec, c->h_infos[s].n_regions);
-        plan_vox = std::max<uint64_t>(plan_vox, c->h_infos[s].n_voters);
-        if (s == Dmax) break;
+        if (*err) break;
+        *leaf_total += c->h_infos[s].n_leaves;
+        if (s == w.Dmax) break;
 
         const uint64_t nin = c->h_infos[s - 1].n_voters;
         if (nin == 0) continue;  // no unit needs level s+1 counts
@@ -550,16 +449,16 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
         a.vin = (const Voter*)c->vox[pi].p;
         a.vout = (Voter*)c->vox[ci].p;
         a.cap_voters = nout;
-        const int shape = (i64 || fht) ? 0 : c->pass_shape;
-        const int occ = fht ? c->occ_pass_fht : (i64 ? c->occ_pass64 : c->occ_shape[shape]);
+        const int shape = (w.i64 || w.fht) ? 0 : c->pass_shape;
+        const int occ = w.fht ? c->occ_pass_fht : (w.i64 ? c->occ_pass64 : c->occ_shape[shape]);
         // enough warp slices to fill the device, no more than the stream needs
-        const uint64_t tile = 8ull * (uint64_t)(fht ? 256 : pass_threads(i64, shape));
+        const uint64_t tile = 8ull * (uint64_t)(w.fht ? 256 : pass_threads(w.i64, shape));
         const uint64_t want_blocks = (nin + tile - 1) / tile;
         const int pass_grid = (int)std::min<uint64_t>(want_blocks, (uint64_t)c->num_sms * occ);
         {
             TraceRange tr_k("pass");
             ProfScope ps(c, 2);
-            if (launch_pass(a, i64, std::max(pass_grid, 1), st, shape, fht) != 0) return HHT_E_CUDA;
+            if (launch_pass(a, w.i64, std::max(pass_grid, 1), st, shape, w.fht) != 0) return HHT_E_CUDA;
         }
         c->prof.launches += 1;
         c->prof.pass_launches += 1;
@@ -567,21 +466,302 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
         c->prof.voters_written += nout;
         c->prof.pass_bytes += 8 * (nin + nout);
     }
+    return HHT_OK;
+}
 
-    // ---- outputs
-    CK(cudaMemcpyAsync(c->h_stats.data(), c->stats.p, stats_words * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
-    c->h_img_err.assign(count, 0);
-    CK(cudaMemcpyAsync(c->h_img_err.data(), c->img_err.p, count * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+// Capacities of the graph form, from hard upper bounds of the wave's sizes.
+// At level l a region is a cell of a 2^l x 2^l grid.  A line's voting cells
+// in column i are the j with G(i, j) < 0 <= G(i + 1, j + 1), an interval of
+// ceil(b_i) - ceil(b_{i+1}) + 1 cells where b_i = j at which G(i, j) = 0;
+// summed over the 2^l columns this telescopes to at most
+// 2^l + x * 2^l / (2L) + 1 cells, and x < W (half 0) or x < H (half 1).  So a
+// half's voters at level l (the votes of its regions) are at most
+// n * (2^l + (W_h - 1) 2^l / (2L) + 2), its passed regions at most that / T
+// (each holds T votes or more) and 4^l, and its leaves likewise at its depth.
+struct GraphCaps {
+    uint64_t vox[2] = {1, 1};  // voter records per stream (even / odd levels)
+    uint64_t rec[2] = {1, 1};  // region records per level (even / odd levels)
+    uint64_t cursors = 1, tiles = 1, leaves = 0;
+    uint64_t bytes = 0;
+};
+
+uint64_t sat_add(uint64_t a, uint64_t b) { return a > UINT64_MAX - b ? UINT64_MAX : a + b; }
+
+bool graph_caps(const Wave& w, GraphCaps& cap) {
+    std::vector<uint64_t> vox(w.Dmax + 1, 0), rec(w.Dmax + 1, 0);
+    uint64_t leaves = 0;
+    for (int u = 0; u < w.n_units; ++u) {
+        const Unit& U = w.units[u];
+        const uint64_t n = (uint64_t)U.n;
+        const uint64_t L = 1ull << U.lL;
+        const uint64_t Wh = (uint64_t)(U.half ? U.H : U.W);
+        // votes of all level-l regions (n lines of at most per_line cells,
+        // and no more cells than the level has): below 2^56 for D <= 24
+        auto votes = [&](int l) {
+            const uint64_t col = 1ull << l;
+            const uint64_t per_line = col + (Wh - 1) * col / (2 * L) + 2;
+            return n * std::min(per_line, col * col);
+        };
+        for (int l = 0; l <= U.D; ++l) {
+            if (l <= U.D - 2) vox[l] = sat_add(vox[l], votes(l));
+            if (l == 0) rec[0] = sat_add(rec[0], 1);  // the level-0 region of every unit
+            else if (l < U.D) rec[l] = sat_add(rec[l], std::min<uint64_t>(1ull << (2 * l), votes(l) / (uint64_t)U.T));
+        }
+        leaves = sat_add(leaves, std::min<uint64_t>(1ull << (2 * U.D), votes(U.D) / (uint64_t)U.T));
+    }
+    for (int l = 0; l <= w.Dmax; ++l) {
+        cap.vox[l & 1] = std::max(cap.vox[l & 1], vox[l]);
+        cap.rec[l & 1] = std::max(cap.rec[l & 1], rec[l]);
+        if (l >= 1) cap.cursors = std::max(cap.cursors, rec[l]);
+    }
+    // 32-bit region indices, and sizes far beyond any device
+    if (std::max(cap.rec[0], cap.rec[1]) > kMaxLevelRecords) return false;
+    if (std::max(cap.vox[0], cap.vox[1]) > (1ull << 40) || leaves > (1ull << 40)) return false;
+    cap.tiles = (std::max(cap.rec[0], cap.rec[1]) + kSelTile - 1) / kSelTile + 1;
+    cap.leaves = leaves;
+    cap.bytes = 8 * (cap.vox[0] + cap.vox[1]) +
+                (cap.rec[0] + cap.rec[1]) * (sizeof(Region) + sizeof(PassRegion) + 4 * sizeof(uint32_t)) +
+                cap.cursors * sizeof(unsigned long long) + cap.tiles * (4 + 2 * 3 * sizeof(uint64_t)) +
+                (w.leaf_base + leaves) * sizeof(DevLeaf) + 64 * w.total;
+    return true;
+}
+
+// Allocate the graph form's buffers; false when they do not fit the budget
+// (the wave then runs level by level).
+bool size_graph_buffers(hht_ctx* c, const Wave& w, GraphCaps& cap) {
+    if (!graph_caps(w, cap)) return false;
+    uint64_t budget = c->budget;
+    if (!budget) {
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        budget = (uint64_t)((double)(fr + c->held) * 0.8);
+    }
+    if (cap.bytes > budget) return false;
+    for (int k = 0; k < 2; ++k) {
+        if (ensure(c, c->vox[k], cap.vox[k] * sizeof(Voter)) != HHT_OK) return false;
+        if (ensure(c, c->rec[k], cap.rec[k] * sizeof(Region)) != HHT_OK) return false;
+        if (ensure(c, c->preg[k], cap.rec[k] * sizeof(PassRegion)) != HHT_OK) return false;
+        if (ensure(c, c->cnt[k], cap.rec[k] * 4 * sizeof(uint32_t)) != HHT_OK) return false;
+    }
+    if (ensure(c, c->cursors, cap.cursors * sizeof(unsigned long long)) != HHT_OK) return false;
+    if (cap.tiles * 4 > c->sel_flags.bytes && ensure(c, c->sel_flags, cap.tiles * 4, true) != HHT_OK) return false;
+    if (ensure(c, c->sel_data, cap.tiles * 2 * 3 * sizeof(uint64_t)) != HHT_OK) return false;
+    if (ensure_keep(c, c->leaves, std::max<uint64_t>(w.leaf_base + cap.leaves, 1) * sizeof(DevLeaf),
+                    w.leaf_base * sizeof(DevLeaf)) != HHT_OK)
+        return false;
+    // the kernels are told the room the buffers have (at least the bounds):
+    // a later job that fits the same buffers then replays the same graph
+    const uint64_t cur = c->cursors.bytes / sizeof(unsigned long long);
+    for (int k = 0; k < 2; ++k) {
+        cap.vox[k] = c->vox[k].bytes / sizeof(Voter);
+        cap.rec[k] = std::min({c->rec[k].bytes / sizeof(Region), c->preg[k].bytes / sizeof(PassRegion),
+                               c->cnt[k].bytes / (4 * sizeof(uint32_t)), cur, (uint64_t)kMaxLevelRecords});
+    }
+    cap.tiles = std::min<uint64_t>(c->sel_flags.bytes / 4, c->sel_data.bytes / (2 * 3 * sizeof(uint64_t)));
+    return true;
+}
+
+// Launch the graph form's kernels on the context's stream: the stage kernel
+// (sizes from the JobDims in device memory), then for every level the
+// selection and the pass, all with fixed arguments; every kernel reads the
+// sizes of its level from the level totals that the previous selection wrote.
+// With `evs`, a pair of events (recorded as graph nodes when capturing)
+// brackets every kernel for hht_profile_*.
+int launch_graph_kernels(hht_ctx* c, const Wave& w, const GraphCaps& cap, cudaStream_t st, bool capturing,
+                         std::vector<hht_ctx::GraphEvent>* evs) {
+    const int shape = w.i64 ? 0 : c->pass_shape;
+    const int occ = w.i64 ? c->occ_pass64 : c->occ_shape[shape];
+    auto record = [&]() -> cudaEvent_t {
+        cudaEvent_t e = take_event(c);
+        if (capturing) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+        else cudaEventRecord(e, st);
+        return e;
+    };
+    cudaEvent_t e0 = nullptr;
+    auto open = [&]() { e0 = evs ? record() : nullptr; };
+    auto close = [&](int kind) {
+        if (evs) evs->push_back({e0, record(), kind});
+    };
+    open();
+    if (launch_stage((const int16_t*)c->pts.p, w.total, (const Unit*)c->units.p, w.count,
+                     (const uint64_t*)c->img_start.p, (const uint32_t*)c->img_unit.p, (Voter*)c->vox[0].p,
+                     (uint32_t*)c->cnt[0].p, (uint64_t*)c->stats.p, (uint32_t*)c->img_err.p,
+                     (DeviceStatus*)c->status.p, w.i64, st, false, (const JobDims*)c->dims.p,
+                     c->num_sms * 8) != 0)
+        return HHT_E_CUDA;
+    close(0);
+    for (int s = 1; s <= w.Dmax; ++s) {
+        const int pi = (s - 1) & 1, ci = s & 1;
+        LevelArgs a = level_args(c, s);
+        a.cap_children = cap.rec[ci];
+        a.cap_leaves = c->leaves.bytes / sizeof(DevLeaf);
+        a.cap_tiles = cap.tiles;
+        a.cap_voters = cap.vox[ci];
+        a.vin = (const Voter*)c->vox[pi].p;
+        a.vout = (Voter*)c->vox[ci].p;
+        open();
+        if (launch_select(a, 256, c->num_sms * c->occ_select, st) != 0) return HHT_E_CUDA;
+        close(1);
+        if (s == w.Dmax) break;
+        open();
+        if (launch_pass(a, w.i64, c->num_sms * occ, st, shape, false) != 0) return HHT_E_CUDA;
+        close(2);
+    }
+    return HHT_OK;
+}
+
+// The graph form: every kernel of the wave's level loop in one CUDA graph,
+// captured once per argument set and replayed, so that a job is one graph
+// launch and one host synchronisation.  On the legacy default stream, where
+// capture is impossible, or if capture failed once, the same kernels are
+// launched directly (still with no host synchronisation between levels).
+// Event pairs captured into the graph stay with it; those of a direct launch
+// go back to the pool once read.
+int run_graph(hht_ctx* c, const Wave& w, const GraphCaps& cap, uint64_t* leaf_total, uint32_t* err) {
+    // The legacy default stream cannot be captured: the graph then runs on the
+    // context's own blocking stream, which the legacy stream orders against in
+    // both directions (its earlier work runs first, its later work waits).
+    if (!c->stream && !c->own_stream) {
+        if (cudaStreamCreate(&c->own_stream) != cudaSuccess) {
+            cudaGetLastError();
+            c->own_stream = nullptr;
+        }
+    }
+    cudaStream_t st = c->stream ? c->stream : c->own_stream;
+    const bool events = c->profile;
+    // everything the captured kernels take as arguments
+    std::vector<unsigned char> key;
+    auto put = [&](const void* p, size_t n) {
+        const unsigned char* b = (const unsigned char*)p;
+        key.insert(key.end(), b, b + n);
+    };
+    const void* ptrs[] = {c->pts.p,  c->units.p, c->img_start.p, c->img_unit.p, c->img_err.p, c->stats.p,
+                          c->infos.p, c->status.p, c->leaf_total.p, c->dims.p, c->rec[0].p, c->rec[1].p,
+                          c->preg[0].p, c->preg[1].p, c->cnt[0].p, c->cnt[1].p, c->vox[0].p, c->vox[1].p,
+                          c->cursors.p, c->leaves.p, c->sel_flags.p, c->sel_data.p, c->scan_states.p, (void*)st};
+    put(ptrs, sizeof ptrs);
+    const int64_t vals[] = {w.Dmax, w.i64, c->pass_shape, events, c->num_sms, c->inject_tile,
+                            (int64_t)(c->leaves.bytes / sizeof(DevLeaf)), (int64_t)cap.tiles,
+                            (int64_t)cap.vox[0], (int64_t)cap.vox[1], (int64_t)cap.rec[0], (int64_t)cap.rec[1]};
+    put(vals, sizeof vals);
+    auto release = [&](hht_ctx::CachedGraph& cg) {
+        for (auto& ev : cg.events) {
+            c->ev_pool.push_back(ev.a);
+            c->ev_pool.push_back(ev.b);
+        }
+        cg.events.clear();
+        if (cg.exec) cudaGraphExecDestroy(cg.exec);
+        cg.exec = nullptr;
+    };
+
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const bool can_capture = st != nullptr && !c->graph_capture_failed &&
+                             cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
+    const hht_ctx::CachedGraph* use = nullptr;
+    if (can_capture) {
+        size_t hit = c->graphs.size();
+        for (size_t k = 0; k < c->graphs.size(); ++k)
+            if (c->graphs[k].key == key) hit = k;
+        if (hit < c->graphs.size()) {
+            std::rotate(c->graphs.begin(), c->graphs.begin() + hit, c->graphs.begin() + hit + 1);
+        } else {
+            hht_ctx::CachedGraph cg;
+            cg.key = key;
+            cudaGraph_t g = nullptr;
+            bool ok = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                const int lr = launch_graph_kernels(c, w, cap, st, true, events ? &cg.events : nullptr);
+                ok = cudaStreamEndCapture(st, &g) == cudaSuccess && lr == HHT_OK && g != nullptr;
+            }
+            if (ok) ok = cudaGraphInstantiate(&cg.exec, g, 0) == cudaSuccess;
+            if (g) cudaGraphDestroy(g);
+            if (ok) {
+                c->prof.graph_captures += 1;
+                if (c->graphs.size() >= hht_ctx::kGraphCache) {
+                    release(c->graphs.back());
+                    c->graphs.pop_back();
+                }
+                c->graphs.insert(c->graphs.begin(), std::move(cg));
+            } else {
+                cudaGetLastError();
+                release(cg);
+                c->graph_capture_failed = true;  // launch directly from now on
+            }
+        }
+        if (!c->graphs.empty() && c->graphs.front().key == key) use = &c->graphs.front();
+    }
+    std::vector<hht_ctx::GraphEvent> direct;
+    const bool graph = use != nullptr;
+    if (graph) {
+        TraceRange tr_k("level loop (graph)");
+        CK(cudaGraphLaunch(use->exec, st));
+    } else {
+        TraceRange tr_k("level loop (direct launches)");
+        RK(launch_graph_kernels(c, w, cap, st, false, events ? &direct : nullptr));
+    }
+    // one read-back of the level totals, the statistics, the image errors,
+    // the leaf count and the status (on the graph's stream)
     DeviceStatus hs{};
-    CK(cudaMemcpyAsync(&hs, d_status, sizeof hs, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(c->h_infos.data(), c->infos.p, (w.Dmax + 1) * sizeof(LevelInfo), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(c->h_stats.data(), c->stats.p, w.stats_words * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    c->h_img_err.assign(w.count, 0);
+    CK(cudaMemcpyAsync(c->h_img_err.data(), c->img_err.p, w.count * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(leaf_total, c->leaf_total.p, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&hs, c->status.p, sizeof hs, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    err |= hs.err;
-    if (persistent && (err & kErrOverflow)) {
-        // the plan's capacities were too small for this data: level by level instead
-        c->plan.valid = false;
-        c->persistent_fallbacks += 1;
-        c->prof.persistent_fallbacks += 1;
-        return kPersistentRetry;
+    *err = hs.err;
+    if (events) {
+        for (const auto& ev : graph ? use->events : direct) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev.a, ev.b) != cudaSuccess) {
+                cudaGetLastError();
+                ms = 0.f;
+            }
+            switch (ev.kind) {
+                case 0: c->prof.stage_ms += ms; break;
+                case 1: c->prof.select_ms += ms; break;
+                default: c->prof.pass_ms += ms; break;
+            }
+        }
+        for (auto& ev : direct) {
+            c->ev_pool.push_back(ev.a);
+            c->ev_pool.push_back(ev.b);
+        }
+    }
+    c->prof.graph_launches += graph ? 1 : 0;
+    c->prof.launches += (uint64_t)(2 * w.Dmax);  // stage, Dmax selections, Dmax - 1 passes
+    c->prof.select_launches += (uint64_t)w.Dmax;
+    for (int s = 1; s < w.Dmax; ++s) {
+        const uint64_t nin = c->h_infos[s - 1].n_voters, nout = c->h_infos[s].n_voters;
+        c->prof.pass_launches += 1;
+        c->prof.voters_read += nin;
+        c->prof.voters_written += nout;
+        c->prof.pass_bytes += 8 * (nin + nout);
+    }
+    if (c->debug)
+        for (int s = 1; s <= w.Dmax; ++s)
+            fprintf(stderr, "[hht]   graph step %d: regions %llu, voters %llu, leaves %llu\n", s,
+                    (unsigned long long)c->h_infos[s].n_regions, (unsigned long long)c->h_infos[s].n_voters,
+                    (unsigned long long)c->h_infos[s].n_leaves);
+    return HHT_OK;
+}
+
+// Statistics, per-image leaf offsets and the copy of each image's leaves into
+// its result (both forms).  `synced`: the statistics, image errors and status
+// have been read back already (the graph form reads them with its totals).
+int finish_wave(hht_ctx* c, const hht_image* im, const Wave& w, hht_result* outs, int job_first,
+                uint64_t leaf_total, uint32_t err, bool synced) {
+    cudaStream_t st = c->stream;
+    const int count = w.count;
+    if (!synced) {
+        CK(cudaMemcpyAsync(c->h_stats.data(), c->stats.p, w.stats_words * sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                           st));
+        c->h_img_err.assign(count, 0);
+        CK(cudaMemcpyAsync(c->h_img_err.data(), c->img_err.p, count * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        DeviceStatus hs{};
+        CK(cudaMemcpyAsync(&hs, c->status.p, sizeof hs, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        err |= hs.err;
     }
     if (err & kErrTimeout) return HHT_E_TIMEOUT;
     if (err & kErrOverflow) return HHT_E_NOMEM;
@@ -589,15 +769,6 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
     if (err & kErrBounds) {
         if (c->debug) fprintf(stderr, "[hht] a kernel met an out-of-range index (checked build)\n");
         return HHT_E_CUDA;
-    }
-    if (!persistent) {
-        // capacities for the persistent form of the same job, with a margin
-        c->plan.sig = sig;
-        c->plan.cap_rec = plan_rec + plan_rec / 8 + 64;
-        c->plan.cap_vox = plan_vox + plan_vox / 8 + 64;
-        const uint64_t wl = leaf_total - wave_leaf_base;
-        c->plan.cap_leaves = wl + wl / 8 + 64;
-        c->plan.valid = true;
     }
 
     // Leaves need no sort: a step emits the leaves of the units whose depth it
@@ -614,7 +785,7 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
         std::vector<int> order(count);
         for (int g = 0; g < count; ++g) order[g] = g;
         std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return im[x].depth < im[y].depth; });
-        uint64_t acc = wave_leaf_base;
+        uint64_t acc = w.leaf_base;
         for (int g : order) {
             img_off[g] = acc;
             acc += img_leaves[g];
@@ -659,6 +830,41 @@ int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int j
     return HHT_OK;
 }
 
+// Run one wave of images through the level loop; fills outs[k] for k in
+// [0, count).  Returns HHT_OK or a job-level error (per-image errors are in
+// outs[k].status).  The graph form runs when the context asks for it, the
+// wave's upper bounds fit the memory budget and the job is of the exact
+// test without a subtree keep mask; the level form otherwise.
+int run_wave(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int job_first) {
+    Wave w;
+    describe_wave(c, im, count, job_first, w);
+    if (w.fht && w.i64) return HHT_E_ARG;  // checked by the entry points before any device work
+    GraphCaps cap;
+    const bool graph = c->batch_mode == HHT_BATCH_GRAPH && !w.fht && !c->job_keep && size_graph_buffers(c, w, cap);
+    if (graph && c->inject_graph_cap >= 0) {
+        // hht_inject_fault: the kernels are told of less room than the buffer has
+        cap.vox[1] = std::min<uint64_t>(cap.vox[1], (uint64_t)c->inject_graph_cap);
+        c->inject_graph_cap = -1;
+    }
+    RK(upload_wave(c, im, w));
+    uint64_t leaf_total = w.leaf_base;
+    uint32_t err = 0;
+    if (graph) {
+        RK(run_graph(c, w, cap, &leaf_total, &err));
+        if (!(err & kErrOverflow)) return finish_wave(c, im, w, outs, job_first, leaf_total, err, true);
+        // the bounds hold for every input, so this is a defect; the wave is
+        // still answered, level by level with exact sizes
+        c->prof.graph_fallbacks += 1;
+        if (c->debug) fprintf(stderr, "[hht] graph form ran out of room; rerun level by level\n");
+        c->job_leaves = w.leaf_base;
+        RK(upload_wave(c, im, w));
+        err = 0;
+    }
+    RK(run_levels(c, w, &leaf_total, &err));
+    return finish_wave(c, im, w, outs, job_first, leaf_total, err, false);
+}
+
+
 // Upper estimate of a wave member's peak device bytes (two voter streams of
 // the two deepest written levels, both halves, dense regime).
 uint64_t estimate_bytes(const hht_image& im, bool fht) {
@@ -696,10 +902,6 @@ int run_waves(hht_ctx* c, const hht_image* im, int count, hht_result* outs, int 
                     budget / 1e9);
         const uint64_t leaves_before = c->job_leaves;
         int rc = run_wave(c, im + first, last - first, outs + first, job_first + first);
-        if (rc == kPersistentRetry) {
-            c->job_leaves = leaves_before;
-            rc = run_wave(c, im + first, last - first, outs + first, job_first + first);
-        }
         if (rc == HHT_E_NOMEM && last - first > 1) {
             // remember that this much did not fit, split the wave and retry each half
             c->wave_cap = acc / 2 > 0 ? acc / 2 : 1;
@@ -770,9 +972,7 @@ int hht_create_with_allocator(hht_ctx** out, int device, void* cuda_stream, uint
     c->occ_pass64 = occupancy_pass(true);
     for (int k = 0; k < kPassShapeCount; ++k) c->occ_shape[k] = occupancy_pass(false, k);
     c->occ_pass_fht = occupancy_pass_fht();
-    c->occ_persistent32 = occupancy_persistent(false);
-    c->occ_persistent64 = occupancy_persistent(true);
-    if (const char* e = getenv("HHT_BATCH_MODE")) c->batch_mode = atoi(e) == 1 ? 1 : 0;
+    if (const char* e = getenv("HHT_BATCH_MODE")) c->batch_mode = atoi(e) == 0 ? HHT_BATCH_LEVELS : HHT_BATCH_GRAPH;
     c->copy_engine_only = getenv("HHT_COPY_ENGINE") && getenv("HHT_COPY_ENGINE")[0] == '1';
     if (const char* e = getenv("HHT_PASS_SHAPE")) {
         const int k = atoi(e);
@@ -801,14 +1001,25 @@ void hht_destroy(hht_ctx* c) {
     hht::serve_destroy(c->serve);
     resolve_profile(c);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
-    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    for (auto& cg : c->graphs) {
+        if (cg.exec) cudaGraphExecDestroy(cg.exec);
+        for (auto& ev : cg.events) {
+            cudaEventDestroy(ev.a);
+            cudaEventDestroy(ev.b);
+        }
+    }
+    if (c->own_stream) {
+        cudaStreamSynchronize(c->own_stream);
+        cudaStreamDestroy(c->own_stream);
+    }
     DevBuf* all[] = {&c->pts,       &c->img_start,  &c->img_unit, &c->units,        &c->stats,     &c->infos,      &c->status,
                      &c->leaf_total, &c->img_err,   &c->scan_states,  &c->rec[0],    &c->rec[1],     &c->preg[0],
                      &c->preg[1],   &c->cnt[0],     &c->cnt[1],       &c->vox[0],    &c->vox[1],     &c->leaves,
                      &c->sel_flags, &c->sel_data,   &c->cursors,      &c->img_buf,   &c->edge_pts[0],
                      &c->edge_pts[1], &c->edge_tot,   &c->line_keys,    &c->line_vals, &c->line_parent,
                      &c->line_cells, &c->line_sums,  &c->line_out,     &c->keep_buf,  &c->rem_pts,
-                     &c->rem_lists,  &c->rem_bitmap, &c->rem_leaves,   &c->rem_stats, &c->rem_tasks};
+                     &c->rem_lists,  &c->rem_bitmap, &c->rem_leaves,   &c->rem_stats, &c->rem_tasks,
+                     &c->dims};
     for (DevBuf* b : all) release(c, *b);
     delete c;
 }
@@ -878,7 +1089,7 @@ int hht_fetch_all_leaves(hht_ctx* c, hht_leaf* leaves, uint64_t capacity, uint64
 }
 
 int hht_set_batch_mode(hht_ctx* c, int32_t mode) {
-    if (!c || (mode != HHT_BATCH_LEVELS && mode != HHT_BATCH_PERSISTENT)) return HHT_E_ARG;
+    if (!c || (mode != HHT_BATCH_LEVELS && mode != HHT_BATCH_GRAPH)) return HHT_E_ARG;
     std::lock_guard<std::mutex> lk(c->mu);
     c->batch_mode = mode;
     return HHT_OK;
@@ -961,7 +1172,6 @@ int hht_detect_subtrees(hht_ctx* c, const hht_point* points, int64_t n, int32_t 
 int hht_set_predicate(hht_ctx* c, int32_t predicate) {
     if (!c || (predicate != HHT_PREDICATE_EXACT && predicate != HHT_PREDICATE_FHT)) return HHT_E_ARG;
     std::lock_guard<std::mutex> lk(c->mu);
-    if (predicate != c->predicate) c->plan.valid = false;  // the persistent form's size plan was for the other test
     c->predicate = predicate;
     return HHT_OK;
 }
@@ -972,6 +1182,11 @@ int hht_inject_fault(hht_ctx* c, int32_t kind, int64_t arg) {
     switch (kind) {
         case HHT_FAULT_NONE:
             c->inject_tile = -1;
+            c->inject_graph_cap = -1;
+            return HHT_OK;
+        case HHT_FAULT_GRAPH_CAPACITY:
+            if (arg < 0 || arg >= (int64_t)UINT32_MAX) return HHT_E_ARG;
+            c->inject_graph_cap = arg;
             return HHT_OK;
         case HHT_FAULT_WITHHOLD_SCAN_TILE:
             if (arg < 0 || arg >= (int64_t)UINT32_MAX) return HHT_E_ARG;

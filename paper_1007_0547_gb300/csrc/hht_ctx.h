@@ -40,22 +40,28 @@ struct hht_ctx {
     int num_sms = 0;
     int occ_select = 1, occ_pass32 = 1, occ_pass64 = 1;
     int pass_shape = 0;                                   // pass-kernel tile shape (autotuned)
-    int batch_mode = 0;                                   // 0: level by level; 1: persistent when planned
-    int occ_persistent32 = 0, occ_persistent64 = 0;
-    // sizes seen by the last level-by-level run of a wave, for the persistent form
-    struct Plan {
-        uint64_t sig = 0;
-        uint64_t cap_rec = 0, cap_vox = 0, cap_leaves = 0;
-        bool valid = false;
-    } plan;
-    uint64_t persistent_runs = 0, persistent_fallbacks = 0;
-    // CUDA graph of the persistent launch, replayed while its arguments are unchanged
-    cudaGraphExec_t graph_exec = nullptr;
-    std::vector<unsigned char> graph_args;
-    int graph_grid = 0;
+    int batch_mode = HHT_BATCH_GRAPH;                     // HHT_BATCH_GRAPH or HHT_BATCH_LEVELS
+    // CUDA graphs of the device-driven level loop (stage, then select and pass
+    // per level, sizes read on the device), each replayed while its arguments
+    // are unchanged; with profiling on, event records around its kernels.
+    // The most recently used come first; at most kGraphCache are kept.
+    struct GraphEvent {
+        cudaEvent_t a, b;
+        int kind;  // as Pending::kind
+    };
+    struct CachedGraph {
+        std::vector<unsigned char> key;
+        cudaGraphExec_t exec = nullptr;
+        std::vector<GraphEvent> events;
+    };
+    static constexpr size_t kGraphCache = 8;
+    std::vector<CachedGraph> graphs;
     bool graph_capture_failed = false;
+    cudaStream_t own_stream = nullptr;  // the graph's stream when the context's stream is the legacy default
+    DevBuf dims;  // JobDims of the job in flight (read by the graph's stage kernel)
     int occ_shape[hht::kPassShapeCount] = {1, 1, 1, 1, 1, 1};  // resident blocks per SM of each shape
     int64_t inject_tile = -1;  // hht_inject_fault: selection tile withheld in the next job (-1 = none)
+    int64_t inject_graph_cap = -1;  // hht_inject_fault: level-1 stream capacity told to the next graph job
     int predicate = 0;         // HHT_PREDICATE_EXACT or HHT_PREDICATE_FHT (hht_detect / hht_detect_batch)
     const uint8_t* job_halves = nullptr;  // during a job: per image, bit h set when half h takes its points
     const uint8_t* job_keep = nullptr;    // during a job: device keep mask of subtree sharding (or NULL)
@@ -81,6 +87,8 @@ struct hht_ctx {
     // host staging
     std::vector<uint64_t> h_stats;
     std::vector<hht::LevelInfo> h_infos;
+    std::vector<hht::Region> h_roots;
+    hht::JobDims h_dims{};
     std::vector<uint32_t> h_img_err;
 
     hht::ServeState* serve = nullptr;

@@ -165,32 +165,24 @@ struct LevelArgs {
     int32_t keep_level;
 };
 
-// Arguments of the persistent (one cooperative launch) form of a batch.
-struct PersistentArgs {
-    LevelArgs base;  // fields common to every level (units, stats, status, scan, cursor, leaves, capacities)
-    Region* rec[2];
-    PassRegion* preg[2];
-    uint32_t* cnt[2];
-    Voter* vox[2];
-    LevelInfo* infos;  // [Dmax + 1]
-    const int16_t* pts;
-    uint64_t total_pts;
-    const uint64_t* img_start;
-    const uint32_t* img_unit;
-    uint32_t* img_err;
+// Sizes of a job that the stage kernel reads from device memory when it is
+// launched from a CUDA graph replayed for many jobs (the graph's arguments
+// stay fixed; the host writes these before each launch).
+struct alignas(16) JobDims {
+    uint64_t total_points;  // points of all images
     int32_t n_images;
-    int32_t Dmax;
+    int32_t pad;
 };
 
 // Kernel launchers (hht_kernels.cu).  All are asynchronous on `stream`.
-int launch_persistent(const PersistentArgs& f, bool int64_path, int grid, void* stream);
-int occupancy_persistent(bool int64_path);
 // Level 0 of the images [0, n_images) of `pts` (image g owns points
 // [img_start[g], img_start[g+1]) and the units img_unit[g], img_unit[g] + 1).
+// With `dims` the kernel reads total_points and n_images from device memory
+// instead, and `grid` (> 0) fixes the grid (for a CUDA graph reused across jobs).
 int launch_stage(const int16_t* pts, uint64_t total_points, const Unit* units, int n_images,
                  const uint64_t* img_start, const uint32_t* img_unit, Voter* vstream, uint32_t* cnt,
                  uint64_t* stats, uint32_t* img_err, DeviceStatus* status, bool int64_path, void* stream,
-                 bool fht = false);
+                 bool fht = false, const JobDims* dims = nullptr, int grid = 0);
 int launch_select(const LevelArgs& a, int threads_per_block, int grid, void* stream);
 // Copy n16 16-byte words from device memory to `dst` (device memory, or the
 // device mapping of pinned host memory).

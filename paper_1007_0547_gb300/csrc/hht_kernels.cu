@@ -14,7 +14,6 @@
 //           counts) into the level-s stream, and grandchild votes are counted
 //           for the next selection.  The copy is skipped where the next level
 //           is the unit's last one, so the largest list is never written.
-#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -84,7 +83,12 @@ __device__ __forceinline__ void stage_body(const int16_t* __restrict__ pts, uint
                                            const uint64_t* __restrict__ img_start,
                                            const uint32_t* __restrict__ img_unit, Voter* __restrict__ v0,
                                            uint32_t* __restrict__ root_cnt, uint64_t* __restrict__ stats,
-                                           uint32_t* __restrict__ img_err, DeviceStatus* status) {
+                                           uint32_t* __restrict__ img_err, DeviceStatus* status,
+                                           const JobDims* __restrict__ dims) {
+    if (dims) {
+        total = dims->total_points;
+        n_images = dims->n_images;
+    }
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t kb = (uint64_t)blockIdx.x * blockDim.x; kb < total; kb += stride) {
         const uint64_t k = kb + threadIdx.x;
@@ -171,8 +175,10 @@ __global__ void __launch_bounds__(256) stage_kernel(const int16_t* __restrict__ 
                                                     const uint64_t* __restrict__ img_start,
                                                     const uint32_t* __restrict__ img_unit, Voter* __restrict__ v0,
                                                     uint32_t* __restrict__ root_cnt, uint64_t* __restrict__ stats,
-                                                    uint32_t* __restrict__ img_err, DeviceStatus* status) {
-    stage_body<I, FHT>(pts, total, units, n_images, img_start, img_unit, v0, root_cnt, stats, img_err, status);
+                                                    uint32_t* __restrict__ img_err, DeviceStatus* status,
+                                                    const JobDims* __restrict__ dims) {
+    stage_body<I, FHT>(pts, total, units, n_images, img_start, img_unit, v0, root_cnt, stats, img_err, status,
+                       dims);
 }
 
 // ============================================================================ select
@@ -886,49 +892,6 @@ __global__ void __launch_bounds__(TPB, MINB) pass_kernel(LevelArgs a) {
 }
 
 
-// ============================================================================ persistent form
-// The whole level loop of a batch in one cooperative launch: level 0, then
-// for every level the selection and the pass, separated by grid-wide
-// barriers.  Buffers have fixed capacities (from an
-// earlier run of the same job); a capacity overflow is flagged, every later
-// phase is skipped and the host runs the job level by level instead.
-template <typename I>
-__global__ void __launch_bounds__(256, 4) persistent_kernel(PersistentArgs f) {
-    namespace cg = cooperative_groups;
-    cg::grid_group grid = cg::this_grid();
-    stage_body<I>(f.pts, f.total_pts, f.base.units, f.n_images, f.img_start, f.img_unit, f.vox[0], f.cnt[0],
-                  f.base.stats, f.img_err, f.base.status);
-    grid.sync();
-    for (int s = 1; s <= f.Dmax; ++s) {
-        const int pi = (s - 1) & 1, ci = s & 1;
-        LevelArgs a = f.base;
-        a.parents = f.rec[pi];
-        a.pregions = f.preg[pi];
-        a.parent_cnt = f.cnt[pi];
-        a.children = f.rec[ci];
-        a.child_cnt = f.cnt[ci];
-        a.vin = f.vox[pi];
-        a.vout = f.vox[ci];
-        a.info_prev = f.infos + (s - 1);
-        a.info = f.infos + s;
-        a.level = s;
-        select_body(a, false);
-        grid.sync();
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            select_totals(a);
-            // the scan state for the next selection
-            a.scan->tile_counter = 0;
-            a.scan->done_counter = 0;
-            a.scan->epoch = a.scan->epoch + 1u;
-            __threadfence();
-        }
-        grid.sync();
-        if (s < f.Dmax) pass_body<I, 4, 256>(a);
-        grid.sync();
-    }
-}
-
-
 // ============================================================================ launchers
 int occupancy_select() {
     int per_sm = 0;
@@ -939,21 +902,23 @@ int occupancy_select() {
 int launch_stage(const int16_t* pts, uint64_t total_points, const Unit* units, int n_images,
                  const uint64_t* img_start, const uint32_t* img_unit, Voter* v0, uint32_t* root_cnt,
                  uint64_t* stats, uint32_t* img_err, DeviceStatus* status, bool int64_path, void* stream,
-                 bool fht) {
-    if (total_points == 0) return 0;
+                 bool fht, const JobDims* dims, int grid) {
+    if (total_points == 0 && !dims) return 0;
     cudaStream_t st = (cudaStream_t)stream;
-    const uint64_t want = (total_points + 255) / 256;
-    const int grid = (int)(want < 4096 ? want : 4096);
+    if (grid <= 0) {
+        const uint64_t want = (total_points + 255) / 256;
+        grid = (int)(want < 4096 ? want : 4096);
+    }
     if (fht) {
         if (int64_path) return -1;  // the circle test is built for int32 corner arithmetic only
         stage_kernel<int32_t, true><<<grid, 256, 0, st>>>(pts, total_points, units, n_images, img_start, img_unit,
-                                                          v0, root_cnt, stats, img_err, status);
+                                                          v0, root_cnt, stats, img_err, status, dims);
     } else if (int64_path)
         stage_kernel<int64_t><<<grid, 256, 0, st>>>(pts, total_points, units, n_images, img_start, img_unit, v0,
-                                                     root_cnt, stats, img_err, status);
+                                                     root_cnt, stats, img_err, status, dims);
     else
         stage_kernel<int32_t><<<grid, 256, 0, st>>>(pts, total_points, units, n_images, img_start, img_unit, v0,
-                                                     root_cnt, stats, img_err, status);
+                                                     root_cnt, stats, img_err, status, dims);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -1013,23 +978,6 @@ const void* pass_fn(bool int64_path, int shape, bool fht = false) {
     }
 }
 }  // namespace
-
-int occupancy_persistent(bool int64_path) {
-    int per_sm = 0;
-    if (int64_path)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel<int64_t>, 256, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel<int32_t>, 256, 0);
-    return per_sm;
-}
-
-int launch_persistent(const PersistentArgs& f, bool int64_path, int grid, void* stream) {
-    void* args[] = {(void*)&f};
-    const void* fn = int64_path ? (const void*)persistent_kernel<int64_t> : (const void*)persistent_kernel<int32_t>;
-    const cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(256), args, 0, (cudaStream_t)stream);
-    if (e != cudaSuccess) cudaGetLastError();
-    return e == cudaSuccess ? 0 : -1;
-}
 
 int pass_threads(bool int64_path, int shape) {
     return int64_path ? 256 : kPassShapes[(shape >= 0 && shape < kPassShapeCount) ? shape : 0].tpb;

@@ -36,8 +36,9 @@ EXPORTS = ("hht_create", "hht_destroy", "hht_detect", "hht_detect_batch", "hht_f
            "hht_inject_fault", "hht_set_predicate", "hht_edges", "hht_detect_image", "hht_lines",
            "hht_detect_subtrees", "hht_detect_removal", "hht_detect_removal_batch",
            "hht_create_with_allocator", "hht_done_tickets")
-BATCH_LEVELS, BATCH_PERSISTENT = 0, 1
-FAULT_NONE, FAULT_WITHHOLD_SCAN_TILE = 0, 1
+BATCH_LEVELS, BATCH_GRAPH = 0, 1
+BATCH_PERSISTENT = BATCH_GRAPH  # earlier name
+FAULT_NONE, FAULT_WITHHOLD_SCAN_TILE, FAULT_GRAPH_CAPACITY = 0, 1, 2
 PREDICATE_EXACT, PREDICATE_FHT = 0, 1
 TUNE_SHAPES = 6
 
@@ -59,9 +60,10 @@ class _Profile(ctypes.Structure):
                 ("select_launches", ctypes.c_uint64), ("voters_read", ctypes.c_uint64),
                 ("voters_written", ctypes.c_uint64), ("pass_bytes", ctypes.c_uint64), ("pass_ms", ctypes.c_double),
                 ("select_ms", ctypes.c_double), ("stage_ms", ctypes.c_double),
-                ("persistent_launches", ctypes.c_uint64), ("persistent_fallbacks", ctypes.c_uint64),
+                ("graph_launches", ctypes.c_uint64), ("graph_fallbacks", ctypes.c_uint64),
                 ("edges_launches", ctypes.c_uint64), ("edges_pixels", ctypes.c_uint64),
-                ("edges_points", ctypes.c_uint64), ("edges_ms", ctypes.c_double)]
+                ("edges_points", ctypes.c_uint64), ("edges_ms", ctypes.c_double),
+                ("graph_captures", ctypes.c_uint64)]
 
 
 class _Line(ctypes.Structure):
@@ -427,8 +429,10 @@ class Context:
         return res
 
     def set_batch_mode(self, mode: int) -> None:
-        """BATCH_LEVELS (one launch per level) or BATCH_PERSISTENT (one
-        cooperative launch per batch once the batch has been run once)."""
+        """BATCH_GRAPH (default: the device-driven level loop, one CUDA-graph
+        launch and one host synchronisation per job, buffers sized from upper
+        bounds) or BATCH_LEVELS (one selection and one level-kernel launch per
+        level with a host synchronisation each, buffers sized exactly)."""
         rc = load().hht_set_batch_mode(self._h, int(mode))
         if rc != HHT_OK:
             raise HhtError(rc, "hht_set_batch_mode")

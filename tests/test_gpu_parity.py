@@ -417,50 +417,86 @@ def test_autotune_picks_a_shape_and_caches_it(hht, tmp_path):
     c.close()
 
 
-def test_persistent_form_matches_and_falls_back(hht):
-    """Batch mode PERSISTENT: the first run of a job goes level by level and
-    records its sizes; the same job then runs as one cooperative launch; a job
-    with the same signature but more voters overflows the recorded room and is
-    rerun level by level.  Every result equals the oracle's."""
+def test_graph_form_first_call_is_one_graph_launch_and_later_jobs_replay_it(hht):
+    """The default form: a fresh batch runs as one CUDA-graph launch on its
+    first call (buffers sized from upper bounds, no earlier run of the job),
+    and a later batch of other images with the same deepest level and buffers
+    replays the captured graph.  Every result equals the oracle's."""
     c = hht.Context(device=0)
-    c.set_batch_mode(hht.BATCH_PERSISTENT)
-    imgs = [synth.plain_128(index=k) for k in range(3)] + [synth.batch_image(0), synth.plain_1024()]
+    try:
+        c.profile(True)
+        first = [synth.plain_128(index=k) for k in range(3)] + [synth.batch_image(0), synth.plain_1024()]
+        got = c.detect_batch([(im.points, im.W, im.H, im.depth, im.T) for im in first])
+        for r, im in zip(got, first):
+            _same(r, oracle.detect(im.points, im.W, im.H, im.depth, im.T))
+        p = c.profile_read()
+        assert p["graph_launches"] == 1 and p["graph_captures"] == 1 and p["graph_fallbacks"] == 0, p
+        # other images whose bounds are no larger, with the same deepest level
+        # (10): the buffers hold them, so the graph is replayed
+        big = first[-1]
+        later = [(synth.plain_128(index=5).points, 128, 128, 7, 20), (big.points, big.W, big.H, big.depth, 200),
+                 (synth.plain_128(index=6).points, 128, 128, 6, 9)]
+        for _ in range(2):
+            got = c.detect_batch(later)
+            for r, x in zip(got, later):
+                _same(r, oracle.detect(*x))
+        p = c.profile_read()
+        assert p["graph_launches"] == 3 and p["graph_captures"] == 1 and p["graph_fallbacks"] == 0, p
+    finally:
+        c.close()
+
+
+def test_graph_and_level_forms_agree(hht):
+    """The graph form and the level form (one launch per level, exact sizes)
+    give the same leaves and statistics, single images and batches."""
+    imgs = [synth.batch_image(k) for k in (2, 9)] + [synth.plain_128(index=7),
+                                                    synth.random_small(444, max_side=200, max_n=700,
+                                                                       max_depth=8, max_T=4)]
     batch = [(im.points, im.W, im.H, im.depth, im.T) for im in imgs]
-    want = [oracle.detect(im.points, im.W, im.H, im.depth, im.T) for im in imgs]
-    c.profile(True)
-    for _ in range(3):
-        got = c.detect_batch(batch)
-        for r, w in zip(got, want):
-            _same(r, w)
-    p = c.profile_read()
-    assert p["persistent_launches"] == 2 and p["persistent_fallbacks"] == 0
-    # same signature (n, W, H, depth, T), more voters: n identical points are
-    # one line (n * 2^l voters at level l); a fan of lines through one point
-    # crosses about 1.25 * 2^l cells each, beyond the plan's margin
-    n = imgs[0].n
-    line = np.stack([np.arange(n) % 128, np.full(n, 64)], axis=1).astype(np.int16)
-    sparse = np.zeros((n, 2), np.int16)
-    c2 = hht.Context(device=0)
-    c2.set_batch_mode(hht.BATCH_PERSISTENT)
-    c2.profile(True)
-    r1 = c2.detect_batch([(sparse, 128, 128, 7, 3)])[0]
-    r2 = c2.detect_batch([(line, 128, 128, 7, 3)])[0]
-    _same(r1, oracle.detect(sparse, 128, 128, 7, 3))
-    _same(r2, oracle.detect(line, 128, 128, 7, 3))
-    p2 = c2.profile_read()
-    assert p2["persistent_launches"] == 1 and p2["persistent_fallbacks"] == 1
-    c.close()
-    c2.close()
+    g = hht.Context(device=0)
+    lv = hht.Context(device=0)
+    try:
+        lv.set_batch_mode(hht.BATCH_LEVELS)
+        for a, b in zip(g.detect_batch(batch), lv.detect_batch(batch)):
+            assert np.array_equal(a.leaves_numpy(), b.leaves_numpy()) and np.array_equal(a.stats, b.stats)
+        for x in batch:
+            a, b = g.detect(*x), lv.detect(*x)
+            assert np.array_equal(a.leaves_numpy(), b.leaves_numpy()) and np.array_equal(a.stats, b.stats)
+        assert lv.profile_read()["graph_launches"] == 0
+    finally:
+        g.close()
+        lv.close()
 
 
-def test_persistent_form_replays_a_cuda_graph_on_a_stream(hht):
-    """On a non-default stream the persistent launch is captured into a CUDA
-    graph once and replayed; results stay equal to the oracle's."""
+def test_graph_form_overflow_reruns_level_by_level(hht):
+    """Host-side injection tells the graph's kernels that the level-1 stream
+    holds 10 records: the selection reports the overflow, every later kernel
+    of the graph skips its work, and the job is rerun level by level with the
+    oracle's result; the next job runs in the graph form again."""
+    img = synth.plain_128(index=1)
+    want = oracle.detect(img.points, img.W, img.H, img.depth, img.T)
+    c = hht.Context(device=0)
+    try:
+        c.profile(True)
+        c.inject_fault(hht.FAULT_GRAPH_CAPACITY, 10)
+        _same(c.detect(img.points, img.W, img.H, img.depth, img.T), want)
+        p = c.profile_read()
+        assert p["graph_fallbacks"] == 1 and p["graph_launches"] == 1, p
+        _same(c.detect(img.points, img.W, img.H, img.depth, img.T), want)
+        p = c.profile_read()
+        assert p["graph_fallbacks"] == 1 and p["graph_launches"] == 2, p
+    finally:
+        c.close()
+
+
+def test_graph_form_on_a_caller_stream(hht):
+    """On a non-default stream the graph is captured on the caller's stream
+    and replayed; results stay equal to the oracle's."""
     import torch
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
         c = hht.Context(device=0, stream=s)
-        c.set_batch_mode(hht.BATCH_PERSISTENT)
+        c.profile(True)
         imgs = [synth.plain_128(index=k) for k in range(2)] + [synth.batch_image(1)]
         batch = [(torch.from_numpy(im.points).cuda(), im.W, im.H, im.depth, im.T) for im in imgs]
         want = [oracle.detect(im.points, im.W, im.H, im.depth, im.T) for im in imgs]
@@ -469,6 +505,8 @@ def test_persistent_form_replays_a_cuda_graph_on_a_stream(hht):
             s.synchronize()
             for r, w in zip(got, want):
                 _same(r, w)
+        p = c.profile_read()
+        assert p["graph_launches"] == 4 and p["graph_captures"] == 1, p
         c.close()
 
 
