@@ -1233,10 +1233,10 @@ const char* hht_strerror(int code) {
 
 const char* hht_version(void) {
 #ifdef HHT_CHECKED
-    return "hht 0.4 checked (sm_103a; every data-derived index of the level kernel bounds-checked)";
+    return "hht 0.5 checked (sm_103a; every data-derived index of the level kernel bounds-checked)";
 #endif
-    return "hht 0.4 (sm_103a, level-synchronous stage/select/pass; pass tile shapes 4x256/3 2x256/4 3x256/4 4x128/6 "
-           "4x256/4 4x512/2)";
+    return "hht 0.5 (sm_103a, device-driven level loop in one CUDA graph; pass tile shapes 4x256/3 4x128/6 3x256/4 "
+           "4x384/2 4x192/4 3x256/3)";
 }
 
 }  // extern "C"

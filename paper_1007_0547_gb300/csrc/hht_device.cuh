@@ -84,13 +84,8 @@ __device__ __forceinline__ int quad_of(int east, int north) {
     return north ? (east ? NE : NW) : (east ? SE : SW);
 }
 
-// Child votes (bit q = quadrant q) from a 5 x 5 below-mask: children are the
-// 2 x 2 step cells with SW corners NE (2,2), NW (0,2), SW (0,0), SE (2,0).
-__device__ __forceinline__ uint32_t child_votes5(uint32_t M) {
-    const uint32_t v = crossing_cells<5, 2>(M);
-    return ((v >> 12) & 1u) | (((v >> 2) & 1u) << 1) | ((v & 1u) << 2) | (((v >> 10) & 1u) << 3);
-}
-// Same for a 3 x 3 below-mask (children are 1 x 1 step cells).
+// Child votes (bit q = quadrant q) from a 3 x 3 below-mask: children are the
+// 1 x 1 step cells with SW corners NE (1,1), NW (0,1), SW (0,0), SE (1,0).
 __device__ __forceinline__ uint32_t child_votes3(uint32_t M) {
     const uint32_t v = crossing_cells<3, 1>(M);
     return ((v >> 4) & 1u) | (((v >> 1) & 1u) << 1) | ((v & 1u) << 2) | (((v >> 3) & 1u) << 3);
@@ -104,24 +99,17 @@ __device__ __forceinline__ uint32_t region_code3(uint32_t M) {
 
 // ---------------------------------------------------------------- pass-kernel bit layouts
 // The corner-sign mask M of the 5 x 5 quarter-step grid holds vertex
-// (alpha, beta) at bit 5*alpha + beta.  The bit-sliced codes are formed with
-// left shifts (multiplies, which run on the FMA pipe) so that the result for
-// the cell whose SW vertex is p lands on the cell's NE vertex bit p + 6*sz:
-// the NE corner bit is M itself, NW is M << 5*sz, SW is M << 6*sz and SE is
-// M << sz.  A line votes for the cell when its code is neither 0000 nor 1111.
-// Every column of M is a prefix (the vertices below the line are the lowest
-// t of the column), so the code is 1111 exactly when both upper corners are
-// set and 0000 exactly when both lower corners are clear.
-template <int sz>
-__device__ __forceinline__ uint32_t code_votes(uint32_t M) {
-    const uint32_t ne = M, nw = M * (1u << (5 * sz)), sw = M * (1u << (6 * sz)), se = M * (1u << sz);
-    return (sw | se) & ~(nw & ne);
-}
-
-// Children (2 x 2 steps) of quadrant q = NE, NW, SW, SE have SW vertices
-// 12, 2, 0, 10 and so vote at bits 24, 14, 12, 22 of code_votes<2>.
+// (alpha, beta) at bit 5*alpha + beta.  Every column of M is a prefix (the
+// vertices below the line are the lowest t of the column).  G grows with i
+// (x >= 0) and with j, so a cell's SW corner is its lowest and its NE corner
+// its highest: the cell's 4-bit code is neither 0000 nor 1111 exactly when SW
+// is below the line and NE is not.  The pass kernel forms that test for all
+// cells of side sz at once as (M << 6*sz) & ~M, which leaves the result of the
+// cell whose SW vertex is p at bit p + 6*sz, its NE vertex.
+// Children (2 x 2 steps, sz = 2) of quadrant q = NE, NW, SW, SE have SW
+// vertices 12, 2, 0, 10 and so vote at bits 24, 14, 12, 22.
 __host__ __device__ __forceinline__ constexpr int quad_bit(int q) { return q == 0 ? 24 : q == 1 ? 14 : q == 2 ? 12 : 22; }
-// Grandchild (alpha, beta), alpha, beta < 4, votes at bit kGrandBase + 5*alpha + beta of code_votes<1>.
+// Grandchild (alpha, beta), alpha, beta < 4 (sz = 1), votes at bit kGrandBase + 5*alpha + beta.
 constexpr int kGrandBase = 6;
 
 // The four quadrant bits of `q4` (bit q = quadrant q) at quad_bit positions.
@@ -153,31 +141,11 @@ __host__ __device__ __forceinline__ constexpr uint32_t quad_byte_rt(uint32_t q) 
 static_assert(quad_byte_rt(0) == 3 && quad_byte_rt(1) == 1 && quad_byte_rt(2) == 0 && quad_byte_rt(3) == 2,
               "run-time quadrant byte table");
 
-// Grandchild cells (1 x 1 steps of the 5 x 5 grid, bits alpha*5 + beta with
-// alpha, beta < 4) that lie inside the children whose bit is set in `kids`.
-__device__ __forceinline__ uint32_t grandchild_mask(uint32_t kids) {
-    uint32_t m = 0;
-    m |= (kids & (1u << NE)) ? 0x63000u : 0u;  // alpha, beta in {2, 3}
-    m |= (kids & (1u << NW)) ? 0x0018Cu : 0u;  // alpha in {0, 1}, beta in {2, 3}
-    m |= (kids & (1u << SW)) ? 0x00063u : 0u;  // alpha, beta in {0, 1}
-    m |= (kids & (1u << SE)) ? 0x18C00u : 0u;  // alpha in {2, 3}, beta in {0, 1}
-    return m;
-}
-
 // An 8-byte store made only when `pred` is non-zero, as one predicated
 // instruction (a plain `if` around a store may become a branch).
 __device__ __forceinline__ void st_pred_v2(void* p, uint32_t pred, uint32_t x, uint32_t y) {
     asm volatile("{ .reg .pred q; setp.ne.u32 q, %0, 0; @q st.global.v2.u32 [%1], {%2, %3}; }"
                  :: "r"(pred), "l"(p), "r"(x), "r"(y));
-}
-
-// An 8-byte read-only load made only when `pred` is non-zero; otherwise the
-// result is `dflt`.  One predicated instruction, no branch.
-__device__ __forceinline__ uint2 ld_pred_v2(const void* p, uint32_t pred, uint2 dflt) {
-    uint32_t x = dflt.x, y = dflt.y;
-    asm("{ .reg .pred q; setp.ne.u32 q, %2, 0; @q ld.global.nc.v2.u32 {%0, %1}, [%3]; }"
-        : "+r"(x), "+r"(y) : "r"(pred), "l"(p));
-    return make_uint2(x, y);
 }
 
 // Spread 4 bits into the low bit of 4 bytes (bit b -> byte b).

@@ -453,7 +453,8 @@ __device__ __forceinline__ void reduce_rows(const uint32_t (&rows)[4], uint32_t 
 // cells, byte beta.
 __device__ __forceinline__ void add_rows(uint32_t (&rows)[4], uint32_t gv) {
 #pragma unroll
-    for (int al = 0; al < 4; ++al) rows[al] += spread4((gv >> (kGrandBase + 5 * al)) & 0xfu);
+    for (int al = 0; al < 4; ++al)
+        rows[al] += spread4((gv >> (kGrandBase + 5 * al)) & 0xfu);
 }
 
 // Constants of one parent region for the corner grid of its voters.  With
@@ -466,6 +467,11 @@ struct ParentGeo {
     I W0, A, Kc, dmul;
     int k;
     uint32_t pspread, wspread;  // pass / write masks at the children's vote bits
+    uint32_t gmask;             // grandchild cells of the passed children (kGrandBase layout)
+    // int32 form on the packed point word xy = x + 2^16 y, in arithmetic mod
+    // 2^32 (exact, because every true value fits in int32):
+    // u0 = xy*cxy + W0 + y*cy and d = xy*dmul + y*d16
+    uint32_t cxy, cy, d16;
     __device__ __forceinline__ void load(const PassRegion* p, uint32_t r) {
         pr = p[r];
         const int sS = (pr.packed >> 8) & 31, lL = (pr.packed >> 13) & 31, D = (pr.packed >> 18) & 31;
@@ -477,6 +483,10 @@ struct ParentGeo {
         dmul = I(1) << (sS - 1);                                        // 2x * S/4
         pspread = spread_quads(pr.packed & 0xfu);
         wspread = spread_quads((pr.packed >> 4) & 0xfu);
+        gmask = grand_cells(pspread);
+        cxy = (uint32_t)Kc - (uint32_t)A;
+        cy = (uint32_t)Kc - 65536u * cxy;
+        d16 = 0u - ((uint32_t)dmul << 16);
     }
 };
 }  // namespace
@@ -508,29 +518,42 @@ struct Classified {
 // then the 4-bit codes of the four children and the sixteen grandchildren
 // (vote when the code is neither 0000 nor 1111).
 template <typename I>
-__device__ __forceinline__ Classified<I> classify(const ParentGeo<I>& g, uint32_t xy) {
-    const I x = I(xy & 0xffffu), y = I(xy >> 16);
-    const I u0 = g.W0 - x * g.A + (x + y) * g.Kc;
-    const I d = x * g.dmul;
+__device__ __forceinline__ Classified<I> classify(const ParentGeo<I>& g, uint32_t xy, uint32_t live) {
     int t[5];
+    if constexpr (sizeof(I) == 4) {
+        // the integer (ALU) pipe limits this kernel: the point's coordinates
+        // enter as multiply-adds on the packed word (y = xy >> 16 as a high
+        // product), which run on the otherwise idle FMA pipe
+        const uint32_t y = __umulhi(xy, 65536u);
+        const int32_t u0 = (int32_t)(xy * g.cxy + (uint32_t)g.W0 + y * g.cy);
+        const int32_t d = (int32_t)(xy * (uint32_t)g.dmul + y * g.d16);
 #pragma unroll
-    for (int alpha = 0; alpha < 5; ++alpha) {
-        const I w = u0 - I(alpha) * d;
-        if constexpr (sizeof(I) == 4) {
-            t[alpha] = __vimin_s32_relu((int)(w >> g.k), 5);
-        } else {
-            I tt = w >> g.k;
+        for (int alpha = 0; alpha < 5; ++alpha) t[alpha] = __vimin_s32_relu((u0 - alpha * d) >> g.k, 5);
+    } else {
+        const I x = I(xy & 0xffffu), y = I(xy >> 16);
+        const I u0 = g.W0 - x * g.A + (x + y) * g.Kc;
+        const I d = x * g.dmul;
+#pragma unroll
+        for (int alpha = 0; alpha < 5; ++alpha) {
+            I tt = (u0 - I(alpha) * d) >> g.k;
             tt = tt < I(0) ? I(0) : (tt > I(5) ? I(5) : tt);
             t[alpha] = (int)tt;
         }
     }
     const uint32_t M = prefix_bits<0>(t[0]) | prefix_bits<5>(t[1]) | prefix_bits<10>(t[2]) |
                        prefix_bits<15>(t[3]) | prefix_bits<20>(t[4]);
-    const uint32_t v2 = code_votes<2>(M);  // children: vote bits at quad_bit(q)
-    const uint32_t v1 = code_votes<1>(M);  // grandchildren: vote bits at kGrandBase + 5*alpha + beta
+    // G grows with i (x >= 0) and with j, so a cell's SW corner is its lowest
+    // and its NE corner its highest: its code is neither 0000 nor 1111 exactly
+    // when SW is below the line and NE is not.  Results at the NE vertex bit
+    // (SW bit + 6 * side): children at quad_bit(q), grandchildren at
+    // kGrandBase + 5*alpha + beta.
+    const uint32_t v2 = (M << 12) & ~M;
+    const uint32_t v1 = (M << 6) & ~M;
     Classified<I> c;
-    c.kw = v2 & g.wspread;
-    c.gv = v1 & grand_cells(v2 & g.pspread);
+    c.kw = v2 & g.wspread & live;
+    // a line that crosses a grandchild cell crosses its child, so the cells of
+    // the passed children need no test of the child's own vote
+    c.gv = v1 & g.gmask & live;
     return c;
 }
 
@@ -574,7 +597,7 @@ struct ParentGeoF {
 };
 
 template <typename I>
-__device__ __forceinline__ Classified<I> classify(const ParentGeoF& g, uint32_t xy) {
+__device__ __forceinline__ Classified<I> classify(const ParentGeoF& g, uint32_t xy, uint32_t live) {
     const int32_t x = (int32_t)(xy & 0xffffu), y = (int32_t)(xy >> 16);
     const int32_t h00 = g.C0 + x * g.Cx - g.yK * y;
     const int32_t hx = x << g.sS;
@@ -599,8 +622,8 @@ __device__ __forceinline__ Classified<I> classify(const ParentGeoF& g, uint32_t 
         v2 |= (sum * sum <= rc ? 1u : 0u) << quad_bit(q);
     }
     Classified<I> c;
-    c.kw = v2 & g.wspread;
-    c.gv = v1 & grand_cells(v2 & g.pspread);
+    c.kw = v2 & g.wspread & live;
+    c.gv = v1 & grand_cells(v2 & g.pspread) & live;
     return c;
 }
 }  // namespace
@@ -720,14 +743,26 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
                 settle();
                 start_run(r_first);
             }
+            if (cg.wspread == 0u) {
+                // no child keeps a list (the children's level is the unit's last
+                // but one): the voters are only counted for the grandchildren
+#pragma unroll
+                for (int k = 0; k < kChunkSteps; ++k) {
+                    const uint32_t live = rec[k].y != kNoRegion ? 0xffffffffu : 0u;
+                    add_rows(rows, classify<I>(cg, rec[k].x, live).gv);
+                }
+                steps += kChunkSteps;
+                if (steps >= 255 - kChunkSteps) settle();  // byte counters nearly full
+                continue;
+            }
             uint32_t kw[kChunkSteps], gv[kChunkSteps];
             uint32_t cnt = 0;
 #pragma unroll
             for (int k = 0; k < kChunkSteps; ++k) {
                 const uint32_t live = rec[k].y != kNoRegion ? 0xffffffffu : 0u;
-                const Classified<I> c = classify<I>(cg, rec[k].x);
-                kw[k] = c.kw & live;
-                gv[k] = c.gv & live;
+                const Classified<I> c = classify<I>(cg, rec[k].x, live);
+                kw[k] = c.kw;
+                gv[k] = c.gv;
                 cnt += quad_counts(kw[k]);
             }
             // reserve each kept child's slots for the whole chunk (one atomic
@@ -793,94 +828,110 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
             continue;
         }
 
-        // ---- a parent boundary inside the chunk: step by step, lanes grouped by
-        // parent (kept rolled: this cold path must not crowd the instruction cache)
+        // ---- more than one parent in the chunk (a run ends inside it), or
+        // records without a parent: the same vectorised body once per parent,
+        // a record taking part when its parent is the run's.  Parent indices
+        // never decrease along the stream (segments are laid out in region
+        // order; records without a parent carry the largest value), so the
+        // runs are taken in order by a warp minimum over the larger parents.
+        {
+            uint32_t m = rec[0].y;
+#pragma unroll
+            for (int k = 1; k < kChunkSteps; ++k) m = min(m, rec[k].y);
+            uint32_t P = __reduce_min_sync(0xffffffffu, m);
 #pragma unroll 1
-        for (int k = 0; k < kChunkSteps; ++k) {
-            uint2 rk = rec[0];
-#pragma unroll
-            for (int kk = 1; kk < kChunkSteps; ++kk)
-                if (kk == k) rk = rec[kk];
-            const uint32_t r = rk.y;
-            const bool valid = r != kNoRegion;
-            const uint32_t active = __ballot_sync(0xffffffffu, valid);
-            if (!active) continue;  // past the end, or only records of points outside their image
-            const int last = 31 - __clz(active);
-            const uint32_t r0 = __shfl_sync(0xffffffffu, r, 0);
-            const uint32_t rl = __shfl_sync(0xffffffffu, r, last);
-            if (r0 == rl && rl == cur) {
-                // still the current run
-                uint32_t kw = 0u;
-                if (valid) {
-                    const Classified<I> c = classify<I>(cg, rk.x);
-                    kw = c.kw;
-                    add_rows(rows, c.gv);
+            while (P != kNoRegion) {
+                if (P != cur) {
+                    settle();
+                    start_run(P);
                 }
-                ++steps;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const bool keep = (kw >> quad_bit(q)) & 1u;
-                    const uint32_t bq = __ballot_sync(0xffffffffu, keep);
-                    if (!bq) continue;
-                    unsigned long long p = 0;
-                    if (lane == 0 && HHT_CHECK_INDEX(ci[q], n_chi, a.status))
-                        p = atomicAdd(&a.cursor[ci[q]], (unsigned long long)__popc(bq));
-                    p = __shfl_sync(0xffffffffu, p, 0);
-                    const uint64_t at = p + __popc(bq & lt);
-                    st_pred_v2(vout + at, keep && at < a.cap_voters, rk.x, ci[q]);
+                if (cg.wspread == 0u) {
+                    // no child keeps a list (the children's level is the unit's last
+                    // but one): the voters are only counted for the grandchildren
+    #pragma unroll
+                    for (int k = 0; k < kChunkSteps; ++k) {
+                        const uint32_t live = rec[k].y == P ? 0xffffffffu : 0u;
+                        add_rows(rows, classify<I>(cg, rec[k].x, live).gv);
+                    }
+                    steps += kChunkSteps;
+                    if (steps >= 255 - kChunkSteps) settle();  // byte counters nearly full
+                } else {
+                uint32_t kw[kChunkSteps], gv[kChunkSteps];
+                uint32_t cnt = 0;
+    #pragma unroll
+                for (int k = 0; k < kChunkSteps; ++k) {
+                    const uint32_t live = rec[k].y == P ? 0xffffffffu : 0u;
+                    const Classified<I> c = classify<I>(cg, rec[k].x, live);
+                    kw[k] = c.kw;
+                    gv[k] = c.gv;
+                    cnt += quad_counts(kw[k]);
                 }
-                continue;
-            }
-            // settle the current run; every lane classifies with its own parent
-            settle();
-            Geo g = cg;
-            if (valid && r != cur) g.load(a.pregions, HHT_CHECK_INDEX(r, n_par, a.status) ? r : 0u);
-            uint32_t kw = 0u, gv = 0u;
-            if (valid) {
-                const Classified<I> c = classify<I>(g, rk.x);
-                kw = c.kw;
-                gv = c.gv;
-            }
-            const uint32_t peers = __match_any_sync(0xffffffffu, r);
+                // reserve each kept child's slots for the whole chunk (one atomic
+                // per child): per-lane counts per quadrant as byte fields, one warp
+                // scan for all four quadrants, then every lane writes its kept
+                // voters of a quadrant to consecutive slots
+                uint32_t inc = cnt;
+    #pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const uint32_t o = __shfl_up_sync(0xffffffffu, inc, off);
+                    if (lane >= off) inc += o;
+                }
+                const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
+                // lanes 0..3 reserve the slots of quadrant `lane` in parallel; the
+                // grandchild counts are added while the reservations are in flight
+                unsigned long long mybase = 0;
+                const uint32_t tq_mine = lane < 4 ? (tot >> (8 * quad_byte_rt(lane))) & 0xffu : 0u;
+                if (tq_mine) {
+                    const uint32_t cq = lane == 0 ? ci[0] : lane == 1 ? ci[1] : lane == 2 ? ci[2] : ci[3];
+                    if (HHT_CHECK_INDEX(cq, n_chi, a.status)) mybase = atomicAdd(&a.cursor[cq], (unsigned long long)tq_mine);
+                }
+    #pragma unroll
+                for (int k = 0; k < kChunkSteps; ++k) add_rows(rows, gv[k]);
+                const bool over = tq_mine && mybase + tq_mine > a.cap_voters;
+                const bool any_over = __any_sync(0xffffffffu, over);
+                steps += kChunkSteps;
+                if (steps >= 255 - kChunkSteps) settle();  // byte counters nearly full
+                const uint32_t excl = inc - cnt;
+                if (!any_over) {
+    #pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int sh = 8 * quad_byte(q);
+                        const uint32_t tq = (tot >> sh) & 0xffu;
+                        if (!tq) continue;
+                        uint2* dst = vout + __shfl_sync(0xffffffffu, mybase, q) + ((excl >> sh) & 0xffu);
+                        const uint32_t bit = 1u << quad_bit(q);
+                        uint32_t j = 0;
+    #pragma unroll
+                        for (int k = 0; k < kChunkSteps; ++k) {
+                            const uint32_t keep = (kw[k] & bit) ? 1u : 0u;
+                            st_pred_v2(dst + j, keep, rec[k].x, ci[q]);
+                            j += keep;
+                        }
+                    }
+                } else {
+                    // the stream overflows its capacity (the host reruns with more room)
+    #pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int sh = 8 * quad_byte(q);
+                        const uint32_t tq = (tot >> sh) & 0xffu;
+                        if (!tq) continue;
+                        uint64_t p = __shfl_sync(0xffffffffu, mybase, q) + ((excl >> sh) & 0xffu);
+                        const uint32_t bit = 1u << quad_bit(q);
+    #pragma unroll
+                        for (int k = 0; k < kChunkSteps; ++k) {
+                            if (kw[k] & bit) {
+                                if (p < a.cap_voters) vout[p] = make_uint2(rec[k].x, ci[q]);
+                                ++p;
+                            }
+                        }
+                    }
+                }
+                }
+                m = kNoRegion;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const bool keep = (kw >> quad_bit(q)) & 1u;
-                const uint32_t bq = __ballot_sync(0xffffffffu, keep);
-                if (!bq) continue;
-                const uint32_t gm = bq & peers;
-                const int leader = keep ? __ffs(gm) - 1 : lane;
-                unsigned long long p = 0;
-                if (keep && lane == leader && HHT_CHECK_INDEX(child_index(g.pr, q), n_chi, a.status))
-                    p = atomicAdd(&a.cursor[child_index(g.pr, q)], (unsigned long long)__popc(gm));
-                p = __shfl_sync(0xffffffffu, p, leader);
-                const uint64_t at = p + __popc(gm & lt);
-                st_pred_v2(vout + at, keep && at < a.cap_voters, rk.x, child_index(g.pr, q));
+                for (int k = 0; k < kChunkSteps; ++k) m = min(m, rec[k].y > P ? rec[k].y : kNoRegion);
+                P = __reduce_min_sync(0xffffffffu, m);
             }
-            // count every parent but the last lane's on its own; the last one
-            // continues as the current run
-            uint32_t own[4] = {0u, 0u, 0u, 0u};
-            add_rows(own, gv);
-            const bool mine = valid && r == rl;
-            uint32_t rest = __ballot_sync(0xffffffffu, valid && !mine);
-            while (rest) {
-                // one parent group at a time; every lane takes part (lanes
-                // outside the group add zero) so the counts land in all lanes
-                const int leader = __ffs(rest) - 1;
-                const uint32_t rg = __shfl_sync(0xffffffffu, r, leader);
-                const uint32_t gmask = __ballot_sync(0xffffffffu, valid && r == rg);
-                const uint32_t in = (gmask >> lane) & 1u ? 0xffffffffu : 0u;
-                const uint32_t part[4] = {own[0] & in, own[1] & in, own[2] & in, own[3] & in};
-                uint32_t c16[8];
-                reduce_rows(part, 0xffffffffu, c16);
-                add_counts_lanes(a.child_cnt, __shfl_sync(0xffffffffu, g.pr.child_base, leader),
-                                 __shfl_sync(0xffffffffu, g.pr.packed, leader), c16, n_chi, a.status);
-                rest &= ~gmask;
-            }
-            start_run(rl);
-            if (mine) {
-                rows[0] = own[0]; rows[1] = own[1]; rows[2] = own[2]; rows[3] = own[3];
-            }
-            steps = 1;
         }
     }
     settle();
@@ -956,8 +1007,8 @@ int launch_copy16(const void* src, void* dst, uint64_t n16, int grid, void* stre
 struct PassShape {
     int steps, tpb, minb;
 };
-constexpr PassShape kPassShapes[kPassShapeCount] = {{4, 256, 3}, {2, 256, 4}, {3, 256, 4},
-                                                    {4, 128, 6}, {4, 256, 4}, {4, 512, 2}};
+constexpr PassShape kPassShapes[kPassShapeCount] = {{4, 256, 3}, {4, 128, 6}, {3, 256, 4},
+                                                    {4, 384, 2}, {4, 192, 4}, {3, 256, 3}};
 
 namespace {
 template <int S>
