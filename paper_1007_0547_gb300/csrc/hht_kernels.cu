@@ -449,12 +449,29 @@ __device__ __forceinline__ void reduce_rows(const uint32_t (&rows)[4], uint32_t 
     }
 }
 
-// Grandchild votes of one voter as byte counters: row alpha of the 4 x 4
-// cells, byte beta.
-__device__ __forceinline__ void add_rows(uint32_t (&rows)[4], uint32_t gv) {
+// Grandchild votes of a lane's voters of one chunk (up to four) added to its
+// byte counters: row alpha of the 4 x 4 cells, byte beta.  Per cell the number
+// of the voters that cross it is first formed as three bit planes (carry-save
+// adds: ones, twos, fours) and then spread into the bytes once per chunk
+// instead of once per voter (the spreading is most of the cost).
+__device__ __forceinline__ void add_rows4(uint32_t (&rows)[4], uint32_t g0, uint32_t g1, uint32_t g2, uint32_t g3) {
+    const uint32_t s01 = g0 ^ g1, c01 = g0 & g1, s23 = g2 ^ g3, c23 = g2 & g3;
+    const uint32_t ones = s01 ^ s23, c_ = s01 & s23;
+    const uint32_t twos = c01 ^ c23 ^ c_;
+    const uint32_t fours = (c01 & c23) | (c_ & (c01 | c23));
 #pragma unroll
-    for (int al = 0; al < 4; ++al)
-        rows[al] += spread4((gv >> (kGrandBase + 5 * al)) & 0xfu);
+    for (int al = 0; al < 4; ++al) {
+        const int sh = kGrandBase + 5 * al;
+        rows[al] += ((((ones >> sh) & 0xfu) * 0x204081u) & 0x01010101u) +
+                    ((((twos >> sh) & 0xfu) * 0x408102u) & 0x02020202u) +
+                    ((((fours >> sh) & 0xfu) * 0x810204u) & 0x04040404u);
+    }
+}
+
+template <int S>
+__device__ __forceinline__ void add_rows_chunk(uint32_t (&rows)[4], const uint32_t (&g)[S]) {
+    static_assert(S >= 1 && S <= 4, "a chunk has one to four warp steps");
+    add_rows4(rows, g[0], S > 1 ? g[S > 1 ? 1 : 0] : 0u, S > 2 ? g[S > 2 ? 2 : 0] : 0u, S > 3 ? g[S > 3 ? 3 : 0] : 0u);
 }
 
 // Constants of one parent region for the corner grid of its voters.  With
@@ -746,11 +763,13 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
             if (cg.wspread == 0u) {
                 // no child keeps a list (the children's level is the unit's last
                 // but one): the voters are only counted for the grandchildren
+                uint32_t gc[kChunkSteps];
 #pragma unroll
                 for (int k = 0; k < kChunkSteps; ++k) {
                     const uint32_t live = rec[k].y != kNoRegion ? 0xffffffffu : 0u;
-                    add_rows(rows, classify<I>(cg, rec[k].x, live).gv);
+                    gc[k] = classify<I>(cg, rec[k].x, live).gv;
                 }
+                add_rows_chunk<kChunkSteps>(rows, gc);
                 steps += kChunkSteps;
                 if (steps >= 255 - kChunkSteps) settle();  // byte counters nearly full
                 continue;
@@ -784,8 +803,7 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
                 const uint32_t cq = lane == 0 ? ci[0] : lane == 1 ? ci[1] : lane == 2 ? ci[2] : ci[3];
                 if (HHT_CHECK_INDEX(cq, n_chi, a.status)) mybase = atomicAdd(&a.cursor[cq], (unsigned long long)tq_mine);
             }
-#pragma unroll
-            for (int k = 0; k < kChunkSteps; ++k) add_rows(rows, gv[k]);
+            add_rows_chunk<kChunkSteps>(rows, gv);
             const bool over = tq_mine && mybase + tq_mine > a.cap_voters;
             const bool any_over = __any_sync(0xffffffffu, over);
             steps += kChunkSteps;
@@ -848,11 +866,13 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
                 if (cg.wspread == 0u) {
                     // no child keeps a list (the children's level is the unit's last
                     // but one): the voters are only counted for the grandchildren
-    #pragma unroll
+                        uint32_t gc[kChunkSteps];
+#pragma unroll
                     for (int k = 0; k < kChunkSteps; ++k) {
                         const uint32_t live = rec[k].y == P ? 0xffffffffu : 0u;
-                        add_rows(rows, classify<I>(cg, rec[k].x, live).gv);
+                        gc[k] = classify<I>(cg, rec[k].x, live).gv;
                     }
+                    add_rows_chunk<kChunkSteps>(rows, gc);
                     steps += kChunkSteps;
                     if (steps >= 255 - kChunkSteps) settle();  // byte counters nearly full
                 } else {
@@ -885,8 +905,7 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
                     const uint32_t cq = lane == 0 ? ci[0] : lane == 1 ? ci[1] : lane == 2 ? ci[2] : ci[3];
                     if (HHT_CHECK_INDEX(cq, n_chi, a.status)) mybase = atomicAdd(&a.cursor[cq], (unsigned long long)tq_mine);
                 }
-    #pragma unroll
-                for (int k = 0; k < kChunkSteps; ++k) add_rows(rows, gv[k]);
+                    add_rows_chunk<kChunkSteps>(rows, gv);
                 const bool over = tq_mine && mybase + tq_mine > a.cap_voters;
                 const bool any_over = __any_sync(0xffffffffu, over);
                 steps += kChunkSteps;
@@ -1017,7 +1036,7 @@ const void* pass_fn32() {
     return (const void*)pass_kernel<int32_t, p.steps, p.tpb, p.minb>;
 }
 const void* pass_fn(bool int64_path, int shape, bool fht = false) {
-    if (fht) return (const void*)pass_kernel<int32_t, 4, 256, 3, true>;
+    if (fht) return (const void*)pass_kernel<int32_t, 4, 256, 2, true>;
     if (int64_path) return (const void*)pass_kernel<int64_t, 4, 256, 3>;
     switch (shape) {
         case 1: return pass_fn32<1>();
