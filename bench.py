@@ -298,8 +298,20 @@ def serving_leg(ctx, n_requests: int, load: float):
     rate = load * sat_rate
     arrivals = list(synth.poisson_arrivals(len(reqs), rate))
     t_arr, t_done, total_s = drain(arrivals)
-    lat = sorted((d - a) * 1e3 for a, d in zip(t_arr, t_done))
+    per = [((d - a) * 1e3, im) for a, d, im in zip(t_arr, t_done, reqs)]
+    lat = sorted(x for x, _ in per)
+
+    def pct(xs, q):
+        xs = sorted(xs)
+        return xs[min(len(xs) - 1, int(q * len(xs)))] if xs else None
+
+    small = [x for x, im in per if im.W <= 1024]
+    large = [x for x, im in per if im.W > 1024]
+    slowest = sorted(per, key=lambda t: -t[0])[:3]
     return {"p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "side_le_1024": {"requests": len(small), "p50_ms": pct(small, 0.5), "p99_ms": pct(small, 0.99)},
+            "side_gt_1024": {"requests": len(large), "p50_ms": pct(large, 0.5), "p99_ms": pct(large, 0.99)},
+            "slowest": [{"ms": round(x, 2), "side": im.W, "n": im.n, "depth": im.depth, "T": im.T} for x, im in slowest],
             "images_per_s": len(reqs) / total_s, "saturated_images_per_s": sat_rate,
             "offered_rate_per_s": rate, "load": load, "requests": len(reqs),
             "description": "side log-uniform 64-4096, 1-256 segments, noise 0-3%, depth ceil(log2 side), "

@@ -349,6 +349,18 @@ int hht_detect_removal(hht_ctx *ctx, const hht_point *points, int64_t n, int32_t
 int hht_detect_removal_batch(hht_ctx *ctx, const hht_image *images, int32_t count, hht_result *outs);
 
 /*
+ * The edge points that solution() plotted (Section 3: the paper draws them on
+ * the image), for image `index` of the context's last removal job
+ * (hht_detect_removal: 0; hht_detect_removal_batch: the image's index), as a
+ * W x H raster written on the device: row-major, one byte per pixel, bit 0
+ * set where a point plotted in half 0 lies and bit 1 where one plotted in
+ * half 1 lies, every other byte 0.  `raster` (host or device) holds
+ * `capacity` >= W * H bytes.  Errors: HHT_E_ARG (NULL, no successful removal
+ * job, index out of range, capacity below W * H), HHT_E_CUDA.
+ */
+int hht_removal_raster(hht_ctx *ctx, int32_t index, uint8_t *raster, uint64_t capacity);
+
+/*
  * One shard of a detection split by subtrees (no paper counterpart: a way to
  * spread one large image over several GPUs).  Below level k = split_level the
  * regions of the two halves are independent given the points, so several

@@ -1019,7 +1019,7 @@ void hht_destroy(hht_ctx* c) {
                      &c->edge_pts[1], &c->edge_tot,   &c->line_keys,    &c->line_vals, &c->line_parent,
                      &c->line_cells, &c->line_sums,  &c->line_out,     &c->keep_buf,  &c->rem_pts,
                      &c->rem_lists,  &c->rem_bitmap, &c->rem_leaves,   &c->rem_stats, &c->rem_tasks,
-                     &c->dims};
+                     &c->dims, &c->rem_flags, &c->rem_raster};
     for (DevBuf* b : all) release(c, *b);
     delete c;
 }

@@ -68,7 +68,10 @@ struct hht_ctx {
     int32_t job_keep_level = 0;
     DevBuf keep_buf;
     // solution() traversal (hht_detect_removal): points, per-level lists, removed bitmaps, leaves, stats, tasks
-    DevBuf rem_pts, rem_lists, rem_bitmap, rem_leaves, rem_stats, rem_tasks;
+    DevBuf rem_pts, rem_lists, rem_bitmap, rem_leaves, rem_stats, rem_tasks, rem_flags, rem_raster;
+    // the last removal job, per image: points offset, n, bitmap offsets of
+    // half 0 and half 1, W, H (hht_removal_raster)
+    std::vector<uint64_t> rem_last;
     // front end (hht_edges, hht_detect_image): staged image, ALPHA and BETA point lists, their counts
     DevBuf img_buf, edge_pts[2], edge_tot;
     // leaves -> lines (hht_lines): hash table, union-find parents, per-root sums, output

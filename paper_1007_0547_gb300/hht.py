@@ -35,7 +35,7 @@ EXPORTS = ("hht_create", "hht_destroy", "hht_detect", "hht_detect_batch", "hht_f
            "hht_detect_noalloc", "hht_autotune", "hht_set_tuning", "hht_set_batch_mode", "hht_fetch_all_leaves",
            "hht_inject_fault", "hht_set_predicate", "hht_edges", "hht_detect_image", "hht_lines",
            "hht_detect_subtrees", "hht_detect_removal", "hht_detect_removal_batch",
-           "hht_create_with_allocator", "hht_done_tickets")
+           "hht_create_with_allocator", "hht_done_tickets", "hht_removal_raster")
 BATCH_LEVELS, BATCH_GRAPH = 0, 1
 BATCH_PERSISTENT = BATCH_GRAPH  # earlier name
 FAULT_NONE, FAULT_WITHHOLD_SCAN_TILE, FAULT_GRAPH_CAPACITY = 0, 1, 2
@@ -163,6 +163,8 @@ def load(path: Optional[str] = None):
     lib.hht_detect_removal.restype = ctypes.c_int
     lib.hht_detect_removal_batch.argtypes = [vp, ctypes.POINTER(_Image), i32, ctypes.POINTER(_Result)]
     lib.hht_detect_removal_batch.restype = ctypes.c_int
+    lib.hht_removal_raster.argtypes = [vp, i32, vp, u64]
+    lib.hht_removal_raster.restype = ctypes.c_int
     lib.hht_detect_subtrees.argtypes = [vp, vp, i64, i32, i32, i32, i32, i32, vp, ctypes.POINTER(_Result)]
     lib.hht_detect_subtrees.restype = ctypes.c_int
     lib.hht_lines.argtypes = [vp, i32, vp, u64, ctypes.POINTER(u64)]
@@ -563,6 +565,22 @@ class Context:
             raise HhtError(rc, "hht_detect_removal")
         k = int(r.n_leaves)
         return Result(buf[:k], _stats_of(r), int(r.depth), int(r.L), rc), (plotted[:, : p.n] if with_plotted else None)
+
+    def removal_raster(self, index: int, W: int, H: int, on_device: bool = False):
+        """The points that solution() plotted for image `index` of the last
+        removal job as a uint8 [H, W] raster (bit 0: half 0, bit 1: half 1),
+        numpy on the host or a torch tensor on the device."""
+        if on_device:
+            import torch
+            buf = torch.empty((int(H), int(W)), dtype=torch.uint8, device=f"cuda:{self.device}")
+            ptr = buf.data_ptr()
+        else:
+            buf = np.empty((int(H), int(W)), dtype=np.uint8)
+            ptr = buf.ctypes.data
+        rc = load().hht_removal_raster(self._h, int(index), ptr, int(W) * int(H))
+        if rc != HHT_OK:
+            raise HhtError(rc, "hht_removal_raster")
+        return buf
 
     def detect_removal_batch(self, images: Sequence[Tuple]) -> List[Result]:
         """hht_detect_removal_batch over (points, W, H, depth, T) tuples."""

@@ -32,7 +32,7 @@ def test_header_declares_the_api():
                                 "hht_inject_fault", "hht_set_predicate", "hht_edges", "hht_detect_image",
                                 "hht_lines", "hht_detect_subtrees", "hht_detect_removal",
                                 "hht_detect_removal_batch", "hht_create_with_allocator",
-                                "hht_done_tickets"}
+                                "hht_done_tickets", "hht_removal_raster"}
 
 
 def test_library_exports_every_declared_symbol(lib):
@@ -70,6 +70,7 @@ def test_host_only_calls(lib):
     assert lib.hht_edges(None, None, 8, 8, 10, None, 0, ctypes.byref(na), None, 0, ctypes.byref(nb)) == hht.HHT_E_ARG
     assert lib.hht_detect_image(None, None, 8, 8, 10, 3, 1, ctypes.byref(r)) == hht.HHT_E_ARG
     assert lib.hht_lines(None, 0, None, 0, ctypes.byref(na)) == hht.HHT_E_ARG
+    assert lib.hht_removal_raster(None, 0, None, 0) == hht.HHT_E_ARG
     assert lib.hht_detect_subtrees(None, None, 0, 8, 8, 3, 1, 1, None, ctypes.byref(r)) == hht.HHT_E_ARG
     assert lib.hht_detect_removal(None, None, 0, 8, 8, 3, 1, ctypes.byref(r), None) == hht.HHT_E_ARG
     assert lib.hht_detect_removal_batch(None, None, 0, None) == hht.HHT_E_ARG
