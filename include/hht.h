@@ -48,11 +48,10 @@ extern "C" {
 /*
  * Size limits.  Images are at most HHT_MAX_SIDE pixels on a side and
  * HHT_MAX_DEPTH levels deep.  One level of a job holds at most 2^32 - 2
- * regions (HHT_E_NOMEM beyond).  Known limit: the selection sums the voters
- * that 1024 consecutive regions of a level pass on in 32 bits, so a level
- * whose 1024 consecutive regions pass on 2^32 or more voters gives wrong
- * leaves with no error.  That takes about 7e8 points in one image, or shallow
- * images (depth 2-5) averaging 1.4e6 points in one batch.
+ * regions (HHT_E_NOMEM beyond).  The voters that a level's regions hand on
+ * to their children are summed in 64 bits at every stage of the selection,
+ * so a level's voter streams have no 32-bit limit; their size is bounded by
+ * device memory (HHT_E_NOMEM when a single image's level does not fit).
  */
 #define HHT_MAX_DEPTH 24
 #define HHT_MAX_SIDE 32767

@@ -176,7 +176,8 @@ struct alignas(16) JobDims {
 
 // Kernel launchers (hht_kernels.cu).  All are asynchronous on `stream`.
 // Level 0 of the images [0, n_images) of `pts` (image g owns points
-// [img_start[g], img_start[g+1]) and the units img_unit[g], img_unit[g] + 1).
+// [img_start[g], img_start[g+1]) and the units img_unit[g], img_unit[g] + 1;
+// a point outside its image sets kErrRange in img_err[img_unit[g] / 2]).
 // With `dims` the kernel reads total_points and n_images from device memory
 // instead, and `grid` (> 0) fixes the grid (for a CUDA graph reused across jobs).
 int launch_stage(const int16_t* pts, uint64_t total_points, const Unit* units, int n_images,

@@ -109,7 +109,10 @@ __device__ __forceinline__ void stage_body(const int16_t* __restrict__ pts, uint
             px = pts[2 * k];
             py = pts[2 * k + 1];
             ok = px >= 0 && px < U.W && py >= 0 && py < U.H;
-            if (!ok) atomicOr(&img_err[img], kErrRange);  // the image fails; the others are unaffected
+            // the image fails; the others are unaffected.  Flags are indexed by
+            // unit pair (img_unit / 2): the image's index in a batch, its
+            // request slot in serving
+            if (!ok) atomicOr(&img_err[img_unit[img] >> 1], kErrRange);
         }
 #pragma unroll
         for (int h = 0; h < 2; ++h) {

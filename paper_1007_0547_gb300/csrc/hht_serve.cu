@@ -43,7 +43,9 @@ struct Request {
     bool done = false;
     bool range_error = false;
     int status = HHT_E_PENDING;
-    std::vector<hht_leaf> leaves;
+    // a finished request's leaves stay in device memory until it is polled
+    void* dev_leaves = nullptr;
+    uint64_t dev_bytes = 0;
     hht_result res{};
 };
 
@@ -67,10 +69,38 @@ struct ServeState {
     uint64_t P = 0, NV = 0;  // regions and voters of the current step
     DevBuf units, stats, infos, status, leaf_total, img_err, scan, pts, img_start, img_unit;
     DevBuf rec[2], preg[2], cnt[2], vox[2], cursors, leaves, sel_flags, sel_data;
-    std::vector<hht_leaf> h_leaves;
+    hht_ctx* ctx = nullptr;  // for the per-request leaf buffers
 };
 
-void serve_destroy(ServeState* s) { delete s; }
+// Device memory for one finished request's leaves: the caller's allocator
+// when the context has one, else the device's stream-ordered pool.
+void* result_alloc(hht_ctx* c, size_t bytes) {
+    void* p = nullptr;
+    if (c->has_allocator) {
+        p = c->allocator.alloc(bytes, (void*)c->stream, c->allocator.user);
+        return p;
+    }
+    if (cudaMallocAsync(&p, bytes, c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+void result_free(hht_ctx* c, void* p, size_t bytes) {
+    if (!p) return;
+    if (c->has_allocator)
+        c->allocator.free(p, bytes, (void*)c->stream, c->allocator.user);
+    else
+        cudaFreeAsync(p, c->stream);
+}
+
+void serve_destroy(ServeState* s) {
+    if (!s) return;
+    if (s->ctx)
+        for (auto& kv : s->reqs) result_free(s->ctx, kv.second.dev_leaves, kv.second.dev_bytes);
+    if (s->ctx) cudaStreamSynchronize(s->ctx->stream);
+    delete s;
+}
 
 }  // namespace hht
 
@@ -80,7 +110,10 @@ namespace {
 
 ServeState* serve_of(hht_ctx* c) {
     ServeState** slot = hht_internal_serve_slot(c);
-    if (!*slot) *slot = new ServeState();
+    if (!*slot) {
+        *slot = new ServeState();
+        (*slot)->ctx = c;
+    }
     return *slot;
 }
 
@@ -113,6 +146,7 @@ int engine_init(hht_ctx* c, ServeState* S) {
     SV_RK(ensure(c, S->infos, 2 * sizeof(LevelInfo), true));
     SV_RK(ensure(c, S->status, sizeof(DeviceStatus), true));
     SV_RK(ensure(c, S->leaf_total, sizeof(uint64_t), true));
+    SV_RK(ensure(c, S->img_err, ServeState::kSlots * sizeof(uint32_t), true));  // range flags per request slot
     SV_RK(ensure(c, S->scan, sizeof(ScanState), true));
     for (int s = ServeState::kSlots - 1; s >= 0; --s) S->free_slots.push_back(s);
     if (c->budget) {
@@ -182,7 +216,6 @@ int engine_admit(hht_ctx* c, ServeState* S) {
     SV_RK(ensure(c, S->pts, std::max<uint64_t>(total, 1) * sizeof(hht_point)));
     SV_RK(ensure(c, S->img_start, (m + 1) * sizeof(uint64_t)));
     SV_RK(ensure(c, S->img_unit, m * sizeof(uint32_t)));
-    SV_RK(ensure(c, S->img_err, m * sizeof(uint32_t)));
     for (int k = 0; k < m; ++k) {
         const Request& r = S->reqs[adm[k]];
         SV_CK(cudaMemcpyAsync((Unit*)S->units.p + 2 * r.slot, &nu[2 * k], 2 * sizeof(Unit), cudaMemcpyHostToDevice, st));
@@ -200,7 +233,8 @@ int engine_admit(hht_ctx* c, ServeState* S) {
         SV_CK(cudaMemcpyAsync(S->pts.p, pts.data(), total * sizeof(hht_point), cudaMemcpyHostToDevice, st));
     SV_CK(cudaMemcpyAsync(S->img_start.p, img_start.data(), (m + 1) * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
     SV_CK(cudaMemcpyAsync(S->img_unit.p, img_unit.data(), m * sizeof(uint32_t), cudaMemcpyHostToDevice, st));
-    SV_CK(cudaMemsetAsync(S->img_err.p, 0, m * sizeof(uint32_t), st));
+    for (int k = 0; k < m; ++k)
+        SV_CK(cudaMemsetAsync((uint32_t*)S->img_err.p + S->reqs[adm[k]].slot, 0, sizeof(uint32_t), st));
     SV_CK(cudaMemcpyAsync((Region*)S->rec[cp].p + S->P, roots.data(), 2 * m * sizeof(Region), cudaMemcpyHostToDevice, st));
     SV_CK(cudaMemsetAsync((char*)S->cnt[cp].p + S->P * 16, 0, 2 * m * 16, st));
     if (launch_stage((const int16_t*)S->pts.p, total, (const Unit*)S->units.p, m, (const uint64_t*)S->img_start.p,
@@ -208,11 +242,7 @@ int engine_admit(hht_ctx* c, ServeState* S) {
                      (uint64_t*)S->stats.p, (uint32_t*)S->img_err.p, (DeviceStatus*)S->status.p, S->n_i64 > 0,
                      st) != 0)
         return HHT_E_CUDA;
-    std::vector<uint32_t> err(m, 0);
-    SV_CK(cudaMemcpyAsync(err.data(), S->img_err.p, m * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-    SV_CK(cudaStreamSynchronize(st));
-    for (int k = 0; k < m; ++k)
-        if (err[k]) S->reqs[adm[k]].range_error = true;
+    // range errors are read when the request completes (no synchronisation here)
     S->P += 2 * (uint64_t)m;
     S->NV += v0;
     return HHT_OK;
@@ -227,18 +257,23 @@ int engine_complete(hht_ctx* c, ServeState* S, uint64_t step_leaves) {
         if (r.t0 + r.im.depth == S->step) fin.push_back(t);
     }
     if (fin.empty()) return HHT_OK;
-    if (step_leaves > 0) {
-        S->h_leaves.resize(step_leaves);
-        SV_CK(cudaMemcpyAsync(S->h_leaves.data(), S->leaves.p, step_leaves * sizeof(hht_leaf), cudaMemcpyDeviceToHost, st));
-    }
     std::vector<std::vector<uint64_t>> rows(fin.size(), std::vector<uint64_t>(2 * (kMaxDepth + 1) * 4));
     for (size_t k = 0; k < fin.size(); ++k) {
         const Request& r = S->reqs[fin[k]];
         SV_CK(cudaMemcpyAsync(rows[k].data(), (uint64_t*)S->stats.p + (size_t)2 * r.slot * (kMaxDepth + 1) * 4,
                               rows[k].size() * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
     }
+    std::vector<uint32_t> slot_err(ServeState::kSlots, 0);
+    SV_CK(cudaMemcpyAsync(slot_err.data(), S->img_err.p, ServeState::kSlots * sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                          st));
     SV_CK(cudaStreamSynchronize(st));
-    // the step's leaves are one block per finishing unit, in record (= admission) order
+    for (uint64_t t : fin) {
+        Request& r = S->reqs[t];
+        if (slot_err[r.slot]) r.range_error = true;
+    }
+    // the step's leaves are one block per finishing unit, in record (= admission)
+    // order; each request's block is copied on the device into its own buffer
+    // (polled later straight into the caller's), so no host copy holds the loop
     uint64_t off = 0;
     std::lock_guard<std::mutex> lk(S->mu);
     for (size_t k = 0; k < fin.size(); ++k) {
@@ -261,9 +296,19 @@ int engine_complete(hht_ctx* c, ServeState* S, uint64_t step_leaves) {
         }
         res.n_leaves = nl;
         if (off + nl > step_leaves) return HHT_E_CUDA;
-        r.leaves.assign(S->h_leaves.begin() + off, S->h_leaves.begin() + off + nl);
-        off += nl;
         r.status = r.range_error ? HHT_E_RANGE : HHT_OK;
+        if (nl > 0 && r.status == HHT_OK) {
+            r.dev_bytes = nl * sizeof(hht_leaf);
+            r.dev_leaves = result_alloc(c, r.dev_bytes);
+            if (!r.dev_leaves) {
+                r.dev_bytes = 0;
+                r.status = HHT_E_NOMEM;
+            } else {
+                SV_CK(cudaMemcpyAsync(r.dev_leaves, (const DevLeaf*)S->leaves.p + off, r.dev_bytes,
+                                      cudaMemcpyDeviceToDevice, st));
+            }
+        }
+        off += nl;
         r.done = true;
         S->finished.push_back(fin[k]);
         r.pts.clear();
@@ -272,6 +317,8 @@ int engine_complete(hht_ctx* c, ServeState* S, uint64_t step_leaves) {
         S->in_flight_bytes -= r.est;
         if (ceil_log2_i(std::max(r.im.W, r.im.H)) + D > 27) --S->n_i64;
     }
+    // the copies are done before any poll reads them (on any stream)
+    SV_CK(cudaStreamSynchronize(st));
     if (off != step_leaves) return HHT_E_CUDA;
     std::vector<uint64_t> keep;
     for (uint64_t t : S->order)
@@ -447,7 +494,7 @@ int hht_poll(hht_ctx* c, uint64_t ticket, hht_result* out) {
         }
         if (res.n_leaves) {
             cudaSetDevice(c->device);
-            if (cudaMemcpy(dst, r.leaves.data(), res.n_leaves * sizeof(hht_leaf), cudaMemcpyDefault) != cudaSuccess) {
+            if (cudaMemcpy(dst, r.dev_leaves, r.dev_bytes, cudaMemcpyDefault) != cudaSuccess) {
                 cudaGetLastError();
                 rc = HHT_E_CUDA;
             }
@@ -455,6 +502,10 @@ int hht_poll(hht_ctx* c, uint64_t ticket, hht_result* out) {
     }
     *out = res;
     out->status = rc;
+    if (r.dev_leaves) {
+        cudaSetDevice(c->device);
+        result_free(c, r.dev_leaves, r.dev_bytes);
+    }
     s->reqs.erase(it);
     // A client that polls without draining hht_done_tickets leaves polled
     // tickets on the completion list: drop them once they outnumber the live
