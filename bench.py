@@ -651,6 +651,10 @@ def main():
                    "accepted_cells": int(sum(r.n_leaves for r in rres))}
 
     # ---------------------------------------------------------------- single images and serving (configs 1, 2, 5)
+    # the batch context's buffers (sized from the batch's upper bounds) are
+    # given back first, so that the serving leg's memory budget is the
+    # device's, as for a serving process of its own
+    ctx.close()
     latency, serving = None, None
     if not args.no_latency and rank == 0:
         lctx = hht.Context(device=local, stream=stream)
@@ -713,7 +717,6 @@ def main():
         "autotune": tuning,
     }
     print(json.dumps(line), flush=True)
-    ctx.close()
     if world > 1:
         dist.destroy_process_group()
 

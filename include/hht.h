@@ -200,13 +200,22 @@ int hht_fetch_all_leaves(hht_ctx *ctx, hht_leaf *leaves, uint64_t capacity, uint
 
 /*
  * Serving interface.  hht_submit() queues one request and returns at once;
- * the image is copied (host points) or referenced (device points; they must
- * stay valid until the request is done).  Requests are admitted to the GPU as
- * the context's memory budget and slots allow and are processed in
- * continuous batches; hht_poll() returns HHT_E_PENDING until the request is
- * done, then fills *out (whose leaf buffer the caller provides at poll time)
- * and releases the ticket.  hht_progress() lets the library advance queued
- * work without blocking (it returns the number of requests in flight).
+ * its points (host or device memory) are copied, so the caller's buffer may
+ * be reused when it returns.  hht_progress() runs one step of the engine's
+ * level loop and returns when that step's kernels have finished, with the
+ * number of requests in flight or waiting (or a negative error code: the
+ * requests in flight then fail with it).  At each step waiting requests are
+ * admitted in arrival order while the context's memory budget (70 % of the
+ * free device memory at the first step when the context has none) and 1024 request slots
+ * allow; a request that does not fit is passed over by later ones that do
+ * for at most 12 steps, after which nothing is admitted until it fits.  A
+ * finished request's leaves stay in device memory until it is polled.
+ * hht_poll() returns HHT_E_PENDING until the request is done, then copies its
+ * leaves into the caller's buffer (host or device memory; pinned host memory
+ * is copied fastest), fills *out and releases the ticket; HHT_E_CAPACITY
+ * (with out->n_leaves set) leaves the ticket valid for a larger buffer.  A
+ * poll's copy runs on a stream of its own and does not wait for the step in
+ * progress, so polls may come from other threads than hht_progress().
  */
 int hht_submit(hht_ctx *ctx, const hht_image *image, uint64_t *ticket);
 int hht_poll(hht_ctx *ctx, uint64_t ticket, hht_result *out);

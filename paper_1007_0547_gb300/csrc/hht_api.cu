@@ -72,6 +72,14 @@ int ensure(hht_ctx* c, DevBuf& b, size_t bytes, bool zero) {
     }
     void* p = nullptr;
     cudaError_t e = dev_alloc(c, &p, want);
+    if (e != cudaSuccess && want > bytes) {
+        // the growth margin did not fit: the exact size may
+        cudaGetLastError();
+        if (p) dev_free(c, p, want);
+        p = nullptr;
+        want = std::max<size_t>((bytes + 4095) & ~size_t(4095), 4096);
+        e = dev_alloc(c, &p, want);
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         if (p) dev_free(c, p, want);  // an allocator's block without the needed alignment
@@ -100,7 +108,15 @@ int ensure_keep(hht_ctx* c, DevBuf& b, size_t bytes, size_t keep) {
         if (c->held + want > c->budget) return HHT_E_NOMEM;
     }
     void* p = nullptr;
-    if (dev_alloc(c, &p, want) != cudaSuccess) {
+    cudaError_t e0 = dev_alloc(c, &p, want);
+    if (e0 != cudaSuccess && want > bytes) {
+        cudaGetLastError();  // the growth margin did not fit: try the exact size
+        if (p) dev_free(c, p, want);
+        p = nullptr;
+        want = (bytes + 4095) & ~size_t(4095);
+        e0 = dev_alloc(c, &p, want);
+    }
+    if (e0 != cudaSuccess) {
         cudaGetLastError();
         if (p) dev_free(c, p, want);
         return HHT_E_NOMEM;
@@ -216,20 +232,34 @@ constexpr int kSelTile = 1024;   // parents per select tile
 // small copies) goes through cudaMemcpyAsync.
 }  // namespace
 
-int hht::copy_out(hht_ctx* c, void* dst, const void* src, size_t bytes) {
+namespace {
+// 1: copied by copy16_kernel, 0: by cudaMemcpyAsync, < 0: an error code
+int copy_out_impl(hht_ctx* c, void* dst, const void* src, size_t bytes, cudaStream_t st) {
     constexpr size_t kKernelMin = 1u << 20;
     if (bytes >= kKernelMin && !c->copy_engine_only && ((uintptr_t)dst % 16) == 0 && ((uintptr_t)src % 16) == 0 &&
         bytes % 16 == 0) {
         cudaPointerAttributes at{};
         if (cudaPointerGetAttributes(&at, dst) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer) {
-            if (launch_copy16(src, at.devicePointer, bytes / 16, c->num_sms * 4, c->stream) != 0) return HHT_E_CUDA;
-            c->prof.launches += 1;
-            return HHT_OK;
+            if (launch_copy16(src, at.devicePointer, bytes / 16, c->num_sms * 4, st) != 0) return HHT_E_CUDA;
+            return 1;
         }
         cudaGetLastError();
     }
-    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream));
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st));
+    return 0;
+}
+}  // namespace
+
+int hht::copy_out(hht_ctx* c, void* dst, const void* src, size_t bytes) {
+    const int r = copy_out_impl(c, dst, src, bytes, c->stream);
+    if (r < 0) return r;
+    c->prof.launches += (uint64_t)r;
     return HHT_OK;
+}
+
+int hht::copy_out_on(hht_ctx* c, void* dst, const void* src, size_t bytes, cudaStream_t stream) {
+    const int r = copy_out_impl(c, dst, src, bytes, stream);
+    return r < 0 ? r : HHT_OK;
 }
 
 namespace {
@@ -373,6 +403,7 @@ LevelArgs level_args(hht_ctx* c, int s) {
     a.tile_data = (uint64_t*)c->sel_data.p;
     a.withhold_tile_plus1 = c->inject_tile >= 0 ? (uint32_t)(c->inject_tile + 1) : 0u;
     a.keep = c->job_keep;
+    a.img_err = (const uint32_t*)c->img_err.p;
     a.keep_level = c->job_keep_level;
     return a;
 }

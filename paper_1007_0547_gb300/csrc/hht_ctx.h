@@ -119,6 +119,9 @@ int cuda_fail(cudaError_t e);
 // Copy leaves (or any 16-byte-aligned device data) to a caller's buffer on
 // the context's stream (hht_api.cu).
 int copy_out(hht_ctx* c, void* dst, const void* src, size_t bytes);
+// The same on `stream`, without touching the context's counters (callers
+// that do not hold the context's lock, such as hht_poll).
+int copy_out_on(hht_ctx* c, void* dst, const void* src, size_t bytes, cudaStream_t stream);
 // Grow a device buffer to at least `bytes` (contents are not kept; zeroed when asked).
 int ensure(hht_ctx* c, DevBuf& b, size_t bytes, bool zero = false);
 // Grow a device buffer keeping its first `keep` bytes.

@@ -163,6 +163,11 @@ struct LevelArgs {
     // keep[half * 4^k + a * 2^k + b] != 0 (NULL = every region may pass)
     const uint8_t* keep;
     int32_t keep_level;
+    // range flags per unit pair (unit / 2), written by the stage kernel: the
+    // root of an image with a point outside it passes no children, so the
+    // dead records of those points in the level-0 stream vote for nothing
+    // (NULL = no flags)
+    const uint32_t* img_err;
 };
 
 // Sizes of a job that the stage kernel reads from device memory when it is

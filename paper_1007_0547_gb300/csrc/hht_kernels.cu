@@ -253,6 +253,8 @@ __device__ __forceinline__ void select_body(const LevelArgs& a, bool standalone)
             uint32_t pm = 0;
 #pragma unroll
             for (int q = 0; q < 4; ++q) pm |= (cnt[j][q] >= (uint32_t)U.T ? 1u : 0u) << q;
+            // an image with a point outside it fails: its root passes nothing
+            if (lev == 1 && a.img_err && a.img_err[R.unit >> 1]) pm = 0u;
             if (a.keep && lev == a.keep_level) {
                 // subtrees that another shard runs: tested and counted, not split
                 const uint64_t side = 1ull << lev;
@@ -723,9 +725,97 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
         for (int q = 0; q < 4; ++q) ci[q] = child_index(cg.pr, q);
     };
 
+    // The voters of one chunk that belong to the run's parent `cur`: every
+    // record when `all` (a constant at each call), else those whose parent
+    // is P.  They are classified against it, the kept ones appended to their
+    // children's segments and the grandchild votes counted.
+    auto run_chunk = [&](const uint2* rec, bool all, uint32_t P) {
+        auto live = [&](int k) { return (all || rec[k].y == P) ? 0xffffffffu : 0u; };
+        if (cg.wspread == 0u) {
+            // no child keeps a list (the children's level is the unit's last
+            // but one): the voters are only counted for the grandchildren
+            uint32_t gc[kChunkSteps];
+#pragma unroll
+            for (int k = 0; k < kChunkSteps; ++k) gc[k] = classify<I>(cg, rec[k].x, live(k)).gv;
+            add_rows_chunk<kChunkSteps>(rows, gc);
+            steps += kChunkSteps;
+            if (steps >= 255 - kChunkSteps) settle();  // byte counters nearly full
+            return;
+        }
+        uint32_t kw[kChunkSteps], gv[kChunkSteps];
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int k = 0; k < kChunkSteps; ++k) {
+            const Classified<I> cl = classify<I>(cg, rec[k].x, live(k));
+            kw[k] = cl.kw;
+            gv[k] = cl.gv;
+            cnt += quad_counts(kw[k]);
+        }
+        // reserve each kept child's slots for the whole chunk (one atomic per
+        // child): per-lane counts per quadrant as byte fields, one warp scan
+        // for all four quadrants, then every lane writes its kept voters of a
+        // quadrant to consecutive slots
+        uint32_t inc = cnt;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t o = __shfl_up_sync(0xffffffffu, inc, off);
+            if (lane >= off) inc += o;
+        }
+        const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
+        // lanes 0..3 reserve the slots of quadrant `lane` in parallel; the
+        // grandchild counts are added while the reservations are in flight
+        unsigned long long mybase = 0;
+        const uint32_t tq_mine = lane < 4 ? (tot >> (8 * quad_byte_rt(lane))) & 0xffu : 0u;
+        if (tq_mine) {
+            const uint32_t cq = lane == 0 ? ci[0] : lane == 1 ? ci[1] : lane == 2 ? ci[2] : ci[3];
+            if (HHT_CHECK_INDEX(cq, n_chi, a.status)) mybase = atomicAdd(&a.cursor[cq], (unsigned long long)tq_mine);
+        }
+        add_rows_chunk<kChunkSteps>(rows, gv);
+        const bool over = tq_mine && mybase + tq_mine > a.cap_voters;
+        const bool any_over = __any_sync(0xffffffffu, over);
+        steps += kChunkSteps;
+        if (steps >= 255 - kChunkSteps) settle();  // byte counters nearly full
+        const uint32_t excl = inc - cnt;
+        if (!any_over) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int sh = 8 * quad_byte(q);
+                const uint32_t tq = (tot >> sh) & 0xffu;
+                if (!tq) continue;
+                uint2* dst = vout + __shfl_sync(0xffffffffu, mybase, q) + ((excl >> sh) & 0xffu);
+                const uint32_t bit = 1u << quad_bit(q);
+                uint32_t j = 0;
+#pragma unroll
+                for (int k = 0; k < kChunkSteps; ++k) {
+                    const uint32_t keep = (kw[k] & bit) ? 1u : 0u;
+                    st_pred_v2(dst + j, keep, rec[k].x, ci[q]);
+                    j += keep;
+                }
+            }
+        } else {
+            // the stream overflows its capacity (the host reruns with more room)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int sh = 8 * quad_byte(q);
+                const uint32_t tq = (tot >> sh) & 0xffu;
+                if (!tq) continue;
+                uint64_t p = __shfl_sync(0xffffffffu, mybase, q) + ((excl >> sh) & 0xffu);
+                const uint32_t bit = 1u << quad_bit(q);
+#pragma unroll
+                for (int k = 0; k < kChunkSteps; ++k) {
+                    if (kw[k] & bit) {
+                        if (p < a.cap_voters) vout[p] = make_uint2(rec[k].x, ci[q]);
+                        ++p;
+                    }
+                }
+            }
+        }
+    };
+
     // chunks are loaded one ahead through a lane pointer with constant
     // offsets; `rem` counts the records of the loaded chunk's grab from the
-    // chunk on (at most G)
+    // chunk on (at most G; grabs hold whole chunks, so only the stream's last
+    // chunk is partial)
     const uint2* pin = vin + c + lane;
     int rem = (int)(c + G < nin ? G : nin - c);
     uint2 nxt[kChunkSteps];
@@ -735,7 +825,7 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
         uint2 rec[kChunkSteps];
 #pragma unroll
         for (int k = 0; k < kChunkSteps; ++k) rec[k] = nxt[k];
-        const int nvalid = rem < kChunk ? rem : kChunk;
+        const bool full = rem >= kChunk;
         // the chunk after this one: the rest of this grab, else the claimed grab
         rem -= kChunk;
         pin += kChunk;
@@ -745,215 +835,53 @@ __device__ __forceinline__ void pass_body(const LevelArgs& a) {
             pin = vin + c + lane;
             if (lane == 0 && rem > 0) claim_at = (uint64_t)nwarps * G + atomicAdd(claim_ctr, (unsigned long long)G);
         }
+        if (rem >= kChunk) {
 #pragma unroll
-        for (int k = 0; k < kChunkSteps; ++k) nxt[k] = 32 * k + lane < rem ? pin[32 * k] : make_uint2(0u, kNoRegion);
+            for (int k = 0; k < kChunkSteps; ++k) nxt[k] = pin[32 * k];
+        } else {
+#pragma unroll
+            for (int k = 0; k < kChunkSteps; ++k)
+                nxt[k] = 32 * k + lane < rem ? pin[32 * k] : make_uint2(0u, kNoRegion);
+        }
         const uint32_t r_first = __shfl_sync(0xffffffffu, rec[0].y, 0);
-        const int lk = (nvalid - 1) >> 5, ll = (nvalid - 1) & 31;
-        uint32_t r_last = rec[0].y;
-#pragma unroll
-        for (int k = 1; k < kChunkSteps; ++k)
-            if (k == lk) r_last = rec[k].y;
-        r_last = __shfl_sync(0xffffffffu, r_last, ll);
+        const uint32_t r_last = __shfl_sync(0xffffffffu, rec[kChunkSteps - 1].y, 31);
 
-        if (r_first == r_last && r_first != kNoRegion) {
-            // ---- the whole chunk belongs to one parent (the stream is grouped by
-            // parent; a chunk that starts and ends with dead records goes step by
-            // step, where only live lanes look up their parent)
+        if (full && r_first == r_last && r_first != kNoRegion) {
+            // ---- a whole chunk of one parent: the stream is grouped by parent,
+            // so every record between the first and the last is the parent's
+            // (records without a parent, of points outside their image, lie
+            // only within their own image's level-0 run, whose root passes
+            // nothing, so they count nowhere)
             if (r_first != cur) {
                 settle();
                 start_run(r_first);
             }
-            if (cg.wspread == 0u) {
-                // no child keeps a list (the children's level is the unit's last
-                // but one): the voters are only counted for the grandchildren
-                uint32_t gc[kChunkSteps];
-#pragma unroll
-                for (int k = 0; k < kChunkSteps; ++k) {
-                    const uint32_t live = rec[k].y != kNoRegion ? 0xffffffffu : 0u;
-                    gc[k] = classify<I>(cg, rec[k].x, live).gv;
-                }
-                add_rows_chunk<kChunkSteps>(rows, gc);
-                steps += kChunkSteps;
-                if (steps >= 255 - kChunkSteps) settle();  // byte counters nearly full
-                continue;
-            }
-            uint32_t kw[kChunkSteps], gv[kChunkSteps];
-            uint32_t cnt = 0;
-#pragma unroll
-            for (int k = 0; k < kChunkSteps; ++k) {
-                const uint32_t live = rec[k].y != kNoRegion ? 0xffffffffu : 0u;
-                const Classified<I> c = classify<I>(cg, rec[k].x, live);
-                kw[k] = c.kw;
-                gv[k] = c.gv;
-                cnt += quad_counts(kw[k]);
-            }
-            // reserve each kept child's slots for the whole chunk (one atomic
-            // per child): per-lane counts per quadrant as byte fields, one warp
-            // scan for all four quadrants, then every lane writes its kept
-            // voters of a quadrant to consecutive slots
-            uint32_t inc = cnt;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const uint32_t o = __shfl_up_sync(0xffffffffu, inc, off);
-                if (lane >= off) inc += o;
-            }
-            const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
-            // lanes 0..3 reserve the slots of quadrant `lane` in parallel; the
-            // grandchild counts are added while the reservations are in flight
-            unsigned long long mybase = 0;
-            const uint32_t tq_mine = lane < 4 ? (tot >> (8 * quad_byte_rt(lane))) & 0xffu : 0u;
-            if (tq_mine) {
-                const uint32_t cq = lane == 0 ? ci[0] : lane == 1 ? ci[1] : lane == 2 ? ci[2] : ci[3];
-                if (HHT_CHECK_INDEX(cq, n_chi, a.status)) mybase = atomicAdd(&a.cursor[cq], (unsigned long long)tq_mine);
-            }
-            add_rows_chunk<kChunkSteps>(rows, gv);
-            const bool over = tq_mine && mybase + tq_mine > a.cap_voters;
-            const bool any_over = __any_sync(0xffffffffu, over);
-            steps += kChunkSteps;
-            if (steps >= 255 - kChunkSteps) settle();  // byte counters nearly full
-            const uint32_t excl = inc - cnt;
-            if (!any_over) {
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int sh = 8 * quad_byte(q);
-                    const uint32_t tq = (tot >> sh) & 0xffu;
-                    if (!tq) continue;
-                    uint2* dst = vout + __shfl_sync(0xffffffffu, mybase, q) + ((excl >> sh) & 0xffu);
-                    const uint32_t bit = 1u << quad_bit(q);
-                    uint32_t j = 0;
-#pragma unroll
-                    for (int k = 0; k < kChunkSteps; ++k) {
-                        const uint32_t keep = (kw[k] & bit) ? 1u : 0u;
-                        st_pred_v2(dst + j, keep, rec[k].x, ci[q]);
-                        j += keep;
-                    }
-                }
-            } else {
-                // the stream overflows its capacity (the host reruns with more room)
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int sh = 8 * quad_byte(q);
-                    const uint32_t tq = (tot >> sh) & 0xffu;
-                    if (!tq) continue;
-                    uint64_t p = __shfl_sync(0xffffffffu, mybase, q) + ((excl >> sh) & 0xffu);
-                    const uint32_t bit = 1u << quad_bit(q);
-#pragma unroll
-                    for (int k = 0; k < kChunkSteps; ++k) {
-                        if (kw[k] & bit) {
-                            if (p < a.cap_voters) vout[p] = make_uint2(rec[k].x, ci[q]);
-                            ++p;
-                        }
-                    }
-                }
-            }
+            run_chunk(rec, true, r_first);
             continue;
         }
 
-        // ---- more than one parent in the chunk (a run ends inside it), or
-        // records without a parent: the same vectorised body once per parent,
-        // a record taking part when its parent is the run's.  Parent indices
-        // never decrease along the stream (segments are laid out in region
-        // order; records without a parent carry the largest value), so the
-        // runs are taken in order by a warp minimum over the larger parents.
-        {
-            uint32_t m = rec[0].y;
+        // ---- more than one parent in the chunk (a run ends inside it), the
+        // stream's partial last chunk, or records without a parent: the same
+        // body once per parent, a record taking part when its parent is the
+        // run's.  Parent indices never decrease along the stream (segments
+        // are laid out in region order; records without a parent carry the
+        // largest value), so the runs are taken in order by a warp minimum
+        // over the larger parents.
+        uint32_t m = rec[0].y;
 #pragma unroll
-            for (int k = 1; k < kChunkSteps; ++k) m = min(m, rec[k].y);
-            uint32_t P = __reduce_min_sync(0xffffffffu, m);
+        for (int k = 1; k < kChunkSteps; ++k) m = min(m, rec[k].y);
+        uint32_t P = __reduce_min_sync(0xffffffffu, m);
 #pragma unroll 1
-            while (P != kNoRegion) {
-                if (P != cur) {
-                    settle();
-                    start_run(P);
-                }
-                if (cg.wspread == 0u) {
-                    // no child keeps a list (the children's level is the unit's last
-                    // but one): the voters are only counted for the grandchildren
-                        uint32_t gc[kChunkSteps];
-#pragma unroll
-                    for (int k = 0; k < kChunkSteps; ++k) {
-                        const uint32_t live = rec[k].y == P ? 0xffffffffu : 0u;
-                        gc[k] = classify<I>(cg, rec[k].x, live).gv;
-                    }
-                    add_rows_chunk<kChunkSteps>(rows, gc);
-                    steps += kChunkSteps;
-                    if (steps >= 255 - kChunkSteps) settle();  // byte counters nearly full
-                } else {
-                uint32_t kw[kChunkSteps], gv[kChunkSteps];
-                uint32_t cnt = 0;
-    #pragma unroll
-                for (int k = 0; k < kChunkSteps; ++k) {
-                    const uint32_t live = rec[k].y == P ? 0xffffffffu : 0u;
-                    const Classified<I> c = classify<I>(cg, rec[k].x, live);
-                    kw[k] = c.kw;
-                    gv[k] = c.gv;
-                    cnt += quad_counts(kw[k]);
-                }
-                // reserve each kept child's slots for the whole chunk (one atomic
-                // per child): per-lane counts per quadrant as byte fields, one warp
-                // scan for all four quadrants, then every lane writes its kept
-                // voters of a quadrant to consecutive slots
-                uint32_t inc = cnt;
-    #pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const uint32_t o = __shfl_up_sync(0xffffffffu, inc, off);
-                    if (lane >= off) inc += o;
-                }
-                const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
-                // lanes 0..3 reserve the slots of quadrant `lane` in parallel; the
-                // grandchild counts are added while the reservations are in flight
-                unsigned long long mybase = 0;
-                const uint32_t tq_mine = lane < 4 ? (tot >> (8 * quad_byte_rt(lane))) & 0xffu : 0u;
-                if (tq_mine) {
-                    const uint32_t cq = lane == 0 ? ci[0] : lane == 1 ? ci[1] : lane == 2 ? ci[2] : ci[3];
-                    if (HHT_CHECK_INDEX(cq, n_chi, a.status)) mybase = atomicAdd(&a.cursor[cq], (unsigned long long)tq_mine);
-                }
-                    add_rows_chunk<kChunkSteps>(rows, gv);
-                const bool over = tq_mine && mybase + tq_mine > a.cap_voters;
-                const bool any_over = __any_sync(0xffffffffu, over);
-                steps += kChunkSteps;
-                if (steps >= 255 - kChunkSteps) settle();  // byte counters nearly full
-                const uint32_t excl = inc - cnt;
-                if (!any_over) {
-    #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int sh = 8 * quad_byte(q);
-                        const uint32_t tq = (tot >> sh) & 0xffu;
-                        if (!tq) continue;
-                        uint2* dst = vout + __shfl_sync(0xffffffffu, mybase, q) + ((excl >> sh) & 0xffu);
-                        const uint32_t bit = 1u << quad_bit(q);
-                        uint32_t j = 0;
-    #pragma unroll
-                        for (int k = 0; k < kChunkSteps; ++k) {
-                            const uint32_t keep = (kw[k] & bit) ? 1u : 0u;
-                            st_pred_v2(dst + j, keep, rec[k].x, ci[q]);
-                            j += keep;
-                        }
-                    }
-                } else {
-                    // the stream overflows its capacity (the host reruns with more room)
-    #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int sh = 8 * quad_byte(q);
-                        const uint32_t tq = (tot >> sh) & 0xffu;
-                        if (!tq) continue;
-                        uint64_t p = __shfl_sync(0xffffffffu, mybase, q) + ((excl >> sh) & 0xffu);
-                        const uint32_t bit = 1u << quad_bit(q);
-    #pragma unroll
-                        for (int k = 0; k < kChunkSteps; ++k) {
-                            if (kw[k] & bit) {
-                                if (p < a.cap_voters) vout[p] = make_uint2(rec[k].x, ci[q]);
-                                ++p;
-                            }
-                        }
-                    }
-                }
-                }
-                m = kNoRegion;
-#pragma unroll
-                for (int k = 0; k < kChunkSteps; ++k) m = min(m, rec[k].y > P ? rec[k].y : kNoRegion);
-                P = __reduce_min_sync(0xffffffffu, m);
+        while (P != kNoRegion) {
+            if (P != cur) {
+                settle();
+                start_run(P);
             }
+            run_chunk(rec, false, P);
+            m = kNoRegion;
+#pragma unroll
+            for (int k = 0; k < kChunkSteps; ++k) m = min(m, rec[k].y > P ? rec[k].y : kNoRegion);
+            P = __reduce_min_sync(0xffffffffu, m);
         }
     }
     settle();

@@ -224,6 +224,7 @@ int noalloc_body(const hht_point* points, int64_t n, int32_t W, int32_t H, int32
         a.tile_flags = (uint32_t*)(base + flag_off);
         a.tile_data = (uint64_t*)(base + data_off);
         a.status = d_status;
+        a.img_err = d_img_err;
         a.cap_children = 4 * P;
         a.cap_leaves = HHT_NOALLOC_MAX_LEAVES;
         a.cap_voters = UINT64_MAX;

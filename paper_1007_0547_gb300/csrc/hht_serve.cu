@@ -39,6 +39,7 @@ struct Request {
     hht_image im{};
     int slot = -1;
     int64_t t0 = 0;
+    int64_t blocked_since = -1;  // first step at which it did not fit the budget
     uint64_t est = 0;
     bool done = false;
     bool range_error = false;
@@ -51,6 +52,11 @@ struct Request {
 
 struct ServeState {
     static constexpr int kSlots = 1024;  // requests in flight at most (two units each)
+    // A waiting request that does not fit the memory budget is passed over by
+    // later ones that do for at most this many steps; after that nothing is
+    // admitted until it fits (the running requests finish within 24 steps).
+    static constexpr int64_t kBypassSteps = 12;
+    static constexpr size_t kAdmitScan = 256;  // waiting requests examined per step
 
     std::mutex mu;
     uint64_t next_ticket = 1;
@@ -70,6 +76,9 @@ struct ServeState {
     DevBuf units, stats, infos, status, leaf_total, img_err, scan, pts, img_start, img_unit;
     DevBuf rec[2], preg[2], cnt[2], vox[2], cursors, leaves, sel_flags, sel_data;
     hht_ctx* ctx = nullptr;  // for the per-request leaf buffers
+    // hht_poll's copies run here, so that a poll does not wait for the step
+    // running on the context's stream
+    cudaStream_t poll_stream = nullptr;
 };
 
 // Device memory for one finished request's leaves: the caller's allocator
@@ -99,6 +108,7 @@ void serve_destroy(ServeState* s) {
     if (s->ctx)
         for (auto& kv : s->reqs) result_free(s->ctx, kv.second.dev_leaves, kv.second.dev_bytes);
     if (s->ctx) cudaStreamSynchronize(s->ctx->stream);
+    if (s->poll_stream) cudaStreamDestroy(s->poll_stream);
     delete s;
 }
 
@@ -154,7 +164,9 @@ int engine_init(hht_ctx* c, ServeState* S) {
     } else {
         size_t fr = 0, tot = 0;
         cudaMemGetInfo(&fr, &tot);
-        S->budget = (uint64_t)(0.5 * (double)fr);
+        // the estimates already carry 20 % headroom over the dense regime's
+        // streams; what is left covers result buffers and allocation slack
+        S->budget = (uint64_t)(0.7 * (double)fr);
     }
     S->init = true;
     return HHT_OK;
@@ -162,17 +174,26 @@ int engine_init(hht_ctx* c, ServeState* S) {
 
 // Admit waiting requests into the current step.
 int engine_admit(hht_ctx* c, ServeState* S) {
+    // Waiting requests are taken in arrival order while they fit the budget
+    // (the first one always fits an idle engine).  One that does not fit is
+    // passed over by later ones that do, so that a large request at the head
+    // does not hold small ones back, until it has waited kBypassSteps steps.
     std::vector<uint64_t> adm;
     {
         std::lock_guard<std::mutex> lk(S->mu);
-        while (!S->waiting.empty() && !S->free_slots.empty()) {
-            Request& r = S->reqs[S->waiting.front()];
-            if (!S->order.empty() || !adm.empty()) {
-                if (S->in_flight_bytes + r.est > S->budget) break;
+        size_t seen = 0;
+        for (auto it = S->waiting.begin();
+             it != S->waiting.end() && adm.size() < S->free_slots.size() && seen < ServeState::kAdmitScan; ++seen) {
+            Request& r = S->reqs[*it];
+            if ((S->order.empty() && adm.empty()) || S->in_flight_bytes + r.est <= S->budget) {
+                adm.push_back(*it);
+                S->in_flight_bytes += r.est;
+                it = S->waiting.erase(it);
+                continue;
             }
-            adm.push_back(S->waiting.front());
-            S->waiting.pop_front();
-            S->in_flight_bytes += r.est;
+            if (r.blocked_since < 0) r.blocked_since = S->step;
+            if (S->step - r.blocked_since >= ServeState::kBypassSteps) break;
+            ++it;
         }
     }
     if (adm.empty()) return HHT_OK;
@@ -368,6 +389,7 @@ int engine_step(hht_ctx* c, ServeState* S) {
         a.tile_flags = (uint32_t*)S->sel_flags.p;
         a.tile_data = (uint64_t*)S->sel_data.p;
         a.status = (DeviceStatus*)S->status.p;
+        a.img_err = (const uint32_t*)S->img_err.p;
         a.cap_children = 4 * P;
         a.cap_leaves = 4 * P;
         a.cap_voters = UINT64_MAX;
@@ -476,47 +498,63 @@ int hht_done_tickets(hht_ctx* c, uint64_t* tickets, uint64_t capacity, uint64_t*
 int hht_poll(hht_ctx* c, uint64_t ticket, hht_result* out) {
     if (!c || !out) return HHT_E_ARG;
     ServeState* s = serve_of(c);
-    std::lock_guard<std::mutex> lk(s->mu);
-    auto it = s->reqs.find(ticket);
-    if (it == s->reqs.end()) return HHT_E_UNKNOWN_TICKET;
-    Request& r = it->second;
-    if (!r.done) return HHT_E_PENDING;
     hht_leaf* dst = out->leaves;
     const uint64_t cap = out->leaf_capacity;
-    hht_result res = r.res;
-    res.leaves = dst;
-    res.leaf_capacity = cap;
-    int rc = r.status;
-    if (rc == HHT_OK) {
-        if (res.n_leaves > cap || (res.n_leaves > 0 && !dst)) {
+    hht_result res{};
+    int rc = HHT_OK;
+    void* src = nullptr;
+    uint64_t src_bytes = 0;
+    cudaStream_t ps = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        auto it = s->reqs.find(ticket);
+        if (it == s->reqs.end()) return HHT_E_UNKNOWN_TICKET;
+        Request& r = it->second;
+        if (!r.done) return HHT_E_PENDING;
+        res = r.res;
+        res.leaves = dst;
+        res.leaf_capacity = cap;
+        rc = r.status;
+        if (rc == HHT_OK && (res.n_leaves > cap || (res.n_leaves > 0 && !dst))) {
             out->n_leaves = res.n_leaves;
             return HHT_E_CAPACITY;  // the ticket stays valid: poll again with a larger buffer
         }
-        if (res.n_leaves) {
+        src = r.dev_leaves;
+        src_bytes = r.dev_bytes;
+        if (rc == HHT_OK && res.n_leaves && !s->poll_stream) {
             cudaSetDevice(c->device);
-            if (cudaMemcpy(dst, r.dev_leaves, r.dev_bytes, cudaMemcpyDefault) != cudaSuccess) {
+            if (cudaStreamCreateWithFlags(&s->poll_stream, cudaStreamNonBlocking) != cudaSuccess) {
                 cudaGetLastError();
-                rc = HHT_E_CUDA;
+                s->poll_stream = nullptr;
+                return HHT_E_CUDA;  // nothing released: the poll can be repeated
             }
         }
+        ps = s->poll_stream;
+        // the ticket is released here; its leaf buffer now belongs to this call
+        s->reqs.erase(it);
+        // A client that polls without draining hht_done_tickets leaves polled
+        // tickets on the completion list: drop them once they outnumber the
+        // live requests two to one, so the list stays bounded (amortised
+        // O(log n) per request, since after a pass it holds live tickets only).
+        if (s->finished.size() > 2 * s->reqs.size() + 64) {
+            std::deque<uint64_t> live;
+            for (uint64_t t : s->finished)
+                if (s->reqs.count(t)) live.push_back(t);
+            s->finished.swap(live);
+        }
     }
+    // The copy needs no lock: the engine finished writing the buffer (and
+    // synchronised) before it marked the request done.
+    if (src) cudaSetDevice(c->device);
+    if (rc == HHT_OK && res.n_leaves) {
+        if (copy_out_on(c, dst, src, src_bytes, ps) != HHT_OK || cudaStreamSynchronize(ps) != cudaSuccess) {
+            cudaGetLastError();
+            rc = HHT_E_CUDA;
+        }
+    }
+    if (src) result_free(c, src, src_bytes);
     *out = res;
     out->status = rc;
-    if (r.dev_leaves) {
-        cudaSetDevice(c->device);
-        result_free(c, r.dev_leaves, r.dev_bytes);
-    }
-    s->reqs.erase(it);
-    // A client that polls without draining hht_done_tickets leaves polled
-    // tickets on the completion list: drop them once they outnumber the live
-    // requests two to one, so the list stays bounded (amortised O(log n) per
-    // request, since after a pass it holds live tickets only).
-    if (s->finished.size() > 2 * s->reqs.size() + 64) {
-        std::deque<uint64_t> live;
-        for (uint64_t t : s->finished)
-            if (s->reqs.count(t)) live.push_back(t);
-        s->finished.swap(live);
-    }
     return rc;
 }
 

@@ -298,11 +298,18 @@ class Context:
         except Exception:
             pass
 
-    def _alloc_leaves(self, cap: int, on_device: bool):
+    def _alloc_leaves(self, cap: int, on_device: bool, pinned: bool = False):
         import torch
         if on_device:
             buf = torch.empty((max(cap, 1), 4), dtype=torch.int32, device=f"cuda:{self.device}")
             return buf, buf.data_ptr()
+        if pinned and cap > 0:
+            # page-locked memory from PyTorch's caching host allocator (reused
+            # across calls): the device -> host copy runs at link speed instead
+            # of through the driver's staging of pageable memory; the numpy
+            # view keeps the tensor alive
+            t = torch.empty((cap, 4), dtype=torch.int32, pin_memory=True)
+            return t.numpy(), t.data_ptr()
         buf = np.empty((max(cap, 1), 4), dtype=np.int32)
         return buf, buf.ctypes.data
 
@@ -714,7 +721,7 @@ class Context:
         buf, ptr = self._alloc_leaves(0, leaves_on_device)
         while rc == HHT_E_CAPACITY:
             cap = int(r.n_leaves)
-            buf, ptr = self._alloc_leaves(cap, leaves_on_device)
+            buf, ptr = self._alloc_leaves(cap, leaves_on_device, pinned=True)
             r = _Result()
             r.leaves = ptr
             r.leaf_capacity = cap

@@ -140,6 +140,64 @@ def test_small_budget_admits_gradually(hht):
     ctx.close()
 
 
+def _admission_estimate(n, depth):
+    """The engine's admission estimate of one request (bytes): the voter
+    streams of its two deepest written levels in the dense regime, both
+    halves, with 20 % headroom, plus its points and a fixed part."""
+    dense = n if depth < 3 else 1.25 * n * (2.0 ** (depth - 2) + 2.0 ** (depth - 3))
+    return int(2.0 * 8.0 * dense * 1.2 + 64.0 * n + (1 << 16))
+
+
+def test_small_requests_pass_a_blocked_large_one_until_it_has_waited(hht):
+    """A large request B that does not fit the budget beside a running one
+    (A) is passed over by a small one (C) that does, which finishes first.
+    Once B has waited 12 steps, a small request D that arrives is held back
+    until B is admitted (after A finishes), although D would fit beside A.
+    One progress() call is one step; a request of depth d finishes d steps
+    after its admission."""
+    rng = np.random.default_rng(20261204)
+    big = (rng.integers(0, 64, size=(200, 2)).astype(np.int16), 64, 64, 20, 4)  # in flight for 20 steps
+    small = (rng.integers(0, 32, size=(10, 2)).astype(np.int16), 32, 32, 3, 1)
+    est_big, est_small = _admission_estimate(200, 20), _admission_estimate(10, 3)
+    budget = est_big + 2 * est_small + (1 << 20)
+    assert budget < 2 * est_big
+
+    class _Im:
+        def __init__(self, t):
+            self.points, self.W, self.H, self.depth, self.T = t
+
+    want = _alone(hht, [_Im(big), _Im(small)])
+    ctx = hht.Context(device=0, mem_budget=budget)
+    try:
+        ta = ctx.submit(*big)
+        ctx.progress()                      # step 0: A admitted (the engine was idle)
+        tb = ctx.submit(*big)
+        ctx.progress()                      # step 1: B does not fit beside A
+        tc = ctx.submit(*small)
+        done_at, got = {}, {}
+        td = None
+        for step in range(2, 200):
+            if step == 13:                  # B has waited 12 steps: nothing passes it now
+                td = ctx.submit(*small)
+            ctx.progress()
+            for t in ctx.done_tickets():
+                done_at[t] = step
+                got[t] = ctx.poll(t)
+            if len(got) == 4:
+                break
+        assert len(got) == 4
+        assert done_at[tc] == 4             # admitted at step 2 beside A
+        assert done_at[ta] == 19
+        assert done_at[td] == 22            # admitted with B at step 20, not at step 13
+        assert done_at[tb] == 39
+        for t in (ta, tb):
+            _same(got[t], want[0])
+        for t in (tc, td):
+            _same(got[t], want[1])
+    finally:
+        ctx.close()
+
+
 def test_bad_request_fails_alone(hht):
     good = synth.plain_128(index=1)
     want = _alone(hht, [good])[0]
