@@ -341,6 +341,40 @@ def single_image_latency(ctx, runs: int = 30):
     return out
 
 
+def run_ncu_case(args, rank):
+    """One small detection for an ncu capture of the pass kernel: 8 images of
+    the 256-image batch (indices 0, 32, ..., 224), level form (one launch per
+    pass), tile shape --tile-shape.  Prints, per pass launch s, the records it
+    reads (the level s-1 stream) and writes (the level s stream), from the
+    detection's statistics: a level's tests are four per voter of a passed
+    parent, and a unit keeps lists of its levels up to depth - 2."""
+    from paper_1007_0547_gb300 import build as hbuild
+    hbuild.build()
+    from paper_1007_0547_gb300 import hht
+    import torch
+    if rank != 0:
+        return
+    imgs = [synth.batch_image(k) for k in range(0, 256, 32)]
+    dev = [(torch.from_numpy(im.points).cuda(), im.W, im.H, im.depth, im.T) for im in imgs]
+    ctx = hht.Context(device=0)
+    ctx.set_batch_mode(hht.BATCH_LEVELS)
+    ctx.set_tuning(args.tile_shape)
+    res = ctx.detect_batch(dev)
+    torch.cuda.synchronize()
+    dmax = max(im.depth for im in imgs)
+    launches = []
+    for s in range(1, dmax):
+        rd = sum(int(r.stats[h, s, 3]) // 4 for r, im in zip(res, imgs) for h in range(2) if s - 1 <= im.depth - 2)
+        wr = sum(int(r.stats[h, s + 1, 3]) // 4 for r, im in zip(res, imgs) for h in range(2) if s <= im.depth - 2)
+        if rd > 0:  # the level form launches no pass over an empty stream
+            launches.append({"launch": len(launches) + 1, "pass": s, "records_read": rd, "records_written": wr,
+                             "algorithmic_bytes": 8 * (rd + wr)})
+    print(json.dumps({"case": "batch8", "images": [k for k in range(0, 256, 32)],
+                      "sides": [im.W for im in imgs], "depths": [im.depth for im in imgs],
+                      "tile_shape": args.tile_shape, "pass_launches": launches}), flush=True)
+    ctx.close()
+
+
 def run_serving(args, rank):
     """The serving leg alone, at --serve-requests and --serve-load."""
     from paper_1007_0547_gb300 import build as hbuild
@@ -381,6 +415,9 @@ def main():
                     help="time only the front-end kernel (Sobel and split) on the 4096x4096 grey image")
     ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--serve-load", type=float, default=0.8, help="offered rate as a fraction of the saturated rate")
+    ap.add_argument("--ncu-case", choices=["batch8"],
+                    help="run one small detection for an ncu capture of the pass kernel and exit")
+    ap.add_argument("--tile-shape", type=int, default=0, help="pass tile shape of --ncu-case")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
@@ -390,6 +427,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.ncu_case:
+        run_ncu_case(args, rank)
         return
     if args.serve:
         run_serving(args, rank)
