@@ -7,13 +7,15 @@
 //
 // GPU form: one warp per (image, half) walks that half's quadtree in the
 // paper's order, with
-//   - an explicit stack (per level: next quadrant, region, list length) in
-//     shared memory;
-//   - one voter list per level in global memory: a child's list is built
-//     from its parent's by the 32 lanes together (exact integer corner signs
-//     on the region's 3 x 3 grid decide the 4-bit codes' votes, in int32 when
-//     log2 L + depth <= 27; a ballot per 32 voters, positions from popc),
-//     skipping removed points;
+//   - an explicit stack in shared memory (per level: next quadrant, region,
+//     its children's list lengths, its votes when entered and the number of
+//     points plotted by then);
+//   - the voters of a region split into its four children's lists once,
+//     when it is entered (exact integer corner signs on the region's 3 x 3
+//     grid decide all four children's votes at once, in int32 when
+//     log2 L + depth <= 27; a ballot per quadrant, positions from popc), so
+//     that a child's list only has to lose the points plotted since, and
+//     while none were, its votes are its length and no pass is needed;
 //   - a removed-point bitmap (one bit per point) read through L2, so that the
 //     warp sees its own atomic updates.
 // Many images and both halves run as independent warps.  Readings (see the
@@ -41,7 +43,7 @@ namespace {
 // One (image, half) of a removal job.
 struct alignas(16) RemovalTask {
     uint64_t pts;        // offset of the image's points (int16 x, y pairs)
-    uint64_t lists;      // offset of (D + 1) voter lists of n entries
+    uint64_t lists;      // offset of 4 D voter lists of n entries (four children per level)
     uint64_t bitmap;     // offset (in 32-bit words) of the removed-point bitmap
     uint64_t leaves;     // offset of the leaf output, `cap` entries
     uint64_t stats;      // offset of [D + 1][4] statistics
@@ -78,8 +80,7 @@ __device__ __forceinline__ int64_t scaled_g(int64_t x, int64_t y, int64_t i, int
 // vertices of the region's 3 x 3 grid (in steps of h from its SW corner):
 // NE child (1,1)-(2,2), NW (0,1)-(1,2), SW (0,0)-(1,1), SE (1,0)-(2,1).
 // I = int32_t when log2 L + depth <= 27 (every vertex value then lies within
-// 2^29).  (All four children per test measured faster than the visited
-// child's two corners alone: 1104 against 1158 ms on the 256-image batch.)
+// 2^29).
 template <typename I>
 __device__ __forceinline__ uint32_t child_crossings(int64_t x, int64_t y, int64_t i0, int64_t j0, int64_t h,
                                                     int64_t L2, int64_t K) {
@@ -100,9 +101,13 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
                                                                  uint64_t* __restrict__ stats_all,
                                                                  uint64_t* __restrict__ leaf_counts,
                                                                  DeviceStatus* status) {
+    // the walk's stack, per level: next quadrant, the region's SW corner, the
+    // lengths of its children's lists, its votes when entered and the
+    // removed-point count at that time
     __shared__ int32_t s_quad[kRemWarps][kMaxDepth + 1];
     __shared__ uint32_t s_i0[kRemWarps][kMaxDepth + 1], s_j0[kRemWarps][kMaxDepth + 1];
-    __shared__ uint32_t s_len[kRemWarps][kMaxDepth + 1];
+    __shared__ uint32_t s_len[kRemWarps][kMaxDepth + 1][4];
+    __shared__ uint32_t s_m[kRemWarps][kMaxDepth + 1], s_rem[kRemWarps][kMaxDepth + 1];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     const int task = blockIdx.x * kRemWarps + w;
@@ -116,27 +121,88 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
     const int64_t n = tk.n, D = tk.D, T = tk.T;
     const int64_t L2 = int64_t(2) << tk.lL, K = int64_t(1) << tk.D;
     const int half = tk.half;
+    // the four children's lists of the region entered at level l
+    auto child_list = [&](int l, int q) { return lists + (uint64_t)(4 * l + q) * (uint64_t)n; };
+
+    // Split the voters of `src` (len entries, or the points 0 .. len - 1 when
+    // src is null) that are not removed into the lists of the four children
+    // of region (i0, j0) of side 2h, kept at level l; lens[q] receive their
+    // lengths.  Returns the number of voters not removed.  `check`: some
+    // entry may have been removed since the list was built (else the bitmap
+    // is not read).  Four groups of 32 entries per iteration: the list
+    // entries, then their bitmap words, then their points are loaded as
+    // independent requests.
+    auto split = [&](const uint32_t* src, uint32_t len, bool check, int l, int64_t i0, int64_t j0, int64_t h,
+                     uint32_t (&lens)[4]) -> uint32_t {
+        constexpr int U = 4;
+        uint32_t alive = 0;
+        lens[0] = lens[1] = lens[2] = lens[3] = 0u;
+        uint32_t* dst[4] = {child_list(l, 0), child_list(l, 1), child_list(l, 2), child_list(l, 3)};
+        for (uint32_t base = 0; base < len; base += 32 * U) {
+            uint32_t v[U], bw[U], xm[U];
+            bool in[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const uint32_t idx = base + 32 * u + lane;
+                in[u] = idx < len;
+                v[u] = in[u] ? (src ? __ldcg(&src[idx]) : idx) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) bw[u] = (in[u] && check) ? __ldcg(&bitmap[v[u] >> 5]) : 0u;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                in[u] = in[u] && ((bw[u] >> (v[u] & 31u)) & 1u) == 0u;  // not removed
+                xm[u] = in[u] ? __ldg(reinterpret_cast<const uint32_t*>(pts) + v[u]) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                uint32_t cross = 0u;
+                if (in[u]) {
+                    const int64_t px = (int16_t)(xm[u] & 0xffffu), py = (int16_t)(xm[u] >> 16);
+                    const int64_t x = half ? py : px, y = half ? px : py;
+                    cross = child_crossings<I>(x, y, i0, j0, h, L2, K);
+                }
+                alive += __popc(__ballot_sync(0xffffffffu, in[u]));
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const bool c = (cross >> q) & 1u;
+                    const uint32_t m = __ballot_sync(0xffffffffu, c);
+                    if (c) dst[q][lens[q] + __popc(m & lt)] = v[u];
+                    lens[q] += __popc(m);
+                }
+            }
+        }
+        return alive;
+    };
 
     // level 0: every line crosses the whole parameter space (points outside
-    // the image fail the image)
+    // the image fail the image); the root's voters are split at once
     for (int64_t k = lane; k < n; k += 32) {
-        lists[k] = (uint32_t)k;
         const int32_t px = pts[2 * k], py = pts[2 * k + 1];
         if (px < 0 || px >= tk.W || py < 0 || py >= tk.H) atomicOr(&status->err, kErrRange);
     }
     for (int64_t k = lane; k < (n + 31) / 32; k += 32) bitmap[k] = 0u;
-    if (lane == 0) {
-        stats[0] = 1;
-        stats[1] = 1;
-        stats[2] = (uint64_t)n;
-        stats[3] = (uint64_t)n;
-        s_quad[w][0] = 0;
-        s_i0[w][0] = 0;
-        s_j0[w][0] = 0;
-        s_len[w][0] = (uint32_t)n;
+    __syncwarp();
+    {
+        uint32_t lens[4];
+        split(nullptr, (uint32_t)n, false, 0, 0, 0, K >> 1, lens);
+        if (lane == 0) {
+            stats[0] = 1;
+            stats[1] = 1;
+            stats[2] = (uint64_t)n;
+            stats[3] = (uint64_t)n;
+            s_quad[w][0] = 0;
+            s_i0[w][0] = 0;
+            s_j0[w][0] = 0;
+            s_m[w][0] = (uint32_t)n;
+            s_rem[w][0] = 0u;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) s_len[w][0][q] = lens[q];
+        }
     }
     __syncwarp();
     uint64_t nleaves = 0;
+    uint32_t removed = 0;  // points plotted so far in this half
     int level = 0;
     // every region is entered once and left after its fourth child, so the
     // walk ends (within tk.max_steps steps)
@@ -157,48 +223,41 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
         const int64_t i0 = (int64_t)s_i0[w][level], j0 = (int64_t)s_j0[w][level];
         const int64_t ci = i0 + ((q == NE || q == SE) ? h : 0);
         const int64_t cj = j0 + ((q == NE || q == NW) ? h : 0);
-        const uint32_t plen = s_len[w][level];
-        const uint32_t* parent = lists + (uint64_t)level * (uint64_t)n;
-        uint32_t* child = lists + (uint64_t)(level + 1) * (uint64_t)n;
-        uint32_t cnt = 0, evaluated = 0;
-        // Every voter not removed yet is tested against the child from its
-        // point (exact integer corner signs on the region's 3 x 3 grid); four
-        // groups of 32 voters per iteration: the list entries, then their
-        // bitmap words, then their points are loaded as independent requests
-        // (the points repeat across a region's four children and stay in L1).
-        constexpr int U = 4;
-        for (uint32_t base = 0; base < plen; base += 32 * U) {
-            uint32_t v[U], bw[U], xm[U];
-            bool in[U];
+        const int cl = level + 1;
+        const uint32_t* src = child_list(level, q);
+        const uint32_t len = s_len[w][level][q];
+        // codes evaluated for this child: the parent's voters not removed by
+        // now, i.e. its votes when entered less the points plotted since
+        // (every one of them was a voter of this parent)
+        const uint32_t evaluated = s_m[w][level] - (removed - s_rem[w][level]);
+        // the child's list was split off when the parent was entered; when
+        // nothing has been plotted since, every entry still votes
+        const bool stale = removed != s_rem[w][level];
+        uint32_t cnt = len;
+        uint32_t lens[4] = {0u, 0u, 0u, 0u};
+        if (cl == D) {
+            // a leaf: its voters not removed are counted
+            if (stale) {
+                cnt = 0;
+                for (uint32_t base = 0; base < len; base += 128) {
+                    uint32_t v[4];
+                    bool in[4];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const uint32_t idx = base + 32 * u + lane;
-                in[u] = idx < plen;
-                v[u] = in[u] ? __ldcg(&parent[idx]) : 0u;
-            }
+                    for (int u = 0; u < 4; ++u) {
+                        in[u] = base + 32 * u + lane < len;
+                        v[u] = in[u] ? __ldcg(&src[base + 32 * u + lane]) : 0u;
+                    }
 #pragma unroll
-            for (int u = 0; u < U; ++u) bw[u] = in[u] ? __ldcg(&bitmap[v[u] >> 5]) : 0u;
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                in[u] = in[u] && ((bw[u] >> (v[u] & 31u)) & 1u) == 0u;  // not removed
-                xm[u] = in[u] ? __ldg(reinterpret_cast<const uint32_t*>(pts) + v[u]) : 0u;
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                bool cross = false;
-                if (in[u]) {
-                    const int64_t px = (int16_t)(xm[u] & 0xffffu), py = (int16_t)(xm[u] >> 16);
-                    const int64_t x = half ? py : px, y = half ? px : py;
-                    cross = ((child_crossings<I>(x, y, i0, j0, h, L2, K) >> q) & 1u) != 0u;
+                    for (int u = 0; u < 4; ++u) {
+                        if (in[u]) in[u] = ((__ldcg(&bitmap[v[u] >> 5]) >> (v[u] & 31u)) & 1u) == 0u;
+                        cnt += __popc(__ballot_sync(0xffffffffu, in[u]));
+                    }
                 }
-                evaluated += __popc(__ballot_sync(0xffffffffu, in[u]));
-                const uint32_t m = __ballot_sync(0xffffffffu, cross);
-                if (cross) child[cnt + __popc(m & lt)] = v[u];
-                cnt += __popc(m);
             }
+        } else {
+            cnt = split(src, len, stale, cl, ci, cj, h >> 1, lens);
         }
         __syncwarp();
-        const int cl = level + 1;
         if (lane == 0) {
             stats[4 * cl + 0] += 1;
             stats[4 * cl + 2] += cnt;
@@ -221,10 +280,14 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
                     }
                 }
                 ++nleaves;
-                for (uint32_t k = lane; k < cnt; k += 32) {
-                    const uint32_t v = __ldcg(&child[k]);
+                // the same voters as counted (nothing was removed in between);
+                // an entry removed earlier keeps its bit, so every entry's bit
+                // is set
+                for (uint32_t k = lane; k < len; k += 32) {
+                    const uint32_t v = __ldcg(&src[k]);
                     atomicOr(&bitmap[v >> 5], 1u << (v & 31u));
                 }
+                removed += cnt;
                 __threadfence();
                 __syncwarp();
             } else {
@@ -232,7 +295,10 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
                     s_quad[w][cl] = 0;
                     s_i0[w][cl] = (uint32_t)ci;
                     s_j0[w][cl] = (uint32_t)cj;
-                    s_len[w][cl] = cnt;
+                    s_m[w][cl] = cnt;
+                    s_rem[w][cl] = removed;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) s_len[w][cl][k] = lens[k];
                 }
                 __syncwarp();
                 level = cl;
@@ -318,7 +384,7 @@ int run_removal(hht_ctx* c, const hht_image* im, int count, hht_result* outs, ui
             t.D = im[g].depth;
             t.T = im[g].T;
             t.half = h;
-            lists_len += (uint64_t)(im[g].depth + 1) * std::max<uint64_t>(n, 1);
+            lists_len += (uint64_t)4 * im[g].depth * std::max<uint64_t>(n, 1);  // four children's lists per level
             bitmap_len += (n + 31) / 32 + 1;
             leaves_len += t.cap;
             stats_len += (uint64_t)(im[g].depth + 1) * 4;
