@@ -16,6 +16,9 @@
 //     log2 L + depth <= 27; a ballot per quadrant, positions from popc), so
 //     that a child's list only has to lose the points plotted since, and
 //     while none were, its votes are its length and no pass is needed;
+//   - the split of a region two levels above the leaves also counting its 16
+//     grandchildren, so that a child one level above the leaves is split (and
+//     entered) only when one of its leaves can pass;
 //   - a removed-point bitmap (one bit per point) read through L2, so that the
 //     warp sees its own atomic updates.
 // Many images and both halves run as independent warps.  Readings (see the
@@ -92,6 +95,34 @@ __device__ __forceinline__ uint32_t child_crossings(int64_t x, int64_t y, int64_
            ((g00 < 0 && g11 >= 0) ? 4u : 0u) | ((g10 < 0 && g21 >= 0) ? 8u : 0u);
 }
 
+// The 16 grandchildren of region (i0, j0) of side 4g (cells of side g) that
+// the line of point (x, y) crosses: bit 4a + b for the cell a steps of g east
+// and b north of the region's SW corner, by the same SW / NE corner test on
+// the region's 5 x 5 grid.
+template <typename I>
+__device__ __forceinline__ uint32_t grand_crossings(int64_t x, int64_t y, int64_t i0, int64_t j0, int64_t g,
+                                                    int64_t L2, int64_t K) {
+    const I g00 = (I)scaled_g(x, y, i0, j0, L2, K);
+    const I di = (I)(2 * x * g), dj = (I)(2 * L2 * g);
+    uint32_t bits = 0u;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const I sw = g00 + (I)a * di + (I)b * dj;
+            if (sw < 0 && sw + di + dj >= 0) bits |= 1u << (4 * a + b);
+        }
+    }
+    return bits;
+}
+
+// Grandchild cell (bit of grand_crossings) of leaf quadrant q2 of child quadrant q.
+__device__ __forceinline__ int grand_cell(int q, int q2) {
+    const int e = (q == NE || q == SE) ? 2 : 0, nn = (q == NE || q == NW) ? 2 : 0;
+    const int e2 = (q2 == NE || q2 == SE) ? 1 : 0, n2 = (q2 == NE || q2 == NW) ? 1 : 0;
+    return 4 * (e + e2) + (nn + n2);
+}
+
 template <typename I>
 __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTask* __restrict__ tasks, int ntasks,
                                                                  const int16_t* __restrict__ pts_all,
@@ -108,6 +139,9 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
     __shared__ uint32_t s_i0[kRemWarps][kMaxDepth + 1], s_j0[kRemWarps][kMaxDepth + 1];
     __shared__ uint32_t s_len[kRemWarps][kMaxDepth + 1][4];
     __shared__ uint32_t s_m[kRemWarps][kMaxDepth + 1], s_rem[kRemWarps][kMaxDepth + 1];
+    // votes of the 16 grandchildren (the leaves) of the region last split at
+    // level depth - 2, counted in its split
+    __shared__ uint32_t s_g[kRemWarps][16];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     const int task = blockIdx.x * kRemWarps + w;
@@ -129,13 +163,17 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
     // of region (i0, j0) of side 2h, kept at level l; lens[q] receive their
     // lengths.  Returns the number of voters not removed.  `check`: some
     // entry may have been removed since the list was built (else the bitmap
-    // is not read).  Four groups of 32 entries per iteration: the list
-    // entries, then their bitmap words, then their points are loaded as
+    // is not read).  `grand`: the votes of the region's 16 grandchildren are
+    // counted too, into s_g.  Four groups of 32 entries per iteration: the
+    // list entries, then their bitmap words, then their points are loaded as
     // independent requests.
     auto split = [&](const uint32_t* src, uint32_t len, bool check, int l, int64_t i0, int64_t j0, int64_t h,
-                     uint32_t (&lens)[4]) -> uint32_t {
+                     uint32_t (&lens)[4], bool grand) -> uint32_t {
         constexpr int U = 4;
         uint32_t alive = 0;
+        uint32_t gc[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) gc[k] = 0u;
         lens[0] = lens[1] = lens[2] = lens[3] = 0u;
         uint32_t* dst[4] = {child_list(l, 0), child_list(l, 1), child_list(l, 2), child_list(l, 3)};
         for (uint32_t base = 0; base < len; base += 32 * U) {
@@ -156,11 +194,16 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                uint32_t cross = 0u;
+                uint32_t cross = 0u, gbits = 0u;
                 if (in[u]) {
                     const int64_t px = (int16_t)(xm[u] & 0xffffu), py = (int16_t)(xm[u] >> 16);
                     const int64_t x = half ? py : px, y = half ? px : py;
                     cross = child_crossings<I>(x, y, i0, j0, h, L2, K);
+                    if (grand) gbits = grand_crossings<I>(x, y, i0, j0, h >> 1, L2, K);
+                }
+                if (grand) {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) gc[k] += __popc(__ballot_sync(0xffffffffu, (gbits >> k) & 1u));
                 }
                 alive += __popc(__ballot_sync(0xffffffffu, in[u]));
 #pragma unroll
@@ -171,6 +214,10 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
                     lens[q] += __popc(m);
                 }
             }
+        }
+        if (grand && lane == 0) {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) s_g[w][k] = gc[k];
         }
         return alive;
     };
@@ -185,7 +232,7 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
     __syncwarp();
     {
         uint32_t lens[4];
-        split(nullptr, (uint32_t)n, false, 0, 0, 0, K >> 1, lens);
+        split(nullptr, (uint32_t)n, false, 0, 0, 0, K >> 1, lens, D == 2);
         if (lane == 0) {
             stats[0] = 1;
             stats[1] = 1;
@@ -254,8 +301,16 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
                     }
                 }
             }
+        } else if (cl == D - 1 && !stale) {
+            // its leaves' votes were counted when its parent was split, and
+            // nothing was plotted since: its own split is needed only when one
+            // of them can pass (it is then entered)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) lens[k] = s_g[w][grand_cell(q, k)];
+            if (max(max(lens[0], lens[1]), max(lens[2], lens[3])) >= (uint32_t)T && len >= (uint32_t)T)
+                split(src, len, false, cl, ci, cj, h >> 1, lens, false);
         } else {
-            cnt = split(src, len, stale, cl, ci, cj, h >> 1, lens);
+            cnt = split(src, len, stale, cl, ci, cj, h >> 1, lens, cl == D - 2);
         }
         __syncwarp();
         if (lane == 0) {
@@ -290,6 +345,16 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
                 removed += cnt;
                 __threadfence();
                 __syncwarp();
+            } else if (cl == D - 1 && max(max(lens[0], lens[1]), max(lens[2], lens[3])) < (uint32_t)T) {
+                // no leaf under this region can reach T, so none is accepted and
+                // nothing is plotted while its four leaves are tested: each one's
+                // votes are its list's length and its evaluated codes are this
+                // region's votes, so the region is not entered
+                if (lane == 0) {
+                    stats[4 * D + 0] += 4;
+                    stats[4 * D + 2] += (uint64_t)lens[0] + lens[1] + lens[2] + lens[3];
+                    stats[4 * D + 3] += 4ull * cnt;
+                }
             } else {
                 if (lane == 0) {
                     s_quad[w][cl] = 0;
