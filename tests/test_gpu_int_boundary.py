@@ -105,3 +105,20 @@ def test_batch_mixing_both_sides_of_the_switch(hht, side, depth):
             assert np.array_equal(r.leaves_numpy(), want.leaves) and np.array_equal(r.stats, want.stats)
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("side,depth", CASES)
+def test_removal_on_both_sides_of_the_switch(hht, side, depth):
+    """The solution() walk decides its children and grandchildren with the
+    same corner signs, in int32 at 27 and int64 at 28."""
+    pts = _points(side, 7100 + depth)
+    ctx = hht.Context(device=0)
+    try:
+        for T in _thresholds(side):
+            got, plotted = ctx.detect_removal(pts, side, side, depth, T)
+            want, want_plotted = oracle.detect_removal(pts, side, side, depth, T)
+            assert np.array_equal(got.leaves_numpy(), want.leaves), (side, depth, T)
+            assert np.array_equal(got.stats, want.stats), (side, depth, T)
+            assert np.array_equal(plotted, want_plotted), (side, depth, T)
+    finally:
+        ctx.close()

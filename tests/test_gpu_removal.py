@@ -44,6 +44,14 @@ def test_removal_random_shapes(ctx, seed):
     _check(ctx, synth.random_small(83000 + seed, max_side=300, max_n=2500, max_depth=9, max_T=12))
 
 
+@pytest.mark.parametrize("k", [13, 160])
+def test_removal_heaviest_batch_images(ctx, k):
+    """Two of the batch's slowest walks at full size (sides 2021 and 2023,
+    depth 11): many accepted cells, so children's lists go stale at every
+    depth and the leaves' counts taken two levels up are often overruled."""
+    _check(ctx, synth.batch_image(k))
+
+
 def test_removal_plain_1024(ctx):
     _check(ctx, synth.plain_1024())
 
