@@ -134,7 +134,12 @@ def edge_points(W: int, H: int, segs: np.ndarray, noise: float, st: Stream) -> n
     m = int(np.floor(m_exact + st.floats(1)[0]))
     if m > 0:
         pix.append(st.ints(0, W * H - 1, m))
-    lin = np.unique(np.concatenate(pix))
+    # the distinct pixel indices in increasing order (a mask of the image:
+    # the same result as np.unique, without its hashing)
+    mask = np.zeros(W * H, dtype=bool)
+    for part in pix:
+        mask[part] = True
+    lin = np.flatnonzero(mask)
     pts = np.empty((lin.size, 2), dtype=np.int16)
     pts[:, 0] = (lin % W).astype(np.int16)
     pts[:, 1] = (lin // W).astype(np.int16)
