@@ -514,6 +514,7 @@ struct GraphCaps {
     uint64_t rec[2] = {1, 1};  // region records per level (even / odd levels)
     uint64_t cursors = 1, tiles = 1, leaves = 0;
     uint64_t bytes = 0;
+    std::vector<uint64_t> lvl_vox, lvl_rec;  // the bounds of each level
 };
 
 uint64_t sat_add(uint64_t a, uint64_t b) { return a > UINT64_MAX - b ? UINT64_MAX : a + b; }
@@ -540,6 +541,8 @@ bool graph_caps(const Wave& w, GraphCaps& cap) {
         }
         leaves = sat_add(leaves, std::min<uint64_t>(1ull << (2 * U.D), votes(U.D) / (uint64_t)U.T));
     }
+    cap.lvl_vox = vox;
+    cap.lvl_rec = rec;
     for (int l = 0; l <= w.Dmax; ++l) {
         cap.vox[l & 1] = std::max(cap.vox[l & 1], vox[l]);
         cap.rec[l & 1] = std::max(cap.rec[l & 1], rec[l]);
@@ -592,16 +595,50 @@ bool size_graph_buffers(hht_ctx* c, const Wave& w, GraphCaps& cap) {
     return true;
 }
 
+// Grids of the graph form's launches, from each level's bounds: a level's
+// selection needs no more blocks than its parents fill tiles, and its pass
+// no more warps than the parents' voter stream holds grabs, so the launches
+// of a small job (or of a large job's first levels) are small.  Every kernel
+// takes its work dynamically, so any grid of at least these sizes gives the
+// same result: a captured graph whose grids cover a job's is replayed for
+// it, and a new one is captured with each grid rounded up to a power of two
+// (at most the full grid), so that jobs of similar size share it.
+// Layout: [stage, sel[1..Dmax], pass[1..Dmax]].
+std::vector<int> graph_grids(const hht_ctx* c, const Wave& w, const GraphCaps& cap) {
+    const int shape = w.i64 ? 0 : c->pass_shape;
+    const uint64_t occ = (uint64_t)(w.i64 ? c->occ_pass64 : c->occ_shape[shape]);
+    const uint64_t warps_per_block = (uint64_t)pass_threads(w.i64, shape) / 32;
+    auto fit = [](uint64_t want, uint64_t most) {
+        uint64_t p = 1;
+        while (p < want && p < most) p <<= 1;
+        return (int)std::min(p, most);
+    };
+    std::vector<int> g(1 + 2 * (size_t)w.Dmax, 1);
+    g[0] = fit((w.total + 255) / 256, (uint64_t)c->num_sms * 8);
+    for (int s = 1; s <= w.Dmax; ++s) {
+        g[s] = fit((cap.lvl_rec[s - 1] + kSelTile - 1) / kSelTile, (uint64_t)c->num_sms * c->occ_select);
+        const uint64_t grabs = (cap.lvl_vox[s - 1] + kPassMinGrab - 1) / kPassMinGrab;
+        g[w.Dmax + s] = fit((grabs + warps_per_block - 1) / warps_per_block, (uint64_t)c->num_sms * occ);
+    }
+    return g;
+}
+
+bool grids_cover(const std::vector<int>& have, const std::vector<int>& need) {
+    if (have.size() != need.size()) return false;
+    for (size_t k = 0; k < need.size(); ++k)
+        if (have[k] < need[k]) return false;
+    return true;
+}
+
 // Launch the graph form's kernels on the context's stream: the stage kernel
 // (sizes from the JobDims in device memory), then for every level the
 // selection and the pass, all with fixed arguments; every kernel reads the
 // sizes of its level from the level totals that the previous selection wrote.
 // With `evs`, a pair of events (recorded as graph nodes when capturing)
 // brackets every kernel for hht_profile_*.
-int launch_graph_kernels(hht_ctx* c, const Wave& w, const GraphCaps& cap, cudaStream_t st, bool capturing,
-                         std::vector<hht_ctx::GraphEvent>* evs) {
+int launch_graph_kernels(hht_ctx* c, const Wave& w, const GraphCaps& cap, const std::vector<int>& grids,
+                         cudaStream_t st, bool capturing, std::vector<hht_ctx::GraphEvent>* evs) {
     const int shape = w.i64 ? 0 : c->pass_shape;
-    const int occ = w.i64 ? c->occ_pass64 : c->occ_shape[shape];
     auto record = [&]() -> cudaEvent_t {
         cudaEvent_t e = take_event(c);
         if (capturing) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
@@ -617,8 +654,7 @@ int launch_graph_kernels(hht_ctx* c, const Wave& w, const GraphCaps& cap, cudaSt
     if (launch_stage((const int16_t*)c->pts.p, w.total, (const Unit*)c->units.p, w.count,
                      (const uint64_t*)c->img_start.p, (const uint32_t*)c->img_unit.p, (Voter*)c->vox[0].p,
                      (uint32_t*)c->cnt[0].p, (uint64_t*)c->stats.p, (uint32_t*)c->img_err.p,
-                     (DeviceStatus*)c->status.p, w.i64, st, false, (const JobDims*)c->dims.p,
-                     c->num_sms * 8) != 0)
+                     (DeviceStatus*)c->status.p, w.i64, st, false, (const JobDims*)c->dims.p, grids[0]) != 0)
         return HHT_E_CUDA;
     close(0);
     for (int s = 1; s <= w.Dmax; ++s) {
@@ -631,11 +667,11 @@ int launch_graph_kernels(hht_ctx* c, const Wave& w, const GraphCaps& cap, cudaSt
         a.vin = (const Voter*)c->vox[pi].p;
         a.vout = (Voter*)c->vox[ci].p;
         open();
-        if (launch_select(a, 256, c->num_sms * c->occ_select, st) != 0) return HHT_E_CUDA;
+        if (launch_select(a, 256, grids[s], st) != 0) return HHT_E_CUDA;
         close(1);
         if (s == w.Dmax) break;
         open();
-        if (launch_pass(a, w.i64, c->num_sms * occ, st, shape, false) != 0) return HHT_E_CUDA;
+        if (launch_pass(a, w.i64, grids[w.Dmax + s], st, shape, false) != 0) return HHT_E_CUDA;
         close(2);
     }
     return HHT_OK;
@@ -675,6 +711,7 @@ int run_graph(hht_ctx* c, const Wave& w, const GraphCaps& cap, uint64_t* leaf_to
                             (int64_t)(c->leaves.bytes / sizeof(DevLeaf)), (int64_t)cap.tiles,
                             (int64_t)cap.vox[0], (int64_t)cap.vox[1], (int64_t)cap.rec[0], (int64_t)cap.rec[1]};
     put(vals, sizeof vals);
+    const std::vector<int> grids = graph_grids(c, w, cap);
     auto release = [&](hht_ctx::CachedGraph& cg) {
         for (auto& ev : cg.events) {
             c->ev_pool.push_back(ev.a);
@@ -690,18 +727,29 @@ int run_graph(hht_ctx* c, const Wave& w, const GraphCaps& cap, uint64_t* leaf_to
                              cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone;
     const hht_ctx::CachedGraph* use = nullptr;
     if (can_capture) {
+        // of the graphs of these arguments whose grids cover the job's, the
+        // one with the smallest grids (the most recently used among equals)
         size_t hit = c->graphs.size();
-        for (size_t k = 0; k < c->graphs.size(); ++k)
-            if (c->graphs[k].key == key) hit = k;
+        long long best = -1;
+        for (size_t k = 0; k < c->graphs.size(); ++k) {
+            if (c->graphs[k].key != key || !grids_cover(c->graphs[k].grids, grids)) continue;
+            long long sum = 0;
+            for (int g : c->graphs[k].grids) sum += g;
+            if (best < 0 || sum < best) {
+                best = sum;
+                hit = k;
+            }
+        }
         if (hit < c->graphs.size()) {
             std::rotate(c->graphs.begin(), c->graphs.begin() + hit, c->graphs.begin() + hit + 1);
         } else {
             hht_ctx::CachedGraph cg;
             cg.key = key;
+            cg.grids = grids;
             cudaGraph_t g = nullptr;
             bool ok = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
             if (ok) {
-                const int lr = launch_graph_kernels(c, w, cap, st, true, events ? &cg.events : nullptr);
+                const int lr = launch_graph_kernels(c, w, cap, grids, st, true, events ? &cg.events : nullptr);
                 ok = cudaStreamEndCapture(st, &g) == cudaSuccess && lr == HHT_OK && g != nullptr;
             }
             if (ok) ok = cudaGraphInstantiate(&cg.exec, g, 0) == cudaSuccess;
@@ -719,7 +767,8 @@ int run_graph(hht_ctx* c, const Wave& w, const GraphCaps& cap, uint64_t* leaf_to
                 c->graph_capture_failed = true;  // launch directly from now on
             }
         }
-        if (!c->graphs.empty() && c->graphs.front().key == key) use = &c->graphs.front();
+        if (!c->graphs.empty() && c->graphs.front().key == key && grids_cover(c->graphs.front().grids, grids))
+            use = &c->graphs.front();
     }
     std::vector<hht_ctx::GraphEvent> direct;
     const bool graph = use != nullptr;
@@ -728,18 +777,44 @@ int run_graph(hht_ctx* c, const Wave& w, const GraphCaps& cap, uint64_t* leaf_to
         CK(cudaGraphLaunch(use->exec, st));
     } else {
         TraceRange tr_k("level loop (direct launches)");
-        RK(launch_graph_kernels(c, w, cap, st, false, events ? &direct : nullptr));
+        RK(launch_graph_kernels(c, w, cap, grids, st, false, events ? &direct : nullptr));
     }
     // one read-back of the level totals, the statistics, the image errors,
-    // the leaf count and the status (on the graph's stream)
+    // the leaf count and the status (on the graph's stream), through the
+    // page-locked staging buffer when it could be had
     DeviceStatus hs{};
-    CK(cudaMemcpyAsync(c->h_infos.data(), c->infos.p, (w.Dmax + 1) * sizeof(LevelInfo), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(c->h_stats.data(), c->stats.p, w.stats_words * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
     c->h_img_err.assign(w.count, 0);
-    CK(cudaMemcpyAsync(c->h_img_err.data(), c->img_err.p, w.count * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(leaf_total, c->leaf_total.p, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
-    CK(cudaMemcpyAsync(&hs, c->status.p, sizeof hs, cudaMemcpyDeviceToHost, st));
+    const size_t b_inf = (w.Dmax + 1) * sizeof(LevelInfo), b_st = w.stats_words * sizeof(uint64_t),
+                 b_err = w.count * sizeof(uint32_t);
+    const size_t o_st = (b_inf + 15) & ~size_t(15), o_err = (o_st + b_st + 15) & ~size_t(15),
+                 o_tot = (o_err + b_err + 15) & ~size_t(15), o_hs = o_tot + 16, need = o_hs + sizeof(DeviceStatus);
+    if (need > c->h_stage_bytes) {
+        if (c->h_stage) cudaFreeHost(c->h_stage);
+        c->h_stage = nullptr;
+        c->h_stage_bytes = 0;
+        const size_t want = std::max<size_t>(need + need / 2, 64 << 10);
+        if (cudaHostAlloc(&c->h_stage, want, cudaHostAllocDefault) == cudaSuccess) {
+            c->h_stage_bytes = want;
+        } else {
+            cudaGetLastError();
+            c->h_stage = nullptr;
+        }
+    }
+    char* hb = (char*)c->h_stage;
+    struct Copy {
+        void* dst;
+        const void* src;
+        size_t off, bytes;
+    } copies[] = {{c->h_infos.data(), c->infos.p, 0, b_inf},
+                  {c->h_stats.data(), c->stats.p, o_st, b_st},
+                  {c->h_img_err.data(), c->img_err.p, o_err, b_err},
+                  {leaf_total, c->leaf_total.p, o_tot, sizeof(uint64_t)},
+                  {&hs, c->status.p, o_hs, sizeof hs}};
+    for (const Copy& k : copies)
+        CK(cudaMemcpyAsync(hb ? (void*)(hb + k.off) : k.dst, k.src, k.bytes, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    if (hb)
+        for (const Copy& k : copies) std::memcpy(k.dst, hb + k.off, k.bytes);
     *err = hs.err;
     if (events) {
         for (const auto& ev : graph ? use->events : direct) {
@@ -1043,6 +1118,7 @@ void hht_destroy(hht_ctx* c) {
         cudaStreamSynchronize(c->own_stream);
         cudaStreamDestroy(c->own_stream);
     }
+    if (c->h_stage) cudaFreeHost(c->h_stage);
     DevBuf* all[] = {&c->pts,       &c->img_start,  &c->img_unit, &c->units,        &c->stats,     &c->infos,      &c->status,
                      &c->leaf_total, &c->img_err,   &c->scan_states,  &c->rec[0],    &c->rec[1],     &c->preg[0],
                      &c->preg[1],   &c->cnt[0],     &c->cnt[1],       &c->vox[0],    &c->vox[1],     &c->leaves,

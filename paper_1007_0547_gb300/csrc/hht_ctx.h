@@ -51,6 +51,7 @@ struct hht_ctx {
     };
     struct CachedGraph {
         std::vector<unsigned char> key;
+        std::vector<int> grids;  // stage, then the selection and pass grids by step
         cudaGraphExec_t exec = nullptr;
         std::vector<GraphEvent> events;
     };
@@ -93,6 +94,10 @@ struct hht_ctx {
     std::vector<hht::Region> h_roots;
     hht::JobDims h_dims{};
     std::vector<uint32_t> h_img_err;
+    // page-locked staging of the graph form's read-back (one wait for all of
+    // its copies instead of a staged round trip per pageable copy)
+    void* h_stage = nullptr;
+    size_t h_stage_bytes = 0;
 
     hht::ServeState* serve = nullptr;
     std::mutex mu;

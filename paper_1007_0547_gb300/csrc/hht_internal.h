@@ -30,6 +30,15 @@ constexpr int kMaxDepth = 24;
 // (4 per parent) with HHT_E_NOMEM, which splits a batch into smaller waves.
 constexpr uint64_t kMaxLevelRecords = 0xfffffffeull;
 
+// The pass kernel cuts its voter stream into grabs of at least this many
+// records (one warp's unit of work; one chunk of 4 x 32), so a level's stream
+// of v records can keep at most ceil(v / kPassMinGrab) warps busy.  Large
+// streams get larger grabs (a quarter of a warp's share, up to 4096); the
+// minimum matters for small streams, whose latency it sets (1024 made each
+// warp of a 128^2 image's passes walk eight chunks in a row: 0.297 against
+// 0.222 ms per image).
+constexpr int kPassMinGrab = 128;
+
 // Quadrant order of the paper's quad1..quad4.
 enum Quad : int { NE = 0, NW = 1, SW = 2, SE = 3 };
 

@@ -653,7 +653,7 @@ __device__ __forceinline__ Classified<I> classify(const ParentGeoF& g, uint32_t 
 // Pass-kernel work distribution: grabs of about 1/kGrabShare of a warp's
 // even share of the stream, within [kMinGrab, kMaxGrab] records.
 constexpr uint32_t kGrabShare = 4;
-constexpr int kMinGrab = 1024;
+constexpr int kMinGrab = kPassMinGrab;
 constexpr int kMaxGrab = 4096;
 
 // Tile shape (autotuned): STEPS warp steps of 32 voters per chunk (one
