@@ -205,11 +205,18 @@ int hht_fetch_all_leaves(hht_ctx *ctx, hht_leaf *leaves, uint64_t capacity, uint
  * level loop and returns when that step's kernels have finished, with the
  * number of requests in flight or waiting (or a negative error code: the
  * requests in flight then fail with it).  At each step waiting requests are
- * admitted in arrival order while the context's memory budget (70 % of the
- * free device memory at the first step when the context has none) and 1024 request slots
- * allow; a request that does not fit is passed over by later ones that do
- * for at most 12 steps, after which nothing is admitted until it fits.  A
- * finished request's leaves stay in device memory until it is polled.
+ * admitted in arrival order while 1024 request slots and the memory budget
+ * allow.  The budget is the context's, capped at 85 % of the device memory
+ * free at the first step (that 85 % when the context has none).  Admission
+ * projects, for every step to come, the voter-list and region bounds of each
+ * request in flight at the level it will then be at (at level l a line
+ * votes in at most 2^l + (W - 1) 2^l / 2L + 2 cells; regions are at most 4^l
+ * and the votes / T), and admits a request when the two voter-stream buffers
+ * and the largest step's region buffers then need at most 90 % of the
+ * budget; requests whose deep levels fall on different steps share it.  A
+ * request that does not fit is passed over by later ones that do for at
+ * most 12 steps, after which nothing is admitted until it fits.  A finished
+ * request's leaves stay in device memory until it is polled.
  * hht_poll() returns HHT_E_PENDING until the request is done, then copies its
  * leaves into the caller's buffer (host or device memory; pinned host memory
  * is copied fastest), fills *out and releases the ticket; HHT_E_CAPACITY

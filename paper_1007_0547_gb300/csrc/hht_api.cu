@@ -131,6 +131,54 @@ int ensure_keep(hht_ctx* c, DevBuf& b, size_t bytes, size_t keep) {
     return e == cudaSuccess ? HHT_OK : cuda_fail(e);
 }
 
+int ensure_sized(hht_ctx* c, DevBuf& b, size_t bytes, size_t keep, size_t target) {
+    if (bytes <= b.bytes && b.p) return HHT_OK;
+    size_t want = std::max<size_t>((std::max(bytes, target) + 4095) & ~size_t(4095), 4096);
+    if (want > bytes) {
+        // the target is a projection: when it does not fit, the present need does
+        const uint64_t held = c->held - (keep == 0 ? b.bytes : 0);
+        size_t fr = 0, tot = 0;
+        const bool over_budget = c->budget && held + want > c->budget;
+        if (over_budget || (cudaMemGetInfo(&fr, &tot) == cudaSuccess && want > fr + (keep == 0 ? b.bytes : 0)))
+            want = std::max<size_t>((bytes + 4095) & ~size_t(4095), 4096);
+    }
+    if (!b.p || keep == 0) {
+        if (b.p) {
+            cudaStreamSynchronize(c->stream);
+            dev_free(c, b.p, b.bytes);
+            c->held -= b.bytes;
+            b.p = nullptr;
+            b.bytes = 0;
+        }
+        if (c->budget && c->held + want > c->budget) return HHT_E_NOMEM;
+        void* p = nullptr;
+        if (dev_alloc(c, &p, want) != cudaSuccess) {
+            cudaGetLastError();
+            if (p) dev_free(c, p, want);
+            return HHT_E_NOMEM;
+        }
+        b.p = p;
+        b.bytes = want;
+        c->held += want;
+        return HHT_OK;
+    }
+    if (c->budget && c->held + want > c->budget) return HHT_E_NOMEM;
+    void* p = nullptr;
+    if (dev_alloc(c, &p, want) != cudaSuccess) {
+        cudaGetLastError();
+        if (p) dev_free(c, p, want);
+        return HHT_E_NOMEM;
+    }
+    c->held += want;
+    cudaError_t e = cudaMemcpyAsync(p, b.p, std::min(keep, b.bytes), cudaMemcpyDeviceToDevice, c->stream);
+    cudaStreamSynchronize(c->stream);
+    dev_free(c, b.p, b.bytes);
+    c->held -= b.bytes;
+    b.p = p;
+    b.bytes = want;
+    return e == cudaSuccess ? HHT_OK : cuda_fail(e);
+}
+
 void release(hht_ctx* c, DevBuf& b) {
     if (b.p) {
         dev_free(c, b.p, b.bytes);

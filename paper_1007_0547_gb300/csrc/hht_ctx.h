@@ -131,5 +131,9 @@ int copy_out_on(hht_ctx* c, void* dst, const void* src, size_t bytes, cudaStream
 int ensure(hht_ctx* c, DevBuf& b, size_t bytes, bool zero = false);
 // Grow a device buffer keeping its first `keep` bytes.
 int ensure_keep(hht_ctx* c, DevBuf& b, size_t bytes, size_t keep);
+// Grow a device buffer that holds fewer than `bytes` to exactly
+// max(bytes, target) (no growth margin: a caller that knows what the buffer
+// will need passes that as `target`), keeping its first `keep` bytes.
+int ensure_sized(hht_ctx* c, DevBuf& b, size_t bytes, size_t keep, size_t target);
 void release(hht_ctx* c, DevBuf& b);
 }  // namespace hht

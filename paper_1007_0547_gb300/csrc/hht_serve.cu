@@ -40,7 +40,6 @@ struct Request {
     int slot = -1;
     int64_t t0 = 0;
     int64_t blocked_since = -1;  // first step at which it did not fit the budget
-    uint64_t est = 0;
     bool done = false;
     bool range_error = false;
     int status = HHT_E_PENDING;
@@ -68,7 +67,18 @@ struct ServeState {
     bool init = false;
     std::vector<int> free_slots;
     std::vector<uint64_t> order;  // tickets in flight, in admission order (= record order)
-    uint64_t in_flight_bytes = 0, budget = 0;
+    uint64_t budget = 0;
+    // Projected voter records of the engine's two streams: stream[k] is the
+    // stream read at step (step + k), held in vox[par ^ (k & 1)] (the one
+    // written at step + k is stream[k + 1]): the sum over the requests in
+    // flight of their bounds at the level each will then be at.
+    static constexpr int kHorizon = kMaxDepth + 3;
+    uint64_t stream[kHorizon] = {};
+    // the same for the regions of each step (the parents: every one sizes a
+    // pass record, four children's records, counters and cursors, or four
+    // leaves)
+    uint64_t regions[kHorizon] = {};
+    static constexpr uint64_t kRegionBytes = sizeof(PassRegion) + 4 * (sizeof(Region) + 16 + 8 + sizeof(DevLeaf));
     int n_i64 = 0;
     int64_t step = 0;
     int par = 0;
@@ -127,12 +137,40 @@ ServeState* serve_of(hht_ctx* c) {
     return *slot;
 }
 
-uint64_t request_bytes(const hht_image& im) {
-    // voter streams of the two deepest written levels, both halves, dense regime
-    const double n = (double)im.n;
-    const int D = im.depth;
-    const double dense = D < 3 ? n : 1.25 * n * (std::ldexp(1.0, D - 2) + std::ldexp(1.0, D - 3));
-    return (uint64_t)(2.0 * 8.0 * dense * 1.2 + 64.0 * n + (1 << 16));
+// Upper bound on a request's voter records at level l, both halves: a list
+// is kept for the levels up to depth - 2, and at level l a line votes in at
+// most 2^l + (W_h - 1) 2^l / (2L) + 2 cells (and no more than the 4^l the
+// level has), W_h the half's x extent (the image's width for half 0, its
+// height for half 1).
+uint64_t stream_bound(const hht_image& im, int l) {
+    if (im.depth < 2 || l > im.depth - 2) return 0;
+    if (l == 0) return 2 * (uint64_t)im.n;
+    const uint64_t L = 1ull << ceil_log2_i(std::max(im.W, im.H));
+    const uint64_t col = 1ull << l;
+    uint64_t total = 0;
+    for (int h = 0; h < 2; ++h) {
+        const uint64_t Wh = (uint64_t)(h ? im.H : im.W);
+        total += (uint64_t)im.n * std::min(col + (Wh - 1) * col / (2 * L) + 2, col * col);
+    }
+    return total;
+}
+
+// Upper bound on a request's regions at level l, both halves (the parents
+// of step t0 + l, for l up to depth - 1; the last ones' children are the
+// leaves, four per parent): the level's cells, and no more than its votes
+// allow at T votes each.
+uint64_t region_bound(const hht_image& im, int l) {
+    if (l >= im.depth) return 0;
+    if (l == 0) return 2;
+    const uint64_t L = 1ull << ceil_log2_i(std::max(im.W, im.H));
+    const uint64_t col = 1ull << l;
+    uint64_t total = 0;
+    for (int h = 0; h < 2; ++h) {
+        const uint64_t Wh = (uint64_t)(h ? im.H : im.W);
+        const uint64_t votes = (uint64_t)im.n * std::min(col + (Wh - 1) * col / (2 * L) + 2, col * col);
+        total += std::min(col * col, votes / (uint64_t)im.T);
+    }
+    return total;
 }
 
 #define SV_CK(call)                     \
@@ -159,17 +197,22 @@ int engine_init(hht_ctx* c, ServeState* S) {
     SV_RK(ensure(c, S->img_err, ServeState::kSlots * sizeof(uint32_t), true));  // range flags per request slot
     SV_RK(ensure(c, S->scan, sizeof(ScanState), true));
     for (int s = ServeState::kSlots - 1; s >= 0; --s) S->free_slots.push_back(s);
-    if (c->budget) {
-        S->budget = c->budget;
-    } else {
-        size_t fr = 0, tot = 0;
-        cudaMemGetInfo(&fr, &tot);
-        // the estimates already carry 20 % headroom over the dense regime's
-        // streams; what is left covers result buffers and allocation slack
-        S->budget = (uint64_t)(0.7 * (double)fr);
-    }
+    // the context's budget, but no more than the device has: admission
+    // counts on every byte of it
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    const uint64_t room = (uint64_t)(0.85 * (double)fr);
+    S->budget = c->budget ? std::min<uint64_t>(c->budget, room) : room;
     S->init = true;
     return HHT_OK;
+}
+
+// The most the projection asks of the stream buffer that is vox[par ^ odd]
+// now (odd = 0: the one read at this step).
+uint64_t projected(const ServeState* S, int odd) {
+    uint64_t m = 0;
+    for (int k = odd; k < ServeState::kHorizon; k += 2) m = std::max(m, S->stream[k]);
+    return m;
 }
 
 // Admit waiting requests into the current step.
@@ -178,16 +221,37 @@ int engine_admit(hht_ctx* c, ServeState* S) {
     // (the first one always fits an idle engine).  One that does not fit is
     // passed over by later ones that do, so that a large request at the head
     // does not hold small ones back, until it has waited kBypassSteps steps.
+    //
+    // A request fits when, with its bounds added to the projection, the two
+    // stream buffers (each at least its present size: a buffer does not
+    // shrink) and the region buffers of the largest step to come need at
+    // most 90 % of the budget (the rest: selection tiles, slack).
     std::vector<uint64_t> adm;
     {
         std::lock_guard<std::mutex> lk(S->mu);
+        const uint64_t have[2] = {S->vox[S->par].bytes / sizeof(Voter), S->vox[S->par ^ 1].bytes / sizeof(Voter)};
+        uint64_t have_reg = S->cursors.bytes + S->leaves.bytes + S->sel_flags.bytes + S->sel_data.bytes;
+        for (int k = 0; k < 2; ++k) have_reg += S->rec[k].bytes + S->cnt[k].bytes + S->preg[k].bytes;
+        auto fits = [&](const hht_image& im) {
+            uint64_t need[2] = {have[0], have[1]}, reg = 0;
+            for (int k = 0; k < ServeState::kHorizon; ++k) {
+                need[k & 1] = std::max(need[k & 1], S->stream[k] + stream_bound(im, k));
+                reg = std::max(reg, S->regions[k] + region_bound(im, k));
+            }
+            return (double)(need[0] + need[1]) * sizeof(Voter) +
+                       std::max((double)have_reg, (double)reg * ServeState::kRegionBytes) <=
+                   0.9 * (double)S->budget;
+        };
         size_t seen = 0;
         for (auto it = S->waiting.begin();
              it != S->waiting.end() && adm.size() < S->free_slots.size() && seen < ServeState::kAdmitScan; ++seen) {
             Request& r = S->reqs[*it];
-            if ((S->order.empty() && adm.empty()) || S->in_flight_bytes + r.est <= S->budget) {
+            if ((S->order.empty() && adm.empty()) || fits(r.im)) {
                 adm.push_back(*it);
-                S->in_flight_bytes += r.est;
+                for (int k = 0; k < ServeState::kHorizon; ++k) {
+                    S->stream[k] += stream_bound(r.im, k);
+                    S->regions[k] += region_bound(r.im, k);
+                }
                 it = S->waiting.erase(it);
                 continue;
             }
@@ -233,7 +297,8 @@ int engine_admit(hht_ctx* c, ServeState* S) {
     const int cp = S->par;
     SV_RK(ensure_keep(c, S->rec[cp], (S->P + 2 * m) * sizeof(Region), S->P * sizeof(Region)));
     SV_RK(ensure_keep(c, S->cnt[cp], (S->P + 2 * m) * 16, S->P * 16));
-    SV_RK(ensure_keep(c, S->vox[cp], std::max<uint64_t>(S->NV + v0, 1) * sizeof(Voter), S->NV * sizeof(Voter)));
+    SV_RK(ensure_sized(c, S->vox[cp], std::max<uint64_t>(S->NV + v0, 1) * sizeof(Voter), S->NV * sizeof(Voter),
+                       projected(S, 0) * sizeof(Voter)));
     SV_RK(ensure(c, S->pts, std::max<uint64_t>(total, 1) * sizeof(hht_point)));
     SV_RK(ensure(c, S->img_start, (m + 1) * sizeof(uint64_t)));
     SV_RK(ensure(c, S->img_unit, m * sizeof(uint32_t)));
@@ -335,7 +400,6 @@ int engine_complete(hht_ctx* c, ServeState* S, uint64_t step_leaves) {
         r.pts.clear();
         r.pts.shrink_to_fit();
         S->free_slots.push_back(r.slot);
-        S->in_flight_bytes -= r.est;
         if (ceil_log2_i(std::max(r.im.W, r.im.H)) + D > 27) --S->n_i64;
     }
     // the copies are done before any poll reads them (on any stream)
@@ -404,7 +468,8 @@ int engine_step(hht_ctx* c, ServeState* S) {
         if (hs.err & kErrTimeout) return HHT_E_TIMEOUT;
         if (hs.err) return HHT_E_CUDA;
         if (S->NV > 0) {
-            SV_RK(ensure(c, S->vox[np], std::max<uint64_t>(h_next.n_voters, 1) * sizeof(Voter)));
+            SV_RK(ensure_sized(c, S->vox[np], std::max<uint64_t>(h_next.n_voters, 1) * sizeof(Voter), 0,
+                               projected(S, 1) * sizeof(Voter)));
             a.vin = (const Voter*)S->vox[cp].p;
             a.vout = (Voter*)S->vox[np].p;
             a.cap_voters = h_next.n_voters;
@@ -419,6 +484,13 @@ int engine_step(hht_ctx* c, ServeState* S) {
     S->P = h_next.n_regions;
     S->NV = h_next.n_voters;
     S->par = np;
+    // the projection moves with the steps
+    for (int k = 0; k + 1 < ServeState::kHorizon; ++k) {
+        S->stream[k] = S->stream[k + 1];
+        S->regions[k] = S->regions[k + 1];
+    }
+    S->stream[ServeState::kHorizon - 1] = 0;
+    S->regions[ServeState::kHorizon - 1] = 0;
     return HHT_OK;
 }
 
@@ -447,7 +519,6 @@ int hht_submit(hht_ctx* c, const hht_image* image, uint64_t* ticket) {
     r.pts.swap(pts);
     r.im = im;
     r.im.points = r.pts.data();
-    r.est = request_bytes(im);
     s->waiting.push_back(t);
     *ticket = t;
     return HHT_OK;
@@ -470,7 +541,8 @@ int hht_progress(hht_ctx* c) {
             s->finished.push_back(t);
         }
         s->order.clear();
-        s->in_flight_bytes = 0;
+        std::fill(std::begin(s->stream), std::end(s->stream), 0ull);
+        std::fill(std::begin(s->regions), std::end(s->regions), 0ull);
         s->n_i64 = 0;
         s->P = s->NV = 0;
         cudaMemsetAsync(s->status.p, 0, sizeof(DeviceStatus), c->stream);

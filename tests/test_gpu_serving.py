@@ -140,27 +140,67 @@ def test_small_budget_admits_gradually(hht):
     ctx.close()
 
 
-def _admission_estimate(n, depth):
-    """The engine's admission estimate of one request (bytes): the voter
-    streams of its two deepest written levels in the dense regime, both
-    halves, with 20 % headroom, plus its points and a fixed part."""
-    dense = n if depth < 3 else 1.25 * n * (2.0 ** (depth - 2) + 2.0 ** (depth - 3))
-    return int(2.0 * 8.0 * dense * 1.2 + 64.0 * n + (1 << 16))
+def _bounds(n, W, H, depth, T, horizon=27):
+    """Per step k after admission: the request's voter records (lists are
+    kept up to level depth - 2; at level l a line votes in at most
+    2^l + (W_h - 1) 2^l / (2L) + 2 cells and no more than 4^l) and parent
+    regions (levels up to depth - 1; at most 4^l, and its votes / T), both
+    halves."""
+    L = 1
+    while L < max(W, H):
+        L *= 2
+    stream, regions = [0] * horizon, [0] * horizon
+    for l in range(horizon):
+        col = 1 << l
+        votes = [n * min(col + (Wh - 1) * col // (2 * L) + 2, col * col) for Wh in (W, H)]
+        if depth >= 2 and l <= depth - 2:
+            stream[l] = 2 * n if l == 0 else sum(votes)
+        if l <= depth - 1:
+            regions[l] = 2 if l == 0 else sum(min(col * col, v // T) for v in votes)
+    return stream, regions
+
+
+def _need(profiles):
+    """Bytes the engine's admission asks for with the given (stream, regions)
+    profiles in flight, each shifted by its admission step: the two stream
+    buffers at their largest, and the largest step's region buffers."""
+    horizon = 40
+    st, rg = [0] * horizon, [0] * horizon
+    for (stream, regions), shift in profiles:
+        for k, (a, b) in enumerate(zip(stream, regions)):
+            if k + shift < horizon:
+                st[k + shift] += a
+                rg[k + shift] += b
+    even = max(st[0::2])
+    odd = max(st[1::2])
+    return 8 * (even + odd) + max(rg) * (16 + 4 * (16 + 16 + 8 + 16))
 
 
 def test_small_requests_pass_a_blocked_large_one_until_it_has_waited(hht):
     """A large request B that does not fit the budget beside a running one
     (A) is passed over by a small one (C) that does, which finishes first.
     Once B has waited 12 steps, a small request D that arrives is held back
-    until B is admitted (after A finishes), although D would fit beside A.
+    until B is admitted, although D would fit beside A.  B is admitted at the
+    first step where the projection of both walks fits: the admission
+    projects each request's voter and region bounds over its coming levels.
     One progress() call is one step; a request of depth d finishes d steps
     after its admission."""
     rng = np.random.default_rng(20261204)
     big = (rng.integers(0, 64, size=(200, 2)).astype(np.int16), 64, 64, 20, 4)  # in flight for 20 steps
     small = (rng.integers(0, 32, size=(10, 2)).astype(np.int16), 32, 32, 3, 1)
-    est_big, est_small = _admission_estimate(200, 20), _admission_estimate(10, 3)
-    budget = est_big + 2 * est_small + (1 << 20)
-    assert budget < 2 * est_big
+    pa = _bounds(200, 64, 64, 20, 4)
+    pc = _bounds(10, 32, 32, 3, 1)
+    with_c = _need([(pa, 0), (pc, 2)])
+    # the admission allows 90 % of the budget: what A and C need, and 64 KiB
+    # for the rounding of buffer sizes, so that B fits beside A only late in
+    # A's walk (then B's regions no longer add much to A's largest step)
+    budget = int((with_c + (64 << 10)) / 0.9) + 1
+    t_b = next(t for t in range(1, 40) if _need([(pa, 0), (pa, t)]) <= 0.9 * budget)
+    assert 14 <= t_b <= 19, t_b  # B still waits when D comes (step 13: B has waited 12 steps)
+    # the engine's buffers are rounded up to 4 KiB, so its sums exceed these
+    # by a few KiB at most: B must fit at t_b with room to spare
+    assert 0.9 * budget - _need([(pa, 0), (pa, t_b)]) >= 16 << 10
+    assert _need([(pa, 0), (pa, t_b), (pc, t_b)]) <= 0.9 * budget  # D fits beside B then
 
     class _Im:
         def __init__(self, t):
@@ -188,12 +228,39 @@ def test_small_requests_pass_a_blocked_large_one_until_it_has_waited(hht):
         assert len(got) == 4
         assert done_at[tc] == 4             # admitted at step 2 beside A
         assert done_at[ta] == 19
-        assert done_at[td] == 22            # admitted with B at step 20, not at step 13
-        assert done_at[tb] == 39
+        assert done_at[tb] == t_b + 19      # admitted at step t_b
+        assert done_at[td] == t_b + 2       # admitted with B, not at step 13
         for t in (ta, tb):
             _same(got[t], want[0])
         for t in (tc, td):
             _same(got[t], want[1])
+    finally:
+        ctx.close()
+
+
+def test_budget_far_below_the_stream_holds(hht):
+    """Forty requests of the serving stream submitted at once under a budget
+    of a fifth of their summed needs (at least what the largest needs
+    alone): admission by projected bounds keeps the engine within it (summed
+    peak estimates could not: the two alternating voter buffers each keep
+    their own largest size), and every result equals the image run alone."""
+    reqs = [synth.serving_request(k) for k in range(40)]
+    alone_need = [_need([(_bounds(im.n, im.W, im.H, im.depth, im.T), 0)]) for im in reqs]
+    budget = int(max(max(alone_need) / 0.9 * 1.05, sum(alone_need) / 5))
+    want = _alone(hht, reqs)
+    ctx = hht.Context(device=0, mem_budget=budget)
+    try:
+        tickets = {ctx.submit(im.points, im.W, im.H, im.depth, im.T): k for k, im in enumerate(reqs)}
+        got = {}
+        for _ in range(100000):
+            ctx.progress()
+            for t in ctx.done_tickets():
+                got[tickets[t]] = ctx.poll(t)
+            if len(got) == len(reqs):
+                break
+        assert len(got) == len(reqs)
+        for k in range(len(reqs)):
+            _same(got[k], want[k])
     finally:
         ctx.close()
 
