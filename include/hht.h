@@ -281,9 +281,8 @@ int hht_profile_read(hht_ctx *ctx, hht_profile_counters *out);
  * The call synchronises `cuda_stream` once per level (the level's totals size
  * the next level) and before it returns, on success and on every error after
  * its first device work.  The first call on a device looks up the array's
- * device address and keeps it for the process's life, so make that first
- * call before any stream capture begins; a cudaDeviceReset between calls is
- * not supported.  The array keeps the previous call's contents; each call
+ * device address and keeps it for the process's life; a cudaDeviceReset
+ * between calls is not supported.  The array keeps the previous call's contents; each call
  * clears what it needs.  Calls that overlap on the GPU (other streams or
  * threads on the same device) race on the array and must not be made.
  * Limits: n <= HHT_NOALLOC_MAX_POINTS, depth <= HHT_NOALLOC_MAX_DEPTH, at most

@@ -11,9 +11,8 @@
 //
 // That array exists on every GPU that loads the library, from load until
 // the process exits.  Its device address is looked up once per device, by
-// the first call on that device (make that first call before any stream
-// capture begins), with cudaGetSymbolAddress, and kept for the process's
-// life: a cudaDeviceReset between calls is not supported.  Every call shares
+// the first call on that device, with cudaGetSymbolAddress, and kept for the
+// process's life: a cudaDeviceReset between calls is not supported.  Every call shares
 // the array and it keeps the last call's contents, so everything a call needs
 // at zero is cleared by that call, and calls that overlap on the GPU
 // (different streams, or different host threads on the same device) race on
