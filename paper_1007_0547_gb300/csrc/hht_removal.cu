@@ -17,8 +17,9 @@
 //     that a child's list only has to lose the points plotted since, and
 //     while none were, its votes are its length and no pass is needed;
 //   - the split of a region two levels above the leaves also counting its 16
-//     grandchildren, so that a child one level above the leaves is split (and
-//     entered) only when one of its leaves can pass;
+//     grandchildren, and that of a region three levels above them its 64
+//     great-grandchildren too, so that a child one or two levels above the
+//     leaves is split (and entered) only when one of its leaves can pass;
 //   - a removed-point bitmap (one bit per point) read through L2, so that the
 //     warp sees its own atomic updates.
 // Many images and both halves run as independent warps.  Readings (see the
@@ -123,6 +124,38 @@ __device__ __forceinline__ int grand_cell(int q, int q2) {
     return 4 * (e + e2) + (nn + n2);
 }
 
+// The 64 great-grandchildren of region (i0, j0) of side 8e (cells of side e)
+// that the line of point (x, y) crosses: in w[a >> 2], bit 8 (a & 3) + b for
+// the cell a steps east and b north of the region's SW corner.  Column a of
+// the region's 9 x 9 grid has t_a vertices below the line (a prefix, as G
+// grows with j; dj = 2 L2 e is a power of two, 2^ldj), and a cell is crossed
+// exactly when its SW vertex is below and its NE vertex is not:
+// t_{a+1} - 1 <= b < t_a.
+template <typename I>
+__device__ __forceinline__ void great_crossings(int64_t x, int64_t y, int64_t i0, int64_t j0, int64_t e, int64_t L2,
+                                                int64_t K, int ldj, uint32_t (&w)[2]) {
+    const I g00 = (I)scaled_g(x, y, i0, j0, L2, K);
+    const I di = (I)(2 * x * e), dj1 = (I)((int64_t)1 << ldj) - 1;
+    uint32_t below[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        const I v = (dj1 - (g00 + (I)a * di)) >> ldj;  // vertices of column a below the line, unclamped
+        const int t = v < (I)0 ? 0 : (v > (I)9 ? 9 : (int)v);
+        below[a] = (1u << t) - 1u;
+    }
+    w[0] = w[1] = 0u;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) w[a >> 2] |= ((below[a] & ~(below[a + 1] >> 1)) & 0xffu) << (8 * (a & 3));
+}
+
+// Leaf (bit of great_crossings, as 8a + b) under leaf quadrant q3 of
+// grandchild quadrant q2 of child quadrant q.
+__device__ __forceinline__ int great_cell(int q, int q2, int q3) {
+    auto e = [](int k) { return (k == NE || k == SE) ? 1 : 0; };
+    auto nn = [](int k) { return (k == NE || k == NW) ? 1 : 0; };
+    return 8 * (4 * e(q) + 2 * e(q2) + e(q3)) + (4 * nn(q) + 2 * nn(q2) + nn(q3));
+}
+
 template <typename I>
 __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTask* __restrict__ tasks, int ntasks,
                                                                  const int16_t* __restrict__ pts_all,
@@ -142,6 +175,9 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
     // votes of the 16 grandchildren (the leaves) of the region last split at
     // level depth - 2, counted in its split
     __shared__ uint32_t s_g[kRemWarps][16];
+    // votes of the 16 grandchildren and the 64 great-grandchildren (the
+    // leaves) of the region last split at level depth - 3, counted in its split
+    __shared__ uint32_t s_gd16[kRemWarps][16], s_gd64[kRemWarps][64];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     const int task = blockIdx.x * kRemWarps + w;
@@ -163,17 +199,23 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
     // of region (i0, j0) of side 2h, kept at level l; lens[q] receive their
     // lengths.  Returns the number of voters not removed.  `check`: some
     // entry may have been removed since the list was built (else the bitmap
-    // is not read).  `grand`: the votes of the region's 16 grandchildren are
-    // counted too, into s_g.  Four groups of 32 entries per iteration: the
-    // list entries, then their bitmap words, then their points are loaded as
-    // independent requests.
+    // is not read).  `mode` 1: the votes of the region's 16 grandchildren
+    // are counted too, into s_g; 2: into s_gd16, and those of its 64
+    // great-grandchildren into s_gd64.  Four groups of 32 entries per
+    // iteration: the list entries, then their bitmap words, then their points
+    // are loaded as independent requests.
     auto split = [&](const uint32_t* src, uint32_t len, bool check, int l, int64_t i0, int64_t j0, int64_t h,
-                     uint32_t (&lens)[4], bool grand) -> uint32_t {
+                     uint32_t (&lens)[4], int mode) -> uint32_t {
         constexpr int U = 4;
+        const bool grand = mode != 0, deep = mode == 2;
         uint32_t alive = 0;
         uint32_t gc[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) gc[k] = 0u;
+        // great-grandchildren: lane L < 16 sums the 4 cells of nibble L (word
+        // L >> 3, nibble L & 7) of the masks
+        uint32_t acc64[4] = {0u, 0u, 0u, 0u};
+        const int ldj = deep ? 1 + (tk.lL + 1) + (31 - __clz((unsigned)(h >> 2))) : 0;
         lens[0] = lens[1] = lens[2] = lens[3] = 0u;
         uint32_t* dst[4] = {child_list(l, 0), child_list(l, 1), child_list(l, 2), child_list(l, 3)};
         for (uint32_t base = 0; base < len; base += 32 * U) {
@@ -192,14 +234,17 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
                 in[u] = in[u] && ((bw[u] >> (v[u] & 31u)) & 1u) == 0u;  // not removed
                 xm[u] = in[u] ? __ldg(reinterpret_cast<const uint32_t*>(pts) + v[u]) : 0u;
             }
+            uint32_t gw[U][2];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 uint32_t cross = 0u, gbits = 0u;
+                gw[u][0] = gw[u][1] = 0u;
                 if (in[u]) {
                     const int64_t px = (int16_t)(xm[u] & 0xffffu), py = (int16_t)(xm[u] >> 16);
                     const int64_t x = half ? py : px, y = half ? px : py;
                     cross = child_crossings<I>(x, y, i0, j0, h, L2, K);
                     if (grand) gbits = grand_crossings<I>(x, y, i0, j0, h >> 1, L2, K);
+                    if (deep) great_crossings<I>(x, y, i0, j0, h >> 2, L2, K, ldj, gw[u]);
                 }
                 if (grand) {
 #pragma unroll
@@ -214,11 +259,43 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
                     lens[q] += __popc(m);
                 }
             }
+            if (deep) {
+                // the four groups' great-grandchild crossings as carry-save bit
+                // planes (ones, twos, fours), spread into byte fields four cells
+                // at a time and summed over the warp (at most 4 x 32 a byte)
+                uint32_t red[16];
+#pragma unroll
+                for (int wd = 0; wd < 2; ++wd) {
+                    const uint32_t s01 = gw[0][wd] ^ gw[1][wd], c01 = gw[0][wd] & gw[1][wd];
+                    const uint32_t s23 = gw[2][wd] ^ gw[3][wd], c23 = gw[2][wd] & gw[3][wd];
+                    const uint32_t ones = s01 ^ s23, c_ = s01 & s23;
+                    const uint32_t twos = c01 ^ c23 ^ c_, fours = (c01 & c23) | (c_ & (c01 | c23));
+#pragma unroll
+                    for (int nb = 0; nb < 8; ++nb) {
+                        const uint32_t packed = ((((ones >> (4 * nb)) & 0xfu) * 0x204081u) & 0x01010101u) +
+                                                ((((twos >> (4 * nb)) & 0xfu) * 0x408102u) & 0x02020202u) +
+                                                ((((fours >> (4 * nb)) & 0xfu) * 0x810204u) & 0x04040404u);
+                        red[8 * wd + nb] = __reduce_add_sync(0xffffffffu, packed);
+                    }
+                }
+                uint32_t mine = red[0];
+#pragma unroll
+                for (int k = 1; k < 16; ++k) mine = lane == k ? red[k] : mine;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc64[i] += (mine >> (8 * i)) & 0xffu;
+            }
         }
         if (grand && lane == 0) {
 #pragma unroll
-            for (int k = 0; k < 16; ++k) s_g[w][k] = gc[k];
+            for (int k = 0; k < 16; ++k) (deep ? s_gd16[w] : s_g[w])[k] = gc[k];
         }
+        if (deep && lane < 16) {
+            // nibble lane: cells a = 4 (lane >> 3) + ((lane & 7) >> 1), b = 4 (lane & 1) + i
+            const int a = 4 * (lane >> 3) + ((lane & 7) >> 1), b0 = 4 * (lane & 1);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) s_gd64[w][8 * a + b0 + i] = acc64[i];
+        }
+        __syncwarp();
         return alive;
     };
 
@@ -232,7 +309,7 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
     __syncwarp();
     {
         uint32_t lens[4];
-        split(nullptr, (uint32_t)n, false, 0, 0, 0, K >> 1, lens, D == 2);
+        split(nullptr, (uint32_t)n, false, 0, 0, 0, K >> 1, lens, D == 2 ? 1 : (D == 3 ? 2 : 0));
         if (lane == 0) {
             stats[0] = 1;
             stats[1] = 1;
@@ -282,6 +359,7 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
         const bool stale = removed != s_rem[w][level];
         uint32_t cnt = len;
         uint32_t lens[4] = {0u, 0u, 0u, 0u};
+        bool accounted = false;  // the child's subtree was accounted from counts
         if (cl == D) {
             // a leaf: its voters not removed are counted
             if (stale) {
@@ -301,6 +379,46 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
                     }
                 }
             }
+        } else if (cl == D - 2 && !stale) {
+            // its children's and grandchildren's votes (levels D - 1 and D)
+            // were counted when its parent was split, and nothing was plotted
+            // since: unless one of its leaves can pass, its subtree follows
+            // from those counts (none of it is accepted, so nothing is plotted
+            // while it is tested) and it is not entered
+            bool leaf_can_pass = false;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t ck = s_gd16[w][grand_cell(q, k)];
+                if (ck >= (uint32_t)T)
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) leaf_can_pass |= s_gd64[w][great_cell(q, k, m)] >= (uint32_t)T;
+            }
+            if (leaf_can_pass && len >= (uint32_t)T) {
+                cnt = split(src, len, false, cl, ci, cj, h >> 1, lens, 1);
+            } else {
+                accounted = true;
+                if (lane == 0 && len >= (uint32_t)T) {
+                    // the region passes: its four children are tested (each
+                    // evaluating its votes), and the four leaves of each child
+                    // that passes (each evaluating that child's votes)
+                    uint64_t cv = 0, cp = 0;
+                    for (int k = 0; k < 4; ++k) {
+                        const uint32_t ck = s_gd16[w][grand_cell(q, k)];
+                        cv += ck;
+                        if (ck < (uint32_t)T) continue;
+                        ++cp;
+                        uint64_t lv = 0;
+                        for (int m = 0; m < 4; ++m) lv += s_gd64[w][great_cell(q, k, m)];
+                        stats[4 * D + 0] += 4;
+                        stats[4 * D + 2] += lv;
+                        stats[4 * D + 3] += 4ull * ck;
+                    }
+                    stats[4 * (D - 1) + 0] += 4;
+                    stats[4 * (D - 1) + 1] += cp;
+                    stats[4 * (D - 1) + 2] += cv;
+                    stats[4 * (D - 1) + 3] += 4ull * len;
+                }
+            }
         } else if (cl == D - 1 && !stale) {
             // its leaves' votes were counted when its parent was split, and
             // nothing was plotted since: its own split is needed only when one
@@ -308,9 +426,9 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
 #pragma unroll
             for (int k = 0; k < 4; ++k) lens[k] = s_g[w][grand_cell(q, k)];
             if (max(max(lens[0], lens[1]), max(lens[2], lens[3])) >= (uint32_t)T && len >= (uint32_t)T)
-                split(src, len, false, cl, ci, cj, h >> 1, lens, false);
+                split(src, len, false, cl, ci, cj, h >> 1, lens, 0);
         } else {
-            cnt = split(src, len, stale, cl, ci, cj, h >> 1, lens, cl == D - 2);
+            cnt = split(src, len, stale, cl, ci, cj, h >> 1, lens, cl == D - 2 ? 1 : (cl == D - 3 ? 2 : 0));
         }
         __syncwarp();
         if (lane == 0) {
@@ -345,6 +463,8 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
                 removed += cnt;
                 __threadfence();
                 __syncwarp();
+            } else if (accounted) {
+                // its subtree's statistics were added above
             } else if (cl == D - 1 && max(max(lens[0], lens[1]), max(lens[2], lens[3])) < (uint32_t)T) {
                 // no leaf under this region can reach T, so none is accepted and
                 // nothing is plotted while its four leaves are tested: each one's
