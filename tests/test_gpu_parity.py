@@ -446,6 +446,48 @@ def test_graph_form_first_call_is_one_graph_launch_and_later_jobs_replay_it(hht)
         c.close()
 
 
+def test_graph_grids_follow_the_job_and_a_covering_graph_is_replayed(hht):
+    """Each level's grids come from the job's own bounds (powers of two), and
+    any graph of the same arguments whose grids cover a job's may run it: a
+    graph captured for a large job runs a smaller one, while a context that
+    saw only the small job captures a second graph for the large one (whose
+    buffers are then larger) and replays it for both.  Every result equals
+    the oracle's."""
+    # the same depth (a graph's arguments include it): 128^2 and 1024^2 at depth 10
+    p128 = synth.plain_128(index=2)
+    small = (p128.points, 128, 128, 10, 20)
+    big = synth.plain_1024()
+    large = (big.points, big.W, big.H, big.depth, big.T)
+    assert big.depth == 10
+    want = {"s": oracle.detect(*small), "l": oracle.detect(*large)}
+
+    def run(c, job, key):
+        _same(c.detect(*job, leaves_on_device=False), want[key])
+        return c.profile_read()
+
+    c = hht.Context(device=0)
+    try:
+        c.profile(True)
+        p = run(c, large, "l")
+        assert p["graph_captures"] == 1 and p["graph_launches"] == 1, p
+        p = run(c, small, "s")  # the large job's graph covers it
+        assert p["graph_captures"] == 1 and p["graph_launches"] == 2, p
+    finally:
+        c.close()
+    c = hht.Context(device=0)
+    try:
+        c.profile(True)
+        p = run(c, small, "s")
+        assert p["graph_captures"] == 1 and p["graph_launches"] == 1, p
+        p = run(c, large, "l")  # not covered by the small job's grids
+        assert p["graph_captures"] == 2 and p["graph_launches"] == 2, p
+        p = run(c, small, "s")  # the large job's buffers and graph now serve both
+        p = run(c, large, "l")
+        assert p["graph_captures"] == 2 and p["graph_launches"] == 4 and p["graph_fallbacks"] == 0, p
+    finally:
+        c.close()
+
+
 def test_graph_and_level_forms_agree(hht):
     """The graph form and the level form (one launch per level, exact sizes)
     give the same leaves and statistics, single images and batches."""
