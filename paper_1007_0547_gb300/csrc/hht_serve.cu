@@ -5,15 +5,18 @@
 // level (step - t0); the stage / select / pass kernels read that per unit, so
 // units of different ages share every launch.  One hht_progress() call is one
 // step:
-//   1. admit waiting requests while request slots and the memory budget allow:
+//   1. admit waiting requests while request slots and the memory budget allow
+//      (by a projection of every request's bounds over the steps to come):
 //      their level-0 regions, vote counters and voter streams are appended to
 //      the current step's (stage kernel);
 //   2. select: children of every current region (or leaves, for units that
 //      reach their depth now);
 //   3. pass: the next step's voter stream and vote counters;
 //   4. requests whose units reached their depth at this step are complete:
-//      their leaves (one block per unit, in the paper's depth-first order) and
-//      statistics are copied out and their slot and budget are released.
+//      their leaves (one block per unit, in the paper's depth-first order) are
+//      copied into a device buffer of their own until polled, their statistics
+//      are read back, and their slot is released (their bounds leave the
+//      projection as the steps pass).
 // Requests that arrive while others run are admitted at the next step and
 // overlap with them on the device; results do not depend on the mix.
 #include <cuda_runtime.h>
