@@ -342,7 +342,8 @@ def single_image_latency(ctx, runs: int = 30):
 
 
 def run_ncu_case(args, rank):
-    """One small detection for an ncu capture of the pass kernel: 8 images of
+    """One small detection for an ncu capture.  removal1024: the solution()
+    walk of the 1024x1024 image.  batch8: the pass kernel on 8 images of
     the 256-image batch (indices 0, 32, ..., 224), level form (one launch per
     pass), tile shape --tile-shape.  Prints, per pass launch s, the records it
     reads (the level s-1 stream) and writes (the level s stream), from the
@@ -353,6 +354,17 @@ def run_ncu_case(args, rank):
     from paper_1007_0547_gb300 import hht
     import torch
     if rank != 0:
+        return
+    if args.ncu_case == "removal1024":
+        # the solution() walk of the 1024x1024 image, once (one removal_kernel launch)
+        im = synth.plain_1024()
+        ctx = hht.Context(device=0)
+        res, _ = ctx.detect_removal(torch.from_numpy(im.points).cuda(), im.W, im.H, im.depth, im.T,
+                                    with_plotted=False)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": "removal1024", "n": im.n, "depth": im.depth, "T": im.T,
+                          "accepted_cells": int(res.n_leaves), "code_tests": int(res.total_tests())}), flush=True)
+        ctx.close()
         return
     imgs = [synth.batch_image(k) for k in range(0, 256, 32)]
     dev = [(torch.from_numpy(im.points).cuda(), im.W, im.H, im.depth, im.T) for im in imgs]
@@ -415,8 +427,9 @@ def main():
                     help="time only the front-end kernel (Sobel and split) on the 4096x4096 grey image")
     ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--serve-load", type=float, default=0.8, help="offered rate as a fraction of the saturated rate")
-    ap.add_argument("--ncu-case", choices=["batch8"],
-                    help="run one small detection for an ncu capture of the pass kernel and exit")
+    ap.add_argument("--ncu-case", choices=["batch8", "removal1024"],
+                    help="run one small detection for an ncu capture (of the pass kernel: batch8; of the "
+                         "solution() walk: removal1024) and exit")
     ap.add_argument("--tile-shape", type=int, default=0, help="pass tile shape of --ncu-case")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
