@@ -70,7 +70,7 @@ uint64_t step_bound(uint64_t n, int D) {
     return steps > 1.8e19 ? ~0ull : (uint64_t)steps;
 }
 
-constexpr int kRemWarps = 4;  // warps per block
+constexpr int kRemWarps = 4;  // warps per (image, half): one block walks one half
 
 __device__ __forceinline__ int64_t scaled_g(int64_t x, int64_t y, int64_t i, int64_t j, int64_t L2, int64_t K) {
     // K * F at grid vertex (i, j): 4L j + 2x i - 2LK - Kx - Ky (L2 = 2L)
@@ -156,32 +156,51 @@ __device__ __forceinline__ int great_cell(int q, int q2, int q3) {
     return 8 * (4 * e(q) + 2 * e(q2) + e(q3)) + (4 * nn(q) + 2 * nn(q2) + nn(q3));
 }
 
-template <typename I>
-__global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTask* __restrict__ tasks, int ntasks,
-                                                                 const int16_t* __restrict__ pts_all,
-                                                                 uint32_t* __restrict__ lists_all,
-                                                                 uint32_t* __restrict__ bitmap_all,
-                                                                 DevLeaf* __restrict__ leaves_all,
-                                                                 uint64_t* __restrict__ stats_all,
-                                                                 uint64_t* __restrict__ leaf_counts,
-                                                                 DeviceStatus* status) {
-    // the walk's stack, per level: next quadrant, the region's SW corner, the
-    // lengths of its children's lists, its votes when entered and the
-    // removed-point count at that time
-    __shared__ int32_t s_quad[kRemWarps][kMaxDepth + 1];
-    __shared__ uint32_t s_i0[kRemWarps][kMaxDepth + 1], s_j0[kRemWarps][kMaxDepth + 1];
-    __shared__ uint32_t s_len[kRemWarps][kMaxDepth + 1][4];
-    __shared__ uint32_t s_m[kRemWarps][kMaxDepth + 1], s_rem[kRemWarps][kMaxDepth + 1];
+// The walk of one (image, half) by a block of WARPS warps.  Every warp keeps
+// its own copy of the stack and takes the same decisions from the same
+// values, so the walk's control runs in step in all of them; every pass over
+// a list (a split, a count of a leaf's voters not removed, the marking of an
+// accepted leaf's voters) is shared out among the warps in groups of 128
+// entries and ends with a block barrier.  Every read of a list or of the
+// bitmap happens inside such a pass, so no warp rewrites a list (or marks a
+// point) while another still reads it.  Lists are sets: the warps append to
+// a child's list through shared cursors, so the order of its entries varies
+// from run to run but no count does.
+template <typename I, int WARPS>
+__global__ void __launch_bounds__(32 * WARPS) removal_kernel(const RemovalTask* __restrict__ tasks, int ntasks,
+                                                          const int16_t* __restrict__ pts_all,
+                                                          uint32_t* __restrict__ lists_all,
+                                                          uint32_t* __restrict__ bitmap_all,
+                                                          DevLeaf* __restrict__ leaves_all,
+                                                          uint64_t* __restrict__ stats_all,
+                                                          uint64_t* __restrict__ leaf_counts,
+                                                          DeviceStatus* status) {
+    // the walk's stack (one copy per warp), per level: next quadrant, the
+    // region's SW corner, the lengths of its children's lists, its votes when
+    // entered and the removed-point count at that time
+    __shared__ int32_t s_quad[WARPS][kMaxDepth + 1];
+    __shared__ uint32_t s_i0[WARPS][kMaxDepth + 1], s_j0[WARPS][kMaxDepth + 1];
+    __shared__ uint32_t s_len[WARPS][kMaxDepth + 1][4];
+    __shared__ uint32_t s_m[WARPS][kMaxDepth + 1], s_rem[WARPS][kMaxDepth + 1];
     // votes of the 16 grandchildren (the leaves) of the region last split at
     // level depth - 2, counted in its split
-    __shared__ uint32_t s_g[kRemWarps][16];
+    __shared__ uint32_t s_g[WARPS][16];
     // votes of the 16 grandchildren and the 64 great-grandchildren (the
     // leaves) of the region last split at level depth - 3, counted in its split
-    __shared__ uint32_t s_gd16[kRemWarps][16], s_gd64[kRemWarps][64];
+    __shared__ uint32_t s_gd16[WARPS][16], s_gd64[WARPS][64];
+    // each warp's share of a pass, two sets used in turn: [0, 16) grandchild
+    // votes, [16, 80) great-grandchild votes, 80 the entries not removed,
+    // [81, 85) the entries appended to each child's list
+    constexpr int kPart = 85;
+    __shared__ uint32_t s_part[2][WARPS][kPart];
+    // the children's list cursors; they count on across passes (mod 2^32),
+    // and each warp knows their value at the start of a pass
+    __shared__ uint32_t s_cur[4];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const bool lead = threadIdx.x == 0;
     const uint32_t lt = (1u << lane) - 1u;
-    const int task = blockIdx.x * kRemWarps + w;
-    if (task >= ntasks) return;
+    const int task = blockIdx.x;
+    if (task >= ntasks) return;  // the same for the whole block
     const RemovalTask tk = tasks[task];
     const int16_t* pts = pts_all + 2 * tk.pts;
     uint32_t* lists = lists_all + tk.lists;
@@ -193,6 +212,25 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
     const int half = tk.half;
     // the four children's lists of the region entered at level l
     auto child_list = [&](int l, int q) { return lists + (uint64_t)(4 * l + q) * (uint64_t)n; };
+    uint32_t cur0[4] = {0u, 0u, 0u, 0u};  // the cursors at the start of the next pass
+    int epoch = 0;                        // passes ended so far (selects the set of shares)
+
+    // End of a pass: wait for every warp's share, then lane k of every warp
+    // sums entries k, k + 32 and k + 64 of the shares.
+    auto gather = [&](uint32_t (&t)[3]) {
+        __syncthreads();
+        const uint32_t(*p)[kPart] = s_part[epoch & 1];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const int k = lane + 32 * r;
+            uint32_t s = 0u;
+            if (k < kPart)
+#pragma unroll
+                for (int v = 0; v < WARPS; ++v) s += p[v][k];
+            t[r] = s;
+        }
+        ++epoch;
+    };
 
     // Split the voters of `src` (len entries, or the points 0 .. len - 1 when
     // src is null) that are not removed into the lists of the four children
@@ -201,14 +239,15 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
     // entry may have been removed since the list was built (else the bitmap
     // is not read).  `mode` 1: the votes of the region's 16 grandchildren
     // are counted too, into s_g; 2: into s_gd16, and those of its 64
-    // great-grandchildren into s_gd64.  Four groups of 32 entries per
-    // iteration: the list entries, then their bitmap words, then their points
-    // are loaded as independent requests.
+    // great-grandchildren into s_gd64.  Warp w takes the groups of 128
+    // entries w, w + WARPS, ...; in a group, each lane's four entries are
+    // loaded as independent requests (list entries, then their bitmap words,
+    // then their points).
     auto split = [&](const uint32_t* src, uint32_t len, bool check, int l, int64_t i0, int64_t j0, int64_t h,
                      uint32_t (&lens)[4], int mode) -> uint32_t {
         constexpr int U = 4;
         const bool grand = mode != 0, deep = mode == 2;
-        uint32_t alive = 0;
+        uint32_t alive = 0, mine[4] = {0u, 0u, 0u, 0u};
         uint32_t gc[16];
 #pragma unroll
         for (int k = 0; k < 16; ++k) gc[k] = 0u;
@@ -216,9 +255,9 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
         // L >> 3, nibble L & 7) of the masks
         uint32_t acc64[4] = {0u, 0u, 0u, 0u};
         const int ldj = deep ? 1 + (tk.lL + 1) + (31 - __clz((unsigned)(h >> 2))) : 0;
-        lens[0] = lens[1] = lens[2] = lens[3] = 0u;
         uint32_t* dst[4] = {child_list(l, 0), child_list(l, 1), child_list(l, 2), child_list(l, 3)};
-        for (uint32_t base = 0; base < len; base += 32 * U) {
+        bool bad = false;
+        for (uint32_t base = 32 * U * w; base < len; base += 32 * U * WARPS) {
             uint32_t v[U], bw[U], xm[U];
             bool in[U];
 #pragma unroll
@@ -226,6 +265,10 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
                 const uint32_t idx = base + 32 * u + lane;
                 in[u] = idx < len;
                 v[u] = in[u] ? (src ? __ldcg(&src[idx]) : idx) : 0u;
+                if (v[u] >= (uint32_t)n) {  // an entry that names no point (cannot happen)
+                    bad = bad || in[u];
+                    in[u] = false;
+                }
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) bw[u] = (in[u] && check) ? __ldcg(&bitmap[v[u] >> 5]) : 0u;
@@ -234,15 +277,16 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
                 in[u] = in[u] && ((bw[u] >> (v[u] & 31u)) & 1u) == 0u;  // not removed
                 xm[u] = in[u] ? __ldg(reinterpret_cast<const uint32_t*>(pts) + v[u]) : 0u;
             }
-            uint32_t gw[U][2];
+            uint32_t gw[U][2], cross[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                uint32_t cross = 0u, gbits = 0u;
+                uint32_t gbits = 0u;
+                cross[u] = 0u;
                 gw[u][0] = gw[u][1] = 0u;
                 if (in[u]) {
                     const int64_t px = (int16_t)(xm[u] & 0xffffu), py = (int16_t)(xm[u] >> 16);
                     const int64_t x = half ? py : px, y = half ? px : py;
-                    cross = child_crossings<I>(x, y, i0, j0, h, L2, K);
+                    cross[u] = child_crossings<I>(x, y, i0, j0, h, L2, K);
                     if (grand) gbits = grand_crossings<I>(x, y, i0, j0, h >> 1, L2, K);
                     if (deep) great_crossings<I>(x, y, i0, j0, h >> 2, L2, K, ldj, gw[u]);
                 }
@@ -251,12 +295,32 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
                     for (int k = 0; k < 16; ++k) gc[k] += __popc(__ballot_sync(0xffffffffu, (gbits >> k) & 1u));
                 }
                 alive += __popc(__ballot_sync(0xffffffffu, in[u]));
+            }
+            // this group's entries per child, one cursor reservation per child
+            // (lanes 0-3), then every entry at its reserved position
+            uint32_t c[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const bool c = (cross >> q) & 1u;
-                    const uint32_t m = __ballot_sync(0xffffffffu, c);
-                    if (c) dst[q][lens[q] + __popc(m & lt)] = v[u];
-                    lens[q] += __popc(m);
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) c[q] += __popc(__ballot_sync(0xffffffffu, (cross[u] >> q) & 1u));
+            const uint32_t cq = lane == 0 ? c[0] : (lane == 1 ? c[1] : (lane == 2 ? c[2] : c[3]));
+            uint32_t at = 0u;
+            if (lane < 4 && cq != 0u) at = atomicAdd(&s_cur[lane], cq);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t pos = __shfl_sync(0xffffffffu, at, q) - cur0[q];  // offset in the child's list
+                if (c[q] == 0u) continue;
+                mine[q] += c[q];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const bool x = (cross[u] >> q) & 1u;
+                    const uint32_t m = __ballot_sync(0xffffffffu, x);
+                    const uint32_t at_q = pos + __popc(m & lt);
+                    if (x) {
+                        if (at_q < (uint32_t)n) dst[q][at_q] = v[u];
+                        else bad = true;
+                    }
+                    pos += __popc(m);
                 }
             }
             if (deep) {
@@ -278,43 +342,66 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
                         red[8 * wd + nb] = __reduce_add_sync(0xffffffffu, packed);
                     }
                 }
-                uint32_t mine = red[0];
+                uint32_t r = red[0];
 #pragma unroll
-                for (int k = 1; k < 16; ++k) mine = lane == k ? red[k] : mine;
+                for (int k = 1; k < 16; ++k) r = lane == k ? red[k] : r;
 #pragma unroll
-                for (int i = 0; i < 4; ++i) acc64[i] += (mine >> (8 * i)) & 0xffu;
+                for (int i = 0; i < 4; ++i) acc64[i] += (r >> (8 * i)) & 0xffu;
             }
         }
-        if (grand && lane == 0) {
+        if (bad) atomicOr(&status->err, kErrInvariant);  // a cursor ran past the list (cannot happen)
+        uint32_t* part = s_part[epoch & 1][w];
+        if (lane == 0) {
+            if (grand)
 #pragma unroll
-            for (int k = 0; k < 16; ++k) (deep ? s_gd16[w] : s_g[w])[k] = gc[k];
+                for (int k = 0; k < 16; ++k) part[k] = gc[k];
+            part[80] = alive;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) part[81 + q] = mine[q];
         }
         if (deep && lane < 16) {
             // nibble lane: cells a = 4 (lane >> 3) + ((lane & 7) >> 1), b = 4 (lane & 1) + i
             const int a = 4 * (lane >> 3) + ((lane & 7) >> 1), b0 = 4 * (lane & 1);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) s_gd64[w][8 * a + b0 + i] = acc64[i];
+            for (int i = 0; i < 4; ++i) part[16 + 8 * a + b0 + i] = acc64[i];
+        }
+        uint32_t t[3];
+        gather(t);
+        if (grand && lane < 16) (deep ? s_gd16[w] : s_g[w])[lane] = t[0];
+        if (deep) {
+            if (lane >= 16) s_gd64[w][lane - 16] = t[0];
+            s_gd64[w][16 + lane] = t[1];
+            if (lane < 16) s_gd64[w][48 + lane] = t[2];
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, t[2], 16);  // entry 80
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            lens[q] = __shfl_sync(0xffffffffu, t[2], 17 + q);  // entries 81-84
+            cur0[q] += lens[q];
         }
         __syncwarp();
-        return alive;
+        return total;
     };
 
     // level 0: every line crosses the whole parameter space (points outside
     // the image fail the image); the root's voters are split at once
-    for (int64_t k = lane; k < n; k += 32) {
+    for (int64_t k = threadIdx.x; k < n; k += 32 * WARPS) {
         const int32_t px = pts[2 * k], py = pts[2 * k + 1];
         if (px < 0 || px >= tk.W || py < 0 || py >= tk.H) atomicOr(&status->err, kErrRange);
     }
-    for (int64_t k = lane; k < (n + 31) / 32; k += 32) bitmap[k] = 0u;
-    __syncwarp();
+    for (int64_t k = threadIdx.x; k < (n + 31) / 32; k += 32 * WARPS) bitmap[k] = 0u;
+    if (threadIdx.x < 4) s_cur[threadIdx.x] = 0u;
+    __syncthreads();
     {
         uint32_t lens[4];
         split(nullptr, (uint32_t)n, false, 0, 0, 0, K >> 1, lens, D == 2 ? 1 : (D == 3 ? 2 : 0));
-        if (lane == 0) {
+        if (lead) {
             stats[0] = 1;
             stats[1] = 1;
             stats[2] = (uint64_t)n;
             stats[3] = (uint64_t)n;
+        }
+        if (lane == 0) {
             s_quad[w][0] = 0;
             s_i0[w][0] = 0;
             s_j0[w][0] = 0;
@@ -363,21 +450,26 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
         if (cl == D) {
             // a leaf: its voters not removed are counted
             if (stale) {
-                cnt = 0;
-                for (uint32_t base = 0; base < len; base += 128) {
+                uint32_t c = 0u;
+                for (uint32_t base = 128 * w; base < len; base += 128 * WARPS) {
                     uint32_t v[4];
                     bool in[4];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         in[u] = base + 32 * u + lane < len;
                         v[u] = in[u] ? __ldcg(&src[base + 32 * u + lane]) : 0u;
+                        in[u] = in[u] && v[u] < (uint32_t)n;  // an entry names a point (always)
                     }
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         if (in[u]) in[u] = ((__ldcg(&bitmap[v[u] >> 5]) >> (v[u] & 31u)) & 1u) == 0u;
-                        cnt += __popc(__ballot_sync(0xffffffffu, in[u]));
+                        c += __popc(__ballot_sync(0xffffffffu, in[u]));
                     }
                 }
+                if (lane == 0) s_part[epoch & 1][w][80] = c;
+                uint32_t t[3];
+                gather(t);
+                cnt = __shfl_sync(0xffffffffu, t[2], 16);
             }
         } else if (cl == D - 2 && !stale) {
             // its children's and grandchildren's votes (levels D - 1 and D)
@@ -397,7 +489,7 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
                 cnt = split(src, len, false, cl, ci, cj, h >> 1, lens, 1);
             } else {
                 accounted = true;
-                if (lane == 0 && len >= (uint32_t)T) {
+                if (lead && len >= (uint32_t)T) {
                     // the region passes: its four children are tested (each
                     // evaluating its votes), and the four leaves of each child
                     // that passes (each evaluating that child's votes)
@@ -431,16 +523,16 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
             cnt = split(src, len, stale, cl, ci, cj, h >> 1, lens, cl == D - 2 ? 1 : (cl == D - 3 ? 2 : 0));
         }
         __syncwarp();
-        if (lane == 0) {
+        if (lead) {
             stats[4 * cl + 0] += 1;
             stats[4 * cl + 2] += cnt;
             stats[4 * cl + 3] += evaluated;
         }
         if ((int64_t)cnt >= T) {
-            if (lane == 0) stats[4 * cl + 1] += 1;
+            if (lead) stats[4 * cl + 1] += 1;
             if (cl == D) {
                 // solution(): plot the voters and remove them from later regions
-                if (lane == 0) {
+                if (lead) {
                     if (nleaves < tk.cap) {
                         DevLeaf f;
                         f.half = (uint32_t)half;
@@ -456,13 +548,13 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
                 // the same voters as counted (nothing was removed in between);
                 // an entry removed earlier keeps its bit, so every entry's bit
                 // is set
-                for (uint32_t k = lane; k < len; k += 32) {
+                for (uint32_t k = threadIdx.x; k < len; k += 32 * WARPS) {
                     const uint32_t v = __ldcg(&src[k]);
-                    atomicOr(&bitmap[v >> 5], 1u << (v & 31u));
+                    if (v < (uint32_t)n) atomicOr(&bitmap[v >> 5], 1u << (v & 31u));
                 }
                 removed += cnt;
                 __threadfence();
-                __syncwarp();
+                __syncthreads();
             } else if (accounted) {
                 // its subtree's statistics were added above
             } else if (cl == D - 1 && max(max(lens[0], lens[1]), max(lens[2], lens[3])) < (uint32_t)T) {
@@ -470,7 +562,7 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
                 // nothing is plotted while its four leaves are tested: each one's
                 // votes are its list's length and its evaluated codes are this
                 // region's votes, so the region is not entered
-                if (lane == 0) {
+                if (lead) {
                     stats[4 * D + 0] += 4;
                     stats[4 * D + 2] += (uint64_t)lens[0] + lens[1] + lens[2] + lens[3];
                     stats[4 * D + 3] += 4ull * cnt;
@@ -490,8 +582,8 @@ __global__ void __launch_bounds__(32 * kRemWarps) removal_kernel(const RemovalTa
             }
         }
     }
-    if (!finished && lane == 0) atomicOr(&status->err, kErrInvariant);
-    if (lane == 0) leaf_counts[task] = nleaves;
+    if (!finished && lead) atomicOr(&status->err, kErrInvariant);
+    if (lead) leaf_counts[task] = nleaves;
 }
 
 // One byte per point and half (half-major) from the removed-point bitmaps of
@@ -592,19 +684,19 @@ int run_removal(hht_ctx* c, const hht_image* im, int count, hht_result* outs, ui
     CKR(cudaMemsetAsync(c->status.p, 0, sizeof(DeviceStatus), st));
     uint64_t* d_counts = (uint64_t*)((char*)c->rem_tasks.p + tasks.size() * sizeof(RemovalTask));
     const int ntasks = 2 * count;
-    const int grid = (ntasks + kRemWarps - 1) / kRemWarps;
+    const int grid = ntasks;  // one block per (image, half)
     // int32 corner arithmetic is exact while log2 L + depth <= 27 (every
     // vertex value then lies within 2^29), as in the level kernel
     bool i64 = false;
     for (int g = 0; g < count; ++g)
         if (ceil_log2_i(std::max(im[g].W, im[g].H)) + im[g].depth > 27) i64 = true;
     if (i64)
-        removal_kernel<int64_t><<<grid, 32 * kRemWarps, 0, st>>>(
+        removal_kernel<int64_t, kRemWarps><<<grid, 32 * kRemWarps, 0, st>>>(
             (const RemovalTask*)c->rem_tasks.p, ntasks, (const int16_t*)c->rem_pts.p, (uint32_t*)c->rem_lists.p,
             (uint32_t*)c->rem_bitmap.p, (DevLeaf*)c->rem_leaves.p, (uint64_t*)c->rem_stats.p,
             d_counts, (DeviceStatus*)c->status.p);
     else
-        removal_kernel<int32_t><<<grid, 32 * kRemWarps, 0, st>>>(
+        removal_kernel<int32_t, kRemWarps><<<grid, 32 * kRemWarps, 0, st>>>(
             (const RemovalTask*)c->rem_tasks.p, ntasks, (const int16_t*)c->rem_pts.p, (uint32_t*)c->rem_lists.p,
             (uint32_t*)c->rem_bitmap.p, (DevLeaf*)c->rem_leaves.p, (uint64_t*)c->rem_stats.p,
             d_counts, (DeviceStatus*)c->status.p);
