@@ -351,7 +351,8 @@ int hht_set_batch_mode(hht_ctx *ctx, int32_t mode);
  * each in visiting order, with their votes when visited; `plotted` (NULL or
  * 2 * n bytes, host or device) receives one flag per point and half
  * (half-major).  The visiting order makes this a sequential walk: each
- * (image, half) is one warp on the GPU; hht_detect_removal_batch runs many
+ * (image, half) is one block of four warps on the GPU, which share every
+ * pass over a region's voters; hht_detect_removal_batch runs many
  * images at once (no plotted flags).  Every accepted cell plots at least T
  * points, so a buffer of 2 * (n / T + 1) leaves always suffices; with a
  * smaller one the call returns HHT_E_CAPACITY with n_leaves set and copies

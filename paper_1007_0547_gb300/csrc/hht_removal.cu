@@ -5,11 +5,12 @@
 // count therefore depends on every cell accepted before it, which makes the
 // traversal order part of the result.
 //
-// GPU form: one warp per (image, half) walks that half's quadtree in the
-// paper's order, with
+// GPU form: one block of four warps per (image, half) walks that half's
+// quadtree in the paper's order, with
 //   - an explicit stack in shared memory (per level: next quadrant, region,
 //     its children's list lengths, its votes when entered and the number of
-//     points plotted by then);
+//     points plotted by then), one copy per warp: every warp takes the same
+//     decisions, and every pass over a list is shared out among the warps;
 //   - the voters of a region split into its four children's lists once,
 //     when it is entered (exact integer corner signs on the region's 3 x 3
 //     grid decide all four children's votes at once, in int32 when
@@ -21,8 +22,8 @@
 //     great-grandchildren too, so that a child one or two levels above the
 //     leaves is split (and entered) only when one of its leaves can pass;
 //   - a removed-point bitmap (one bit per point) read through L2, so that the
-//     warp sees its own atomic updates.
-// Many images and both halves run as independent warps.  Readings (see the
+//     block sees its own atomic updates.
+// Many images and both halves run as independent blocks.  Readings (see the
 // oracle): removal is per half; the `tests` statistic counts the codes
 // actually evaluated (parent voters not removed by then); a region passes
 // when its votes reach T.
