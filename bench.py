@@ -699,7 +699,7 @@ def main():
         rm = min(r_ms)
         rtests = sum(r.total_tests() for r in rres)
         removal = {"what": "depth-first traversal with the paper's solution() step (voters of accepted cells removed "
-                           "from later regions); one warp per image and half",
+                           "from later regions); one block of four warps per image and half",
                    "ms_per_step": rm, "tests_per_s": rtests / (rm / 1e3), "images_per_s": len(dev_images) / (rm / 1e3),
                    "accepted_cells": int(sum(r.n_leaves for r in rres))}
 
